@@ -1,0 +1,201 @@
+/*
+ * submat.h -- C ABI of the GB300 submatrix sign library.
+ *
+ * The library evaluates the density matrix of a symmetric block-sparse,
+ * orthogonalised Kohn-Sham matrix K,
+ *
+ *     D = 1/2 (I - sign(K - mu I))            (Eq. DsignSym with S = I)
+ *
+ * by the submatrix method (Section III-A): for every block column j it
+ * assembles the principal submatrix a_j = K[N(j), N(j)] - mu I over the block
+ * rows N(j) that hold a stored block in column j, evaluates sign(a_j) on the
+ * GPU by scaled Newton-Schulz iteration (Section II-B), and copies the columns
+ * of block j of 1/2 (I - sign(a_j)) into block column j of D, keeping K's
+ * block pattern.
+ *
+ * Matrix format (both K and D, and the gradients Dbar and Kbar): block CSR
+ * over nblk block rows.  row_ptr[nblk + 1] (int64) and col_idx[nnzb] (int32)
+ * list the stored blocks; column indices must be strictly increasing inside a
+ * row, every diagonal block must be stored and the pattern must be symmetric
+ * (block (i, j) stored iff (j, i) stored).  Block p of row r and column c
+ * holds block_sizes[r] * block_sizes[c] doubles, row-major; blocks follow
+ * one another in CSR order with no padding, so block p starts at
+ * sum_{q < p} area(q).  K must be numerically symmetric (K_(j,i) = K_(i,j)^T).
+ *
+ * Conventions.
+ *   - Device pointers are CUDA device memory that the caller owns.  The plan
+ *     owns its own workspaces (it allocates them with cudaMalloc when it is
+ *     created, and on first use of the host-buffer entry point).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every entry point that returns a status synchronises that
+ *     stream before it returns, so results and statuses are final.
+ *   - No C++ exception crosses this boundary.  On failure a function returns
+ *     a nonzero submat_status and submat_last_error() describes it.
+ *   - A plan is not thread-safe: calls on one plan must not overlap.
+ */
+#ifndef SUBMAT_H
+#define SUBMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct submat_plan submat_plan;
+
+typedef enum {
+  SUBMAT_OK = 0,
+  SUBMAT_ERR_INVALID_ARG = 1,   /* null pointer, bad size or option */
+  SUBMAT_ERR_PATTERN = 2,       /* pattern not symmetric / unsorted / out of range / no diagonal */
+  SUBMAT_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  SUBMAT_ERR_OOM = 4,           /* workspace does not fit (even one submatrix per wave) */
+  SUBMAT_ERR_NONFINITE = 5,     /* K (or a gradient input) holds NaN or Inf */
+  SUBMAT_ERR_NOT_CONVERGED = 6, /* some submatrix hit max_iter; D is written, see stats */
+  SUBMAT_ERR_MU_NO_ROOT = 7,    /* mu search ended on a step of the electron-count staircase */
+  SUBMAT_ERR_TIMEOUT = 8,       /* a bounded device wait gave up */
+  SUBMAT_ERR_UNSUPPORTED = 9    /* feature not available for these sizes/options */
+} submat_status;
+
+typedef enum {
+  SUBMAT_FP64 = 0,               /* Newton-Schulz in FP64 throughout */
+  SUBMAT_FP32 = 1,               /* Newton-Schulz in FP32 (no refinement) */
+  SUBMAT_MIXED_BF16_REFINE = 2   /* BF16 tensor-core Newton-Schulz, then FP64 refinement */
+} submat_precision;
+
+typedef struct {
+  int prec;                    /* submat_precision */
+  double tol;                  /* stop when ||X^2 - I||_F <= sqrt(n_j) * tol, then one more
+                                  iteration (Section VI-A: involution as stopping test);
+                                  0 selects 1e-14 for FP64, 1e-6 for FP32, 3e-3 for BF16 */
+  int max_iter;                /* Newton-Schulz iteration cap; 0 selects 100 */
+  int beta_mode;               /* X_0 = a / beta.  0: beta = min(max row abs-sum, ||a||_F)
+                                  (a guaranteed bound on the spectral radius);
+                                  1: beta = 1.05 x a power-iteration estimate */
+  int symmetrize;              /* 1: return (D + D^T) / 2 on the pattern; 0: column-assembled D */
+  size_t workspace_cap_bytes;  /* device workspace cap; 0 = 80 % of free memory at plan time */
+  int refine_rounds;           /* mixed path: correction rounds; 0 selects 2 */
+  int reserved[8];             /* must be zero */
+} submat_options;
+
+/* Aggregate statistics of the last submat_sign / submat_mu_search call. */
+typedef struct {
+  int32_t nsub;            /* number of submatrices (= nblk) */
+  int32_t n_min, n_max;    /* smallest / largest submatrix dimension */
+  int32_t waves;           /* workspace waves the batch was split into */
+  int32_t iters_min, iters_max; /* Newton-Schulz iterations over submatrices */
+  int32_t not_converged;   /* submatrices that hit max_iter */
+  int32_t refine_rounds;   /* correction rounds run (mixed path) */
+  double  sum_n2, sum_n3;  /* sum over submatrices of n_j^2 and n_j^3 */
+  double  flops_ns;        /* standard-count Newton-Schulz flops: sum_j 4 n_j^3 iters_j */
+  double  flops_refine;    /* standard-count refinement flops */
+  double  max_resid;       /* largest final ||X^2 - I||_F / sqrt(n_j) */
+  double  ms_gather, ms_ns, ms_refine, ms_scatter; /* phase times (CUDA events) */
+  size_t  workspace_bytes; /* device workspace held by the plan */
+} submat_stats;
+
+/* Fill *opt with defaults (FP64, default tolerances, beta_mode 0). */
+void submat_options_default(submat_options* opt);
+
+/*
+ * Build a plan for one block pattern (Section IV-A: the global pattern and
+ * the per-submatrix index maps are computed once and reused).
+ *   nblk         number of block rows/columns (>= 1)
+ *   block_sizes  host int32[nblk], each >= 1
+ *   row_ptr      host int64[nblk + 1], row_ptr[0] = 0, non-decreasing
+ *   col_idx      host int32[row_ptr[nblk]]
+ *   opt          host options (NULL = defaults)
+ *   stream       stream used for the plan's uploads
+ *   out          receives the plan (NULL on failure)
+ * The host arrays are copied; the caller may free them afterwards.
+ * Errors: INVALID_ARG, PATTERN, OOM, CUDA.
+ */
+submat_status submat_plan_create(int nblk, const int32_t* block_sizes,
+                                 const int64_t* row_ptr, const int32_t* col_idx,
+                                 const submat_options* opt, void* stream,
+                                 submat_plan** out);
+
+/* Release the plan and all device memory it owns.  NULL is allowed. */
+submat_status submat_plan_destroy(submat_plan* plan);
+
+/*
+ * D = 1/2 (I - sign(K - mu I)) by the submatrix method (Section III-A,
+ * Eq. DsignSym with S = I, sign(0) = 0 as in Eq. signevext).
+ *   K_vals  device double[plan value count], the BSR values of K
+ *   mu      chemical potential
+ *   D_vals  device double[plan value count], written in K's layout
+ * Returns OK, NONFINITE (K holds NaN/Inf; D untouched), NOT_CONVERGED
+ * (D written; some submatrix reached max_iter, e.g. a singular one),
+ * TIMEOUT, CUDA.
+ */
+submat_status submat_sign(submat_plan* plan, const double* K_vals, double mu,
+                          double* D_vals, void* stream);
+
+/* As submat_sign, but K_vals and D_vals are HOST arrays; the copies to and
+ * from the device run inside the call (on plan-owned device buffers). */
+submat_status submat_sign_host(submat_plan* plan, const double* K_host, double mu,
+                               double* D_host, void* stream);
+
+/*
+ * Tr D in FP64 (Section IV-G: the electron count n_elec).  Sums the diagonal
+ * entries of the diagonal blocks; the reduction order is fixed, so the
+ * result is deterministic.
+ *   D_vals  device double[plan value count];  tr  host double (output)
+ */
+submat_status submat_trace(submat_plan* plan, const double* D_vals, double* tr,
+                           void* stream);
+
+/*
+ * Find mu with Tr D(mu) = n_el (canonical adaptation, Section IV-G /
+ * Algorithm 1), re-evaluating the submatrix signs at each trial mu.
+ * Safeguarded Newton-bisection: Newton steps use dN/dmu from the adjoint when
+ * it is above a floor and the step stays inside the bracket, else bisection.
+ *   n_el       target electron count;  mu0  starting guess
+ *   tol        stop when |Tr D - n_el| <= tol * n_el
+ *   max_steps  cap on sign evaluations (>= 1)
+ *   mu_out     host double: final mu
+ *   D_vals     device double[value count]: D at mu_out
+ * At zero temperature Tr D(mu) is a staircase: if the bracket shrinks below
+ * 1e-10 x the spectral bound without meeting tol, the call returns
+ * MU_NO_ROOT with mu_out and D at the bracket end nearest n_el.
+ */
+submat_status submat_mu_search(submat_plan* plan, const double* K_vals, double n_el,
+                               double mu0, double tol, int max_steps, double* mu_out,
+                               double* D_vals, void* stream);
+
+/*
+ * Vector-Jacobian product of K -> D (the adjoint of the submatrix density
+ * map).  Block column j contributes abar_j = -1/2 L_sign(a_j, G_j), where G_j
+ * holds Dbar's block column j in its columns of block j and zeros elsewhere,
+ * and L_sign is the Frechet derivative of sign (computed by the coupled
+ * Newton-Schulz iteration on [[X, E], [0, X]]); abar_j is added into every
+ * stored block of K that a_j was assembled from.
+ *   Dbar_vals  device double[value count]  (upstream gradient, K's layout)
+ *   Kbar_vals  device double[value count]  (output, overwritten)
+ *   dN_dmu     host double or NULL: 1/2 sum_j sum_{c in block j} L_sign(a_j, I)_cc
+ */
+submat_status submat_sign_backward(submat_plan* plan, const double* K_vals, double mu,
+                                   const double* Dbar_vals, double* Kbar_vals,
+                                   double* dN_dmu, void* stream);
+
+/* Number of doubles in K's (and D's) value array for this plan. */
+int64_t submat_plan_value_count(const submat_plan* plan);
+
+/* Statistics of the last sign evaluation (host struct). */
+submat_status submat_get_stats(const submat_plan* plan, submat_stats* out);
+
+/* Per-submatrix data of the last sign evaluation, host arrays of length nblk
+ * (any may be NULL): dimension n_j, Newton-Schulz iterations, final
+ * ||X^2 - I||_F / sqrt(n_j), and beta. */
+submat_status submat_get_sub_stats(const submat_plan* plan, int32_t* dims, int32_t* iters,
+                                   double* resid, double* beta);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* submat_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SUBMAT_H */

@@ -1,0 +1,136 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "submat.h"
+
+namespace submat {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define SM_CUDA(x)                                                                   \
+  do {                                                                               \
+    cudaError_t e_ = (x);                                                            \
+    if (e_ != cudaSuccess) {                                                         \
+      ::submat::set_error("%s:%d: %s failed: %s", __FILE__, __LINE__, #x,            \
+                          cudaGetErrorString(e_));                                   \
+      return SUBMAT_ERR_CUDA;                                                        \
+    }                                                                                \
+  } while (0)
+
+#define SM_TRY(x)                                \
+  do {                                           \
+    submat_status s_ = (x);                      \
+    if (s_ != SUBMAT_OK) return s_;              \
+  } while (0)
+
+// Device status word bits (plan->d_flags[0]).
+enum : int { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2, FLAG_DIVERGED = 4, FLAG_BOUNDS = 8 };
+
+// Newton-Schulz state of one submatrix.
+enum : int { ST_ACTIVE = 0, ST_LAST = 1, ST_DONE = 2 };
+
+// Pattern and per-submatrix maps (device, indexed by global block / CSR position).
+struct PatternDev {
+  const int32_t* bs;       // [nblk] block sizes
+  const int64_t* row_ptr;  // [nblk + 1]
+  const int32_t* col;      // [nnzb]; row j lists N(j) (the pattern is symmetric)
+  const int64_t* valptr;   // [nnzb + 1] first value of each block
+  const int32_t* locoff;   // [nnzb] local row/column offset of local block t of submatrix j
+  const int32_t* tpos;     // [nnzb] CSR position of the transposed block
+  const int32_t* nsub;     // [nblk] submatrix dimension n_j
+  const int32_t* koff;     // [nblk] local offset of block j inside submatrix j
+  const int32_t* diagpos;  // [nblk] CSR position of block (j, j)
+};
+
+// One wave: a set of submatrices whose dense buffers fit the workspace together.
+struct WaveDev {
+  int nsub;
+  const int32_t* sub;  // [nsub] global block column j of local submatrix s
+  const int64_t* off;  // [nsub] element offset of submatrix s in every workspace buffer
+  const int32_t* ld;   // [nsub] leading dimension (multiple of 64)
+  const int32_t* n;    // [nsub] dimension n_j
+};
+
+// Per-submatrix Newton-Schulz state (device, indexed by local s).
+struct NsStateDev {
+  int* state;       // ST_*
+  int* iters;       // iterations done
+  int* par;         // buffer (0/1) that holds the current / final iterate
+  int* notconv;     // 1 if max_iter was hit
+  double* res2;     // ||X^2 - I||_F^2 accumulated by the squaring GEMM
+  double* rprev;    // previous ||X^2 - I||_F / sqrt(n)
+  double* beta;     // scale of X_0
+  unsigned long long* gersh;  // max row abs-sum (bits of a non-negative double)
+  double* fro2;     // ||a||_F^2
+};
+
+// ---- kernel launchers (kernels.cu) ----
+cudaError_t launch_gather(const PatternDev& g, const WaveDev& w, const int2* items, int nitems,
+                          int nb_max, const double* K, double mu, double* A, NsStateDev ns,
+                          int* flags, cudaStream_t st);
+cudaError_t launch_beta(const WaveDev& w, NsStateDev ns, int beta_mode, cudaStream_t st);
+cudaError_t launch_scale_f64(const WaveDev& w, const double* A, double* X, const double* beta,
+                             int64_t max_ld2, cudaStream_t st);
+cudaError_t launch_scale_f32(const WaveDev& w, const double* A, float* X, const double* beta,
+                             int64_t max_ld2, cudaStream_t st);
+cudaError_t launch_ns_update(const WaveDev& w, NsStateDev ns, double tol, double floor_thr,
+                             int max_iter, int* flags, cudaStream_t st);
+cudaError_t launch_ns_post(const WaveDev& w, NsStateDev ns, int par_new, int* d_active,
+                           cudaStream_t st);
+cudaError_t launch_scatter_f64(const PatternDev& g, const WaveDev& w, NsStateDev ns,
+                               const double* buf0, const double* buf1, double* D,
+                               double* trpart, int nb_max, cudaStream_t st);
+cudaError_t launch_scatter_f32(const PatternDev& g, const WaveDev& w, NsStateDev ns,
+                               const float* buf0, const float* buf1, double* D,
+                               double* trpart, int nb_max, cudaStream_t st);
+cudaError_t launch_trace(const PatternDev& g, int nblk, const double* D, double* part,
+                         double* out, cudaStream_t st);
+cudaError_t launch_symmetrize_impl(const PatternDev& g, int64_t nnzb, const double* Din,
+                                   double* Dout, const int64_t* rowof, cudaStream_t st);
+cudaError_t launch_check_finite(const double* v, int64_t count, int* flags, cudaStream_t st);
+
+// ---- FP64 GEMM (gemm_f64.cu) ----
+// C = alpha * A * B + beta * C0 on every listed 64x64 tile (s, ti, tj);
+// all operands are row-major per submatrix at wave offsets.  With sym != 0
+// the listed tiles have ti <= tj and the transposed tile is written as well.
+struct GemmF64Args {
+  WaveDev w;
+  const int4* items;
+  int nitems;
+  const double* A;
+  const double* B;
+  const double* C0;
+  double* C;
+  double alpha, beta;
+  int sym;
+  double* res2;      // optional: accumulate ||C - I_n||_F^2 per submatrix
+  const int* state;  // optional: skip submatrices with state == skip_state
+  int skip_state;
+};
+cudaError_t launch_gemm_f64(const GemmF64Args& a, cudaStream_t st);
+
+// Same contract in FP32 (FFMA).
+struct GemmF32Args {
+  WaveDev w;
+  const int4* items;
+  int nitems;
+  const float* A;
+  const float* B;
+  const float* C0;
+  float* C;
+  double alpha, beta;
+  int sym;
+  double* res2;
+  const int* state;
+  int skip_state;
+};
+cudaError_t launch_gemm_f32(const GemmF32Args& a, cudaStream_t st);
+
+}  // namespace submat

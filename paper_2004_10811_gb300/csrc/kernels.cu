@@ -1,0 +1,387 @@
+// Memory-bound kernels of the submatrix path: assembly (gather), scaling,
+// Newton-Schulz bookkeeping, extraction (scatter) and the trace.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace submat {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Section III-A step 1 (block-wise, Section IV-C): rows [locoff[t], +bs[i1])
+// of the dense a_j = K[N(j), N(j)] - mu I, for local block row t of
+// submatrix s.  One CTA per (s, t); the CTA of the last block row also zeroes
+// the padding rows n_j..ld-1.  Row abs-sums (Gershgorin) and ||a_j||_F^2 are
+// accumulated for the scaling of X_0.
+__global__ void __launch_bounds__(256) k_gather(PatternDev g, WaveDev w, const int2* items,
+                                                const double* __restrict__ K, double mu,
+                                                double* __restrict__ A, NsStateDev ns,
+                                                int* flags) {
+  extern __shared__ int sm[];
+  const int2 it = items[blockIdx.x];
+  const int s = it.x, t = it.y;
+  const int j = w.sub[s];
+  const int64_t rp0 = g.row_ptr[j];
+  const int nb = int(g.row_ptr[j + 1] - rp0);
+  int* nbr = sm;            // N(j)
+  int* blk = sm + nb;       // CSR position of block (i1, N(j)[u]) or -1
+  int* loc = sm + 2 * nb;   // local offsets, loc[nb] = n
+  const int n = w.n[s];
+  const int ld = w.ld[s];
+  for (int u = threadIdx.x; u < nb; u += blockDim.x) {
+    nbr[u] = g.col[rp0 + u];
+    blk[u] = -1;
+    loc[u] = g.locoff[rp0 + u];
+  }
+  if (threadIdx.x == 0) loc[nb] = n;
+  __syncthreads();
+  const int i1 = nbr[t];
+  const int64_t q0 = g.row_ptr[i1], q1 = g.row_ptr[i1 + 1];
+  for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    const int c = g.col[q];
+    int lo = 0, hi = nb - 1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int v = nbr[mid];
+      if (v == c) { blk[mid] = int(q); break; }
+      if (v < c) lo = mid + 1; else hi = mid - 1;
+    }
+  }
+  __syncthreads();
+  const int r0 = loc[t];
+  const int br = g.bs[i1];
+  double* Aj = A + w.off[s];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int rows_total = br + ((t == nb - 1) ? (ld - n) : 0);
+  double fro = 0.0;
+  bool bad = false;
+  for (int rr = warp; rr < rows_total; rr += nw) {
+    if (rr < br) {
+      double* row = Aj + int64_t(r0 + rr) * ld;
+      double rs = 0.0;
+      for (int c = lane; c < ld; c += 32) {
+        double v = 0.0;
+        if (c < n) {
+          int lo = 0, hi = nb - 1;  // largest u with loc[u] <= c
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (loc[mid] <= c) lo = mid; else hi = mid - 1;
+          }
+          const int q = blk[lo];
+          if (q >= 0) {
+            const int i2 = nbr[lo];
+            const int cc = c - loc[lo];
+            v = K[g.valptr[q] + int64_t(rr) * g.bs[i2] + cc];
+            if (i2 == i1 && cc == rr) v -= mu;
+          }
+        }
+        if (!isfinite(v)) bad = true;
+        row[c] = v;
+        rs += fabs(v);
+        fro += v * v;
+      }
+      rs = warp_sum(rs);
+      if (lane == 0 && isfinite(rs)) atomicMax(&ns.gersh[s], (unsigned long long)__double_as_longlong(rs));
+    } else {
+      double* row = Aj + int64_t(n + rr - br) * ld;
+      for (int c = lane; c < ld; c += 32) row[c] = 0.0;
+    }
+  }
+  fro = warp_sum(fro);
+  if (lane == 0) atomicAdd(&ns.fro2[s], fro);
+  if (bad) atomicOr(flags, FLAG_NONFINITE);
+}
+
+// beta_s >= rho(a_s): min(max row abs-sum, ||a_s||_F).  A zero submatrix has
+// sign 0 (Eq. signevext), so it is finished before any iteration.
+__global__ void k_beta(WaveDev w, NsStateDev ns, int beta_mode) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= w.nsub) return;
+  const double gersh = __longlong_as_double((long long)ns.gersh[s]);
+  const double fro = sqrt(ns.fro2[s]);
+  double b = fmin(gersh, fro);
+  (void)beta_mode;
+  ns.iters[s] = 0;
+  ns.notconv[s] = 0;
+  ns.par[s] = 0;
+  ns.res2[s] = 0.0;
+  ns.rprev[s] = 1e300;
+  if (!(b > 0.0) || !isfinite(b)) {
+    ns.beta[s] = 1.0;
+    ns.state[s] = ST_DONE;
+  } else {
+    ns.beta[s] = b;
+    ns.state[s] = ST_ACTIVE;
+  }
+}
+
+template <typename T>
+__global__ void k_scale(WaveDev w, const double* __restrict__ A, T* __restrict__ X,
+                        const double* __restrict__ beta) {
+  const int s = blockIdx.y;
+  const int ld = w.ld[s];
+  const int64_t total = int64_t(ld) * ld;
+  const int64_t off = w.off[s];
+  const double ib = 1.0 / beta[s];
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x)
+    X[off + e] = T(A[off + e] * ib);
+}
+
+// After the squaring GEMM: r = ||X^2 - I||_F / sqrt(n); decide whether this
+// is the last iteration (Section VI-A: involution as the stopping test).
+__global__ void k_ns_update(WaveDev w, NsStateDev ns, double tol, double floor_thr,
+                            int max_iter, int* flags) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= w.nsub) return;
+  if (ns.state[s] != ST_ACTIVE) return;
+  const double r = sqrt(ns.res2[s] / double(w.n[s]));
+  ns.res2[s] = 0.0;
+  const int it = ++ns.iters[s];
+  const double prev = ns.rprev[s];
+  ns.rprev[s] = r;
+  if (!isfinite(r) || r > 1e6) {
+    ns.state[s] = ST_DONE;
+    ns.notconv[s] = 1;
+    atomicOr(flags, FLAG_DIVERGED);
+    return;
+  }
+  const bool converged = r <= tol;
+  const bool at_floor = (r < floor_thr) && (r > 0.5 * prev);
+  if (converged || at_floor) {
+    ns.state[s] = ST_LAST;
+  } else if (it >= max_iter) {
+    ns.state[s] = ST_LAST;
+    ns.notconv[s] = 1;
+  }
+}
+
+__global__ void k_ns_post(WaveDev w, NsStateDev ns, int par_new, int* d_active) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int active = 0;
+  if (s < w.nsub) {
+    const int st = ns.state[s];
+    if (st == ST_LAST) {
+      ns.state[s] = ST_DONE;
+      ns.par[s] = par_new;
+    } else if (st == ST_ACTIVE) {
+      ns.par[s] = par_new;
+      active = 1;
+    }
+  }
+  active = __syncthreads_count(active);
+  if (threadIdx.x == 0 && active) atomicAdd(d_active, active);
+}
+
+// Section III-A step 3: block column j of D from the columns of block j of
+// 1/2 (I - S_j).  S_j is symmetric, so row koff + c of S_j is read (coalesced)
+// for column koff + c.  The diagonal block's trace is written to trpart[j].
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter(PatternDev g, WaveDev w, NsStateDev ns,
+                                                 const T* __restrict__ buf0,
+                                                 const T* __restrict__ buf1,
+                                                 double* __restrict__ D, double* trpart) {
+  extern __shared__ int sm[];
+  __shared__ double red[8];
+  const int s = blockIdx.x;
+  const int j = w.sub[s];
+  const int64_t rp0 = g.row_ptr[j];
+  const int nb = int(g.row_ptr[j + 1] - rp0);
+  int* loc = sm;
+  const int n = w.n[s], ld = w.ld[s];
+  for (int u = threadIdx.x; u < nb; u += blockDim.x) loc[u] = g.locoff[rp0 + u];
+  if (threadIdx.x == 0) loc[nb] = n;
+  __syncthreads();
+  const T* S = (ns.par[s] ? buf1 : buf0) + w.off[s];
+  const int koff = g.koff[j];
+  const int bj = g.bs[j];
+  double tr = 0.0;
+  const int64_t total = int64_t(bj) * n;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const int c = int(e / n);
+    const int col = int(e - int64_t(c) * n);
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (loc[mid] <= col) lo = mid; else hi = mid - 1;
+    }
+    const int r = col - loc[lo];
+    const int64_t p = g.tpos[rp0 + lo];  // block (N(j)[lo], j)
+    const double sv = double(S[int64_t(koff + c) * ld + col]);
+    const bool diag = (col == koff + c);
+    const double v = (diag ? 0.5 : 0.0) - 0.5 * sv;
+    D[g.valptr[p] + int64_t(r) * bj + c] = v;
+    if (diag) tr += v;
+  }
+  tr = warp_sum(tr);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tr;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int q = 0; q < int(blockDim.x >> 5); ++q) acc += red[q];
+    trpart[j] = acc;
+  }
+}
+
+__global__ void k_diag_sums(PatternDev g, int nblk, const double* __restrict__ D, double* part) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nblk) return;
+  const int64_t p = g.diagpos[j];
+  const int b = g.bs[j];
+  const double* blk = D + g.valptr[p];
+  double acc = 0.0;
+  for (int c = 0; c < b; ++c) acc += blk[c * b + c];
+  part[j] = acc;
+}
+
+// Fixed-order reduction (one CTA): deterministic for a given nblk.
+__global__ void k_reduce_fixed(const double* part, int count, double* out) {
+  __shared__ double red[1024];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// (D + D^T) / 2 on the pattern: block p gets 1/2 (D_p + D_{tpos[p]}^T).
+__global__ void k_symmetrize(PatternDev g, int64_t nnzb, const double* __restrict__ Din,
+                             double* __restrict__ Dout, const int64_t* __restrict__ rowof) {
+  const int64_t p = blockIdx.x;
+  if (p >= nnzb) return;
+  const int r = int(rowof[p]);
+  const int c = g.col[p];
+  const int br = g.bs[r], bc = g.bs[c];
+  const double* a = Din + g.valptr[p];
+  const double* b = Din + g.valptr[g.tpos[p]];  // block (c, r): bc x br
+  double* o = Dout + g.valptr[p];
+  for (int e = threadIdx.x; e < br * bc; e += blockDim.x) {
+    const int u = e / bc, v = e - (e / bc) * bc;
+    o[e] = 0.5 * (a[e] + b[v * br + u]);
+  }
+}
+
+__global__ void k_check_finite(const double* __restrict__ v, int64_t count, int* flags) {
+  bool bad = false;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < count;
+       e += int64_t(gridDim.x) * blockDim.x)
+    if (!isfinite(v[e])) bad = true;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, FLAG_NONFINITE);
+}
+
+}  // namespace
+
+cudaError_t launch_gather(const PatternDev& g, const WaveDev& w, const int2* items, int nitems,
+                          int nb_max, const double* K, double mu, double* A, NsStateDev ns,
+                          int* flags, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  const size_t smem = size_t(3 * nb_max + 1) * sizeof(int);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  k_gather<<<nitems, 256, smem, st>>>(g, w, items, K, mu, A, ns, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_beta(const WaveDev& w, NsStateDev ns, int beta_mode, cudaStream_t st) {
+  k_beta<<<(w.nsub + 255) / 256, 256, 0, st>>>(w, ns, beta_mode);
+  return cudaGetLastError();
+}
+
+static dim3 scale_grid(const WaveDev& w, int64_t max_ld2) {
+  int64_t bx = (max_ld2 + 256 * 8 - 1) / (256 * 8);
+  if (bx > 512) bx = 512;
+  if (bx < 1) bx = 1;
+  return dim3(unsigned(bx), unsigned(w.nsub));
+}
+
+cudaError_t launch_scale_f64(const WaveDev& w, const double* A, double* X, const double* beta,
+                             int64_t max_ld2, cudaStream_t st) {
+  k_scale<double><<<scale_grid(w, max_ld2), 256, 0, st>>>(w, A, X, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_f32(const WaveDev& w, const double* A, float* X, const double* beta,
+                             int64_t max_ld2, cudaStream_t st) {
+  k_scale<float><<<scale_grid(w, max_ld2), 256, 0, st>>>(w, A, X, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_update(const WaveDev& w, NsStateDev ns, double tol, double floor_thr,
+                             int max_iter, int* flags, cudaStream_t st) {
+  k_ns_update<<<(w.nsub + 255) / 256, 256, 0, st>>>(w, ns, tol, floor_thr, max_iter, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_post(const WaveDev& w, NsStateDev ns, int par_new, int* d_active,
+                           cudaStream_t st) {
+  k_ns_post<<<(w.nsub + 255) / 256, 256, 0, st>>>(w, ns, par_new, d_active);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t scatter_impl(const PatternDev& g, const WaveDev& w, NsStateDev ns,
+                                const T* buf0, const T* buf1, double* D, double* trpart,
+                                int nb_max, cudaStream_t st) {
+  const size_t smem = size_t(nb_max + 1) * sizeof(int);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_scatter<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  k_scatter<T><<<w.nsub, 256, smem, st>>>(g, w, ns, buf0, buf1, D, trpart);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_f64(const PatternDev& g, const WaveDev& w, NsStateDev ns,
+                               const double* buf0, const double* buf1, double* D,
+                               double* trpart, int nb_max, cudaStream_t st) {
+  return scatter_impl<double>(g, w, ns, buf0, buf1, D, trpart, nb_max, st);
+}
+
+cudaError_t launch_scatter_f32(const PatternDev& g, const WaveDev& w, NsStateDev ns,
+                               const float* buf0, const float* buf1, double* D,
+                               double* trpart, int nb_max, cudaStream_t st) {
+  return scatter_impl<float>(g, w, ns, buf0, buf1, D, trpart, nb_max, st);
+}
+
+cudaError_t launch_trace(const PatternDev& g, int nblk, const double* D, double* part,
+                         double* out, cudaStream_t st) {
+  k_diag_sums<<<(nblk + 255) / 256, 256, 0, st>>>(g, nblk, D, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_reduce_fixed<<<1, 1024, 0, st>>>(part, nblk, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symmetrize_impl(const PatternDev& g, int64_t nnzb, const double* Din,
+                                   double* Dout, const int64_t* rowof, cudaStream_t st) {
+  if (nnzb <= 0) return cudaSuccess;
+  k_symmetrize<<<unsigned(nnzb), 64, 0, st>>>(g, nnzb, Din, Dout, rowof);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const double* v, int64_t count, int* flags, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_check_finite<<<unsigned(blocks), 256, 0, st>>>(v, count, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace submat

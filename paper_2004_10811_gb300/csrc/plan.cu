@@ -1,0 +1,669 @@
+// Host side of the submatrix library: the plan (Section IV-A: global pattern,
+// per-submatrix index maps, waves), the Newton-Schulz drivers and the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "plan.cuh"
+
+namespace submat {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+const char* last_error() { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// device memory helpers
+// ---------------------------------------------------------------------------
+
+submat_status dev_alloc(void** p, size_t bytes, const char* what) {
+  *p = nullptr;
+  if (bytes == 0) return SUBMAT_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("cudaMalloc of %zu bytes for %s failed: %s", bytes, what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SUBMAT_ERR_OOM : SUBMAT_ERR_CUDA;
+  }
+  return SUBMAT_OK;
+}
+
+template <typename T>
+static submat_status upload(T** dst, const std::vector<T>& src, cudaStream_t st, const char* what) {
+  SM_TRY(dev_alloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T), what));
+  if (!src.empty())
+    SM_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return SUBMAT_OK;
+}
+
+Plan::~Plan() {
+  for (void* p : owned) cudaFree(p);
+  if (h_pinned) cudaFreeHost(h_pinned);
+  for (auto& e : ev) if (e) cudaEventDestroy(e);
+}
+
+template <typename T>
+submat_status Plan::alloc(T** p, size_t count, const char* what) {
+  void* q = nullptr;
+  SM_TRY(dev_alloc(&q, count * sizeof(T), what));
+  if (q) owned.push_back(q);
+  *p = static_cast<T*>(q);
+  return SUBMAT_OK;
+}
+
+template <typename T>
+submat_status Plan::put(T** p, const std::vector<T>& v, cudaStream_t st, const char* what) {
+  SM_TRY(upload(p, v, st, what));
+  if (*p) owned.push_back(*p);
+  return SUBMAT_OK;
+}
+
+// bytes of workspace per dense element for each precision
+static size_t bytes_per_elem(int prec) {
+  switch (prec) {
+    case SUBMAT_FP64: return 3 * 8;                 // X ping-pong + X^2
+    case SUBMAT_FP32: return 8 + 3 * 4;             // A (FP64) + X ping-pong + X^2
+    default: return mixed_bytes_per_elem();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// plan construction
+// ---------------------------------------------------------------------------
+
+static submat_status validate_pattern(int nblk, const int32_t* bs, const int64_t* rp,
+                                      const int32_t* ci) {
+  if (rp[0] != 0) { set_error("row_ptr[0] must be 0"); return SUBMAT_ERR_PATTERN; }
+  for (int i = 0; i < nblk; ++i) {
+    if (bs[i] < 1) { set_error("block_sizes[%d] = %d < 1", i, bs[i]); return SUBMAT_ERR_INVALID_ARG; }
+    if (rp[i + 1] < rp[i]) { set_error("row_ptr decreases at row %d", i); return SUBMAT_ERR_PATTERN; }
+  }
+  const int64_t nnzb = rp[nblk];
+  for (int i = 0; i < nblk; ++i) {
+    bool diag = false;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      const int c = ci[p];
+      if (c < 0 || c >= nblk) {
+        set_error("col_idx[%lld] = %d out of range [0, %d)", (long long)p, c, nblk);
+        return SUBMAT_ERR_PATTERN;
+      }
+      if (p > rp[i] && ci[p - 1] >= c) {
+        set_error("col_idx not strictly increasing in row %d", i);
+        return SUBMAT_ERR_PATTERN;
+      }
+      if (c == i) diag = true;
+    }
+    if (!diag) { set_error("diagonal block (%d, %d) is not stored", i, i); return SUBMAT_ERR_PATTERN; }
+  }
+  (void)nnzb;
+  return SUBMAT_OK;
+}
+
+submat_status validate_pattern_public(int nblk, const int32_t* bs, const int64_t* rp,
+                                      const int32_t* ci) {
+  return validate_pattern(nblk, bs, rp, ci);
+}
+
+static int64_t find_block(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci, int r,
+                          int c) {
+  auto b = ci.begin() + rp[r], e = ci.begin() + rp[r + 1];
+  auto it = std::lower_bound(b, e, c);
+  if (it == e || *it != c) return -1;
+  return int64_t(it - ci.begin());
+}
+
+submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, const int32_t* ci_,
+                          const submat_options* o, cudaStream_t st) {
+  nblk = nblk_;
+  opt = *o;
+  bs.assign(bs_, bs_ + nblk);
+  row_ptr.assign(rp_, rp_ + nblk + 1);
+  nnzb = row_ptr[nblk];
+  col.assign(ci_, ci_ + nnzb);
+  // value offsets (CSR order, no padding)
+  valptr.assign(nnzb + 1, 0);
+  rowof.assign(nnzb, 0);
+  for (int r = 0; r < nblk; ++r)
+    for (int64_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
+      rowof[p] = r;
+      valptr[p + 1] = valptr[p] + int64_t(bs[r]) * bs[col[p]];
+    }
+  nvals = valptr[nnzb];
+  // symmetry of the pattern and the transpose map
+  tpos.assign(nnzb, -1);
+  diagpos.assign(nblk, -1);
+  for (int r = 0; r < nblk; ++r)
+    for (int64_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
+      const int c = col[p];
+      const int64_t q = find_block(row_ptr, col, c, r);
+      if (q < 0) {
+        set_error("pattern is not symmetric: block (%d, %d) stored but (%d, %d) is not", r, c, c, r);
+        return SUBMAT_ERR_PATTERN;
+      }
+      if (q > INT32_MAX) { set_error("more than 2^31 blocks"); return SUBMAT_ERR_UNSUPPORTED; }
+      tpos[p] = int32_t(q);
+      if (c == r) diagpos[r] = int32_t(p);
+    }
+  // submatrices: N(j) = column j's block rows = row j's columns (symmetric)
+  locoff.assign(nnzb, 0);
+  nsub.assign(nblk, 0);
+  koff.assign(nblk, 0);
+  nb_max = 0;
+  n_max = 0;
+  n_min = INT32_MAX;
+  sum_n2 = sum_n3 = 0.0;
+  for (int j = 0; j < nblk; ++j) {
+    int64_t acc = 0;
+    for (int64_t p = row_ptr[j]; p < row_ptr[j + 1]; ++p) {
+      locoff[p] = int32_t(acc);
+      if (col[p] == j) koff[j] = int32_t(acc);
+      acc += bs[col[p]];
+    }
+    if (acc > 32768) {
+      set_error("submatrix %d has dimension %lld > 32768", j, (long long)acc);
+      return SUBMAT_ERR_UNSUPPORTED;
+    }
+    nsub[j] = int32_t(acc);
+    nb_max = std::max<int>(nb_max, int(row_ptr[j + 1] - row_ptr[j]));
+    n_max = std::max<int>(n_max, nsub[j]);
+    n_min = std::min<int>(n_min, nsub[j]);
+    sum_n2 += double(acc) * acc;
+    sum_n3 += double(acc) * acc * acc;
+  }
+  if (nb_max * 3 + 1 > 48 * 1024) {
+    set_error("a submatrix spans %d blocks; at most 16383 are supported", nb_max);
+    return SUBMAT_ERR_UNSUPPORTED;
+  }
+  // device copies of the pattern and maps
+  {
+    int32_t* d_bs; int64_t* d_rp; int32_t* d_col; int64_t* d_vp; int32_t* d_loc; int32_t* d_tp;
+    int32_t* d_ns; int32_t* d_ko; int32_t* d_dp;
+    SM_TRY(put(&d_bs, bs, st, "block sizes"));
+    SM_TRY(put(&d_rp, row_ptr, st, "row_ptr"));
+    SM_TRY(put(&d_col, col, st, "col_idx"));
+    SM_TRY(put(&d_vp, valptr, st, "value offsets"));
+    SM_TRY(put(&d_loc, locoff, st, "local offsets"));
+    SM_TRY(put(&d_tp, tpos, st, "transpose map"));
+    SM_TRY(put(&d_ns, nsub, st, "submatrix dims"));
+    SM_TRY(put(&d_ko, koff, st, "k offsets"));
+    SM_TRY(put(&d_dp, diagpos, st, "diagonal positions"));
+    SM_TRY(put(&d_rowof, rowof, st, "row of block"));
+    g = PatternDev{d_bs, d_rp, d_col, d_vp, d_loc, d_tp, d_ns, d_ko, d_dp};
+  }
+  // waves
+  const size_t bpe = bytes_per_elem(opt.prec);
+  size_t cap = opt.workspace_cap_bytes;
+  if (cap == 0) {
+    size_t fre = 0, tot = 0;
+    SM_CUDA(cudaMemGetInfo(&fre, &tot));
+    cap = size_t(double(fre) * 0.8);
+  }
+  std::vector<int64_t> ld_of(nblk);
+  for (int j = 0; j < nblk; ++j) ld_of[j] = (nsub[j] + 63) / 64 * 64;
+  waves.clear();
+  {
+    int first = 0;
+    while (first < nblk) {
+      int64_t elems = 0;
+      int cnt = 0;
+      while (first + cnt < nblk) {
+        const int64_t e = ld_of[first + cnt] * ld_of[first + cnt];
+        if (cnt > 0 && size_t(elems + e) * bpe > cap) break;
+        if (cnt == 0 && size_t(e) * bpe > cap) {
+          set_error("one submatrix (dim %d) needs %zu bytes > workspace cap %zu", nsub[first],
+                    size_t(e) * bpe, cap);
+          return SUBMAT_ERR_OOM;
+        }
+        elems += e;
+        ++cnt;
+        if (cnt >= 65535) break;  // grid.y limit of the scaling kernel
+      }
+      Wave wv;
+      wv.first = first;
+      wv.count = cnt;
+      wv.elems = elems;
+      waves.push_back(wv);
+      first += cnt;
+    }
+  }
+  int64_t max_elems = 0;
+  max_wave = 0;
+  for (auto& wv : waves) {
+    max_elems = std::max(max_elems, wv.elems);
+    max_wave = std::max(max_wave, wv.count);
+  }
+  // per-wave maps and work lists
+  for (auto& wv : waves) {
+    std::vector<int32_t> sub(wv.count), ld(wv.count), nn(wv.count);
+    std::vector<int64_t> off(wv.count);
+    std::vector<int2> gitems;
+    std::vector<int4> sym64, full64;
+    int64_t o = 0;
+    wv.max_ld2 = 0;
+    for (int s = 0; s < wv.count; ++s) {
+      const int j = wv.first + s;
+      sub[s] = j;
+      ld[s] = int32_t(ld_of[j]);
+      nn[s] = nsub[j];
+      off[s] = o;
+      o += ld_of[j] * ld_of[j];
+      wv.max_ld2 = std::max(wv.max_ld2, ld_of[j] * ld_of[j]);
+      const int nbj = int(row_ptr[j + 1] - row_ptr[j]);
+      for (int t = 0; t < nbj; ++t) gitems.push_back(make_int2(s, t));
+      const int T = int(ld_of[j] / 64);
+      for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+          full64.push_back(make_int4(s, a, b, 0));
+          if (a <= b) sym64.push_back(make_int4(s, a, b, 0));
+        }
+    }
+    int32_t* d_sub; int32_t* d_ld; int32_t* d_n; int64_t* d_off;
+    SM_TRY(put(&d_sub, sub, st, "wave submatrices"));
+    SM_TRY(put(&d_ld, ld, st, "wave ld"));
+    SM_TRY(put(&d_n, nn, st, "wave dims"));
+    SM_TRY(put(&d_off, off, st, "wave offsets"));
+    wv.dev = WaveDev{wv.count, d_sub, d_off, d_ld, d_n};
+    SM_TRY(put(&wv.gather_items, gitems, st, "gather items"));
+    wv.n_gather = int(gitems.size());
+    SM_TRY(put(&wv.sym64, sym64, st, "tile list"));
+    wv.n_sym64 = int(sym64.size());
+    SM_TRY(put(&wv.full64, full64, st, "tile list"));
+    wv.n_full64 = int(full64.size());
+    wv.host_ld = ld;
+    wv.host_n = nn;
+    wv.host_off = off;
+  }
+  // workspace
+  ws_elems = max_elems;
+  ws_bytes = size_t(max_elems) * bpe;
+  SM_TRY(dev_alloc(&ws, ws_bytes, "workspace"));
+  if (ws) owned.push_back(ws);
+  // Newton-Schulz state (per wave slot) and per-block results
+  SM_TRY(alloc(&ns.state, max_wave, "ns state"));
+  SM_TRY(alloc(&ns.iters, max_wave, "ns iters"));
+  SM_TRY(alloc(&ns.par, max_wave, "ns parity"));
+  SM_TRY(alloc(&ns.notconv, max_wave, "ns flags"));
+  SM_TRY(alloc(&ns.res2, max_wave, "ns residual"));
+  SM_TRY(alloc(&ns.rprev, max_wave, "ns residual"));
+  SM_TRY(alloc(&ns.beta, max_wave, "ns beta"));
+  SM_TRY(alloc(&ns.gersh, max_wave, "ns gersh"));
+  SM_TRY(alloc(&ns.fro2, max_wave, "ns fro"));
+  SM_TRY(alloc(&d_flags, 4, "flags"));
+  SM_TRY(alloc(&d_active, 1, "active count"));
+  SM_TRY(alloc(&d_trpart, size_t(nblk), "trace partials"));
+  SM_TRY(alloc(&d_scalar, 8, "scalars"));
+  SM_CUDA(cudaMallocHost(&h_pinned, 64));
+  for (auto& e : ev) SM_CUDA(cudaEventCreate(&e));
+  res_iters.assign(nblk, 0);
+  res_resid.assign(nblk, 0.0);
+  res_beta.assign(nblk, 0.0);
+  res_notconv.assign(nblk, 0);
+  SM_CUDA(cudaStreamSynchronize(st));
+  return SUBMAT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sign evaluation
+// ---------------------------------------------------------------------------
+
+submat_status Plan::read_flags(cudaStream_t st, int* out) {
+  SM_CUDA(cudaMemcpyAsync(h_pinned, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaStreamSynchronize(st));
+  *out = reinterpret_cast<int*>(h_pinned)[0];
+  return SUBMAT_OK;
+}
+
+submat_status Plan::gather_wave(Wave& wv, const double* K, double mu, double* A, cudaStream_t st) {
+  SM_CUDA(cudaMemsetAsync(ns.gersh, 0, sizeof(unsigned long long) * wv.count, st));
+  SM_CUDA(cudaMemsetAsync(ns.fro2, 0, sizeof(double) * wv.count, st));
+  SM_CUDA(launch_gather(g, wv.dev, wv.gather_items, wv.n_gather, nb_max, K, mu, A, ns, d_flags, st));
+  int fl = 0;
+  SM_TRY(read_flags(st, &fl));
+  if (fl & FLAG_NONFINITE) {
+    set_error("K holds a NaN or Inf value (in the submatrices of wave starting at block %d)",
+              wv.first);
+    return SUBMAT_ERR_NONFINITE;
+  }
+  SM_CUDA(launch_beta(wv.dev, ns, opt.beta_mode, st));
+  return SUBMAT_OK;
+}
+
+submat_status Plan::collect_wave(const Wave& wv, cudaStream_t st) {
+  std::vector<int> it(wv.count), nc(wv.count);
+  std::vector<double> rp(wv.count), be(wv.count);
+  SM_CUDA(cudaMemcpyAsync(it.data(), ns.iters, sizeof(int) * wv.count, cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaMemcpyAsync(nc.data(), ns.notconv, sizeof(int) * wv.count, cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaMemcpyAsync(rp.data(), ns.rprev, sizeof(double) * wv.count, cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaMemcpyAsync(be.data(), ns.beta, sizeof(double) * wv.count, cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaStreamSynchronize(st));
+  for (int s = 0; s < wv.count; ++s) {
+    const int j = wv.first + s;
+    res_iters[j] = it[s];
+    res_notconv[j] = nc[s];
+    res_resid[j] = rp[s] > 1e299 ? 0.0 : rp[s];
+    res_beta[j] = be[s];
+  }
+  return SUBMAT_OK;
+}
+
+// Newton-Schulz X <- 1/2 X (3 I - X^2) (Section II-B) on one wave, in T
+// (double or float) with the SIMT GEMM.  X_0 is in buf[0]; on return
+// ns.par[s] names the buffer that holds sign(a_s).
+template <typename T, typename Args>
+submat_status Plan::ns_simt(const Wave& wv, T* buf0, T* buf1, T* Y, double tol, double floor_thr,
+                            cudaStream_t st, cudaError_t (*gemm)(const Args&, cudaStream_t)) {
+  T* bufs[2] = {buf0, buf1};
+  int cur = 0;
+  for (int k = 0; k < opt.max_iter; ++k) {
+    Args a1{};
+    a1.w = wv.dev; a1.items = wv.sym64; a1.nitems = wv.n_sym64;
+    a1.A = bufs[cur]; a1.B = bufs[cur]; a1.C0 = nullptr; a1.C = Y;
+    a1.alpha = 1.0; a1.beta = 0.0; a1.sym = 1; a1.res2 = ns.res2;
+    a1.state = ns.state; a1.skip_state = ST_DONE;
+    SM_CUDA(gemm(a1, st));
+    SM_CUDA(launch_ns_update(wv.dev, ns, tol, floor_thr, opt.max_iter, d_flags, st));
+    Args a2 = a1;
+    a2.B = Y; a2.C0 = bufs[cur]; a2.C = bufs[cur ^ 1];
+    a2.alpha = -0.5; a2.beta = 1.5; a2.res2 = nullptr;
+    SM_CUDA(gemm(a2, st));
+    SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
+    SM_CUDA(launch_ns_post(wv.dev, ns, cur ^ 1, d_active, st));
+    SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SM_CUDA(cudaStreamSynchronize(st));
+    cur ^= 1;
+    if (reinterpret_cast<int*>(h_pinned)[0] == 0) break;
+  }
+  return SUBMAT_OK;
+}
+
+submat_status Plan::sign_fp64(const double* K, double mu, double* D, cudaStream_t st) {
+  double* B0 = static_cast<double*>(ws);
+  double* B1 = B0 + ws_elems;
+  double* Y = B1 + ws_elems;
+  for (auto& wv : waves) {
+    SM_CUDA(cudaEventRecord(ev[0], st));
+    SM_TRY(gather_wave(wv, K, mu, B0, st));
+    SM_CUDA(launch_scale_f64(wv.dev, B0, B0, ns.beta, wv.max_ld2, st));
+    SM_CUDA(cudaEventRecord(ev[1], st));
+    SM_TRY((ns_simt<double, GemmF64Args>(wv, B0, B1, Y, tol_eff, 1e-9, st, launch_gemm_f64)));
+    SM_CUDA(cudaEventRecord(ev[2], st));
+    SM_CUDA(launch_scatter_f64(g, wv.dev, ns, B0, B1, D, d_trpart, nb_max, st));
+    SM_CUDA(cudaEventRecord(ev[3], st));
+    SM_TRY(collect_wave(wv, st));
+    SM_TRY(add_phase_times());
+  }
+  return SUBMAT_OK;
+}
+
+submat_status Plan::sign_fp32(const double* K, double mu, double* D, cudaStream_t st) {
+  double* A = static_cast<double*>(ws);
+  float* B0 = reinterpret_cast<float*>(A + ws_elems);
+  float* B1 = B0 + ws_elems;
+  float* Y = B1 + ws_elems;
+  for (auto& wv : waves) {
+    SM_CUDA(cudaEventRecord(ev[0], st));
+    SM_TRY(gather_wave(wv, K, mu, A, st));
+    SM_CUDA(launch_scale_f32(wv.dev, A, B0, ns.beta, wv.max_ld2, st));
+    SM_CUDA(cudaEventRecord(ev[1], st));
+    SM_TRY((ns_simt<float, GemmF32Args>(wv, B0, B1, Y, tol_eff, 1e-4, st, launch_gemm_f32)));
+    SM_CUDA(cudaEventRecord(ev[2], st));
+    SM_CUDA(launch_scatter_f32(g, wv.dev, ns, B0, B1, D, d_trpart, nb_max, st));
+    SM_CUDA(cudaEventRecord(ev[3], st));
+    SM_TRY(collect_wave(wv, st));
+    SM_TRY(add_phase_times());
+  }
+  return SUBMAT_OK;
+}
+
+submat_status Plan::add_phase_times() {
+  float t01 = 0, t12 = 0, t23 = 0;
+  SM_CUDA(cudaEventSynchronize(ev[3]));
+  SM_CUDA(cudaEventElapsedTime(&t01, ev[0], ev[1]));
+  SM_CUDA(cudaEventElapsedTime(&t12, ev[1], ev[2]));
+  SM_CUDA(cudaEventElapsedTime(&t23, ev[2], ev[3]));
+  stats.ms_gather += t01;
+  stats.ms_ns += t12;
+  stats.ms_scatter += t23;
+  return SUBMAT_OK;
+}
+
+void Plan::reset_stats() {
+  std::memset(&stats, 0, sizeof(stats));
+  stats.nsub = nblk;
+  stats.n_min = n_min;
+  stats.n_max = n_max;
+  stats.waves = int(waves.size());
+  stats.sum_n2 = sum_n2;
+  stats.sum_n3 = sum_n3;
+  stats.workspace_bytes = ws_bytes;
+}
+
+void Plan::finish_stats() {
+  int imin = INT32_MAX, imax = 0, nc = 0;
+  double flops = 0.0, rmax = 0.0;
+  for (int j = 0; j < nblk; ++j) {
+    imin = std::min(imin, res_iters[j]);
+    imax = std::max(imax, res_iters[j]);
+    nc += res_notconv[j];
+    flops += 4.0 * double(nsub[j]) * nsub[j] * nsub[j] * res_iters[j];
+    rmax = std::max(rmax, res_resid[j]);
+  }
+  stats.iters_min = imin == INT32_MAX ? 0 : imin;
+  stats.iters_max = imax;
+  stats.not_converged = nc;
+  stats.flops_ns = flops;
+  stats.max_resid = rmax;
+}
+
+submat_status Plan::sign(const double* K, double mu, double* D, cudaStream_t st) {
+  if (!K || !D) { set_error("K_vals and D_vals must be device pointers"); return SUBMAT_ERR_INVALID_ARG; }
+  reset_stats();
+  SM_CUDA(cudaMemsetAsync(d_flags, 0, 4 * sizeof(int), st));
+  double* Dout = D;
+  if (opt.symmetrize) {
+    if (!d_symtmp) SM_TRY(alloc(&d_symtmp, size_t(nvals), "symmetrize buffer"));
+    Dout = d_symtmp;
+  }
+  switch (opt.prec) {
+    case SUBMAT_FP64: SM_TRY(sign_fp64(K, mu, Dout, st)); break;
+    case SUBMAT_FP32: SM_TRY(sign_fp32(K, mu, Dout, st)); break;
+    case SUBMAT_MIXED_BF16_REFINE: SM_TRY(sign_mixed(K, mu, Dout, st)); break;
+    default: set_error("unknown precision %d", opt.prec); return SUBMAT_ERR_INVALID_ARG;
+  }
+  if (opt.symmetrize) SM_CUDA(launch_symmetrize_impl(g, nnzb, d_symtmp, D, d_rowof, st));
+  SM_CUDA(cudaStreamSynchronize(st));
+  finish_stats();
+  int fl = 0;
+  SM_TRY(read_flags(st, &fl));
+  if (fl & FLAG_TIMEOUT) { set_error("a bounded device wait timed out"); return SUBMAT_ERR_TIMEOUT; }
+  if (stats.not_converged > 0) {
+    set_error("%d submatrices did not converge within %d iterations (D written)",
+              stats.not_converged, opt.max_iter);
+    return SUBMAT_ERR_NOT_CONVERGED;
+  }
+  return SUBMAT_OK;
+}
+
+submat_status Plan::trace(const double* D, double* tr, cudaStream_t st) {
+  if (!D || !tr) { set_error("null argument"); return SUBMAT_ERR_INVALID_ARG; }
+  SM_CUDA(launch_trace(g, nblk, D, d_trpart, d_scalar, st));
+  SM_CUDA(cudaMemcpyAsync(h_pinned, d_scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaStreamSynchronize(st));
+  *tr = reinterpret_cast<double*>(h_pinned)[0];
+  return SUBMAT_OK;
+}
+
+}  // namespace submat
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+using submat::Plan;
+
+struct submat_plan {
+  Plan impl;
+};
+
+#define ABI_GUARD(body)                                                   \
+  try {                                                                   \
+    body                                                                  \
+  } catch (const std::bad_alloc&) {                                       \
+    submat::set_error("host allocation failed");                          \
+    return SUBMAT_ERR_OOM;                                                \
+  } catch (...) {                                                         \
+    submat::set_error("unexpected host exception");                       \
+    return SUBMAT_ERR_INVALID_ARG;                                        \
+  }
+
+extern "C" {
+
+void submat_options_default(submat_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->prec = SUBMAT_FP64;
+}
+
+submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int64_t* row_ptr,
+                                 const int32_t* col_idx, const submat_options* opt, void* stream,
+                                 submat_plan** out) {
+  ABI_GUARD({
+    submat::clear_error();
+    if (!out) { submat::set_error("out is NULL"); return SUBMAT_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (nblk < 1 || !block_sizes || !row_ptr || !col_idx) {
+      submat::set_error("nblk must be >= 1 and the pattern arrays non-NULL");
+      return SUBMAT_ERR_INVALID_ARG;
+    }
+    submat_options o;
+    submat_options_default(&o);
+    if (opt) o = *opt;
+    if (o.prec < 0 || o.prec > 2) { submat::set_error("bad precision %d", o.prec); return SUBMAT_ERR_INVALID_ARG; }
+    if (o.max_iter < 0 || o.tol < 0.0 || o.refine_rounds < 0) {
+      submat::set_error("negative max_iter, tol or refine_rounds");
+      return SUBMAT_ERR_INVALID_ARG;
+    }
+    for (int r : o.reserved)
+      if (r != 0) { submat::set_error("reserved option fields must be zero"); return SUBMAT_ERR_INVALID_ARG; }
+    if (o.max_iter == 0) o.max_iter = 100;
+    if (o.refine_rounds == 0) o.refine_rounds = 2;
+    submat_status s = submat::validate_pattern_public(nblk, block_sizes, row_ptr, col_idx);
+    if (s != SUBMAT_OK) return s;
+    std::unique_ptr<submat_plan> p(new submat_plan());
+    p->impl.tol_eff = o.tol > 0 ? o.tol : (o.prec == SUBMAT_FP64 ? 1e-14 : (o.prec == SUBMAT_FP32 ? 1e-6 : 3e-3));
+    s = p->impl.build(nblk, block_sizes, row_ptr, col_idx, &o, static_cast<cudaStream_t>(stream));
+    if (s != SUBMAT_OK) return s;
+    *out = p.release();
+    return SUBMAT_OK;
+  })
+}
+
+submat_status submat_plan_destroy(submat_plan* plan) {
+  ABI_GUARD({
+    delete plan;
+    return SUBMAT_OK;
+  })
+}
+
+submat_status submat_sign(submat_plan* plan, const double* K_vals, double mu, double* D_vals,
+                          void* stream) {
+  ABI_GUARD({
+    submat::clear_error();
+    if (!plan) { submat::set_error("plan is NULL"); return SUBMAT_ERR_INVALID_ARG; }
+    if (!std::isfinite(mu)) { submat::set_error("mu is not finite"); return SUBMAT_ERR_INVALID_ARG; }
+    return plan->impl.sign(K_vals, mu, D_vals, static_cast<cudaStream_t>(stream));
+  })
+}
+
+submat_status submat_sign_host(submat_plan* plan, const double* K_host, double mu, double* D_host,
+                               void* stream) {
+  ABI_GUARD({
+    submat::clear_error();
+    if (!plan || !K_host || !D_host) { submat::set_error("null argument"); return SUBMAT_ERR_INVALID_ARG; }
+    if (!std::isfinite(mu)) { submat::set_error("mu is not finite"); return SUBMAT_ERR_INVALID_ARG; }
+    return plan->impl.sign_host(K_host, mu, D_host, static_cast<cudaStream_t>(stream));
+  })
+}
+
+submat_status submat_trace(submat_plan* plan, const double* D_vals, double* tr, void* stream) {
+  ABI_GUARD({
+    submat::clear_error();
+    if (!plan) { submat::set_error("plan is NULL"); return SUBMAT_ERR_INVALID_ARG; }
+    return plan->impl.trace(D_vals, tr, static_cast<cudaStream_t>(stream));
+  })
+}
+
+submat_status submat_mu_search(submat_plan* plan, const double* K_vals, double n_el, double mu0,
+                               double tol, int max_steps, double* mu_out, double* D_vals,
+                               void* stream) {
+  ABI_GUARD({
+    submat::clear_error();
+    if (!plan || !mu_out || !K_vals || !D_vals || max_steps < 1 || !(tol > 0) ||
+        !std::isfinite(n_el) || !std::isfinite(mu0)) {
+      submat::set_error("bad argument to submat_mu_search");
+      return SUBMAT_ERR_INVALID_ARG;
+    }
+    return plan->impl.mu_search(K_vals, n_el, mu0, tol, max_steps, mu_out, D_vals,
+                                static_cast<cudaStream_t>(stream));
+  })
+}
+
+submat_status submat_sign_backward(submat_plan* plan, const double* K_vals, double mu,
+                                   const double* Dbar_vals, double* Kbar_vals, double* dN_dmu,
+                                   void* stream) {
+  ABI_GUARD({
+    submat::clear_error();
+    if (!plan || !K_vals || !Dbar_vals || !Kbar_vals || !std::isfinite(mu)) {
+      submat::set_error("bad argument to submat_sign_backward");
+      return SUBMAT_ERR_INVALID_ARG;
+    }
+    return plan->impl.backward(K_vals, mu, Dbar_vals, Kbar_vals, dN_dmu,
+                               static_cast<cudaStream_t>(stream));
+  })
+}
+
+int64_t submat_plan_value_count(const submat_plan* plan) { return plan ? plan->impl.nvals : -1; }
+
+submat_status submat_get_stats(const submat_plan* plan, submat_stats* out) {
+  if (!plan || !out) { submat::set_error("null argument"); return SUBMAT_ERR_INVALID_ARG; }
+  *out = plan->impl.stats;
+  return SUBMAT_OK;
+}
+
+submat_status submat_get_sub_stats(const submat_plan* plan, int32_t* dims, int32_t* iters,
+                                   double* resid, double* beta) {
+  if (!plan) { submat::set_error("plan is NULL"); return SUBMAT_ERR_INVALID_ARG; }
+  const Plan& p = plan->impl;
+  for (int j = 0; j < p.nblk; ++j) {
+    if (dims) dims[j] = p.nsub[j];
+    if (iters) iters[j] = p.res_iters[j];
+    if (resid) resid[j] = p.res_resid[j];
+    if (beta) beta[j] = p.res_beta[j];
+  }
+  return SUBMAT_OK;
+}
+
+const char* submat_last_error(void) { return submat::last_error(); }
+
+}  // extern "C"

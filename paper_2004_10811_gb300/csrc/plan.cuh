@@ -1,0 +1,106 @@
+// The plan object behind the opaque submat_plan handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "common.cuh"
+
+namespace submat {
+
+submat_status dev_alloc(void** p, size_t bytes, const char* what);
+submat_status validate_pattern_public(int nblk, const int32_t* bs, const int64_t* rp,
+                                      const int32_t* ci);
+const char* last_error();
+size_t mixed_bytes_per_elem();
+
+struct Wave {
+  int first = 0;           // first global block column of the wave
+  int count = 0;           // submatrices in the wave
+  int64_t elems = 0;       // sum of ld^2
+  int64_t max_ld2 = 0;
+  WaveDev dev{};
+  int2* gather_items = nullptr;  // (s, t) for every local block row
+  int n_gather = 0;
+  int4* sym64 = nullptr;   // 64x64 tiles with ti <= tj
+  int n_sym64 = 0;
+  int4* full64 = nullptr;  // all 64x64 tiles
+  int n_full64 = 0;
+  std::vector<int32_t> host_ld, host_n;
+  std::vector<int64_t> host_off;
+  // tensor-core work (filled by the mixed path on first use)
+  void* tc = nullptr;
+};
+
+struct Plan {
+  ~Plan();
+
+  // pattern (host)
+  int nblk = 0;
+  int64_t nnzb = 0, nvals = 0;
+  submat_options opt{};
+  double tol_eff = 1e-14;
+  std::vector<int32_t> bs, col, locoff, tpos, nsub, koff, diagpos;
+  std::vector<int64_t> row_ptr, valptr, rowof;
+  int nb_max = 0, n_max = 0, n_min = 0;
+  double sum_n2 = 0, sum_n3 = 0;
+
+  // device
+  PatternDev g{};
+  int64_t* d_rowof = nullptr;
+  std::vector<Wave> waves;
+  int max_wave = 0;
+  void* ws = nullptr;
+  int64_t ws_elems = 0;
+  size_t ws_bytes = 0;
+  NsStateDev ns{};
+  int* d_flags = nullptr;
+  int* d_active = nullptr;
+  double* d_trpart = nullptr;
+  double* d_scalar = nullptr;
+  double* d_symtmp = nullptr;
+  double* d_hostK = nullptr;   // staging for submat_sign_host
+  double* d_hostD = nullptr;
+  void* h_pinned = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<void*> owned;
+  void* mixed = nullptr;       // mixed-path state (mixed.cu)
+
+  // results of the last evaluation (per global block column)
+  std::vector<int> res_iters, res_notconv;
+  std::vector<double> res_resid, res_beta;
+  submat_stats stats{};
+
+  template <typename T>
+  submat_status alloc(T** p, size_t count, const char* what);
+  template <typename T>
+  submat_status put(T** p, const std::vector<T>& v, cudaStream_t st, const char* what);
+
+  submat_status build(int nblk, const int32_t* bs, const int64_t* rp, const int32_t* ci,
+                      const submat_options* o, cudaStream_t st);
+  submat_status sign(const double* K, double mu, double* D, cudaStream_t st);
+  submat_status sign_host(const double* K, double mu, double* D, cudaStream_t st);
+  submat_status trace(const double* D, double* tr, cudaStream_t st);
+  submat_status mu_search(const double* K, double n_el, double mu0, double tol, int max_steps,
+                          double* mu_out, double* D, cudaStream_t st);
+  submat_status backward(const double* K, double mu, const double* Dbar, double* Kbar,
+                         double* dN_dmu, cudaStream_t st);
+
+  // internals
+  submat_status read_flags(cudaStream_t st, int* out);
+  submat_status gather_wave(Wave& wv, const double* K, double mu, double* A, cudaStream_t st);
+  submat_status collect_wave(const Wave& wv, cudaStream_t st);
+  submat_status add_phase_times();
+  void reset_stats();
+  void finish_stats();
+  submat_status sign_fp64(const double* K, double mu, double* D, cudaStream_t st);
+  submat_status sign_fp32(const double* K, double mu, double* D, cudaStream_t st);
+  submat_status sign_mixed(const double* K, double mu, double* D, cudaStream_t st);
+  template <typename T, typename Args>
+  submat_status ns_simt(const Wave& wv, T* buf0, T* buf1, T* Y, double tol, double floor_thr,
+                        cudaStream_t st, cudaError_t (*gemm)(const Args&, cudaStream_t));
+};
+
+}  // namespace submat
