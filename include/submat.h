@@ -68,7 +68,8 @@ typedef struct {
   int prec;                    /* submat_precision */
   double tol;                  /* stop when ||X^2 - I||_F <= sqrt(n_j) * tol, then one more
                                   iteration (Section VI-A: involution as stopping test);
-                                  0 selects 1e-14 for FP64, 1e-6 for FP32, 3e-3 for BF16 */
+                                  0 selects 1e-14 for FP64, 1e-6 for FP32, 2e-5 for the
+                                  BF16x3 stage of the mixed path */
   int max_iter;                /* Newton-Schulz iteration cap; 0 selects 100 */
   int beta_mode;               /* X_0 = a / beta.  0: beta = min(max row abs-sum, ||a||_F)
                                   (a guaranteed bound on the spectral radius);

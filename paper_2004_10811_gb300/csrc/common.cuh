@@ -109,6 +109,7 @@ struct GemmF64Args {
   const double* C0;
   double* C;
   double alpha, beta;
+  double diag;       // added to C on the diagonal of the n x n block (C += diag * I_n)
   int sym;
   double* res2;      // optional: accumulate ||C - I_n||_F^2 per submatrix
   const int* state;  // optional: skip submatrices with state == skip_state
@@ -126,6 +127,7 @@ struct GemmF32Args {
   const float* C0;
   float* C;
   double alpha, beta;
+  double diag;
   int sym;
   double* res2;
   const int* state;

@@ -1,0 +1,137 @@
+// Test hooks (include/submat_debug.h): one kernel in isolation.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "plan.cuh"
+#include "submat_debug.h"
+#include "tc_gemm.cuh"
+
+namespace submat {
+
+long long timeout_cycles_for(double seconds) {
+  int dev = 0, khz = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  if (khz <= 0) khz = 2000000;
+  if (!(seconds > 0)) seconds = 2.0;
+  return static_cast<long long>(seconds * double(khz) * 1000.0);
+}
+
+int num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+}  // namespace submat
+
+namespace {
+
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  submat_status put(T** d, const void* src, size_t bytes, cudaStream_t st) {
+    void* q = nullptr;
+    submat_status s = submat::dev_alloc(&q, bytes, "debug scratch");
+    if (s != SUBMAT_OK) return s;
+    ptrs.push_back(q);
+    *d = static_cast<T*>(q);
+    if (src) SM_CUDA(cudaMemcpyAsync(q, src, bytes, cudaMemcpyHostToDevice, st));
+    return SUBMAT_OK;
+  }
+};
+
+}  // namespace
+
+extern "C" submat_status submat_debug_tc_gemm(int count, int ld, int n, const void* A_hi,
+                                              const void* A_lo, const void* B_hi, const void* B_lo,
+                                              int split, int sym, float* C, double* res2,
+                                              int skip_arrive, double timeout_s, void* stream) {
+  using namespace submat;
+  clear_error();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (count < 1 || count > (1 << 22) || ld < 64 || ld % 64 || ld > 8192 || n < 0 || n > ld ||
+      !A_hi || !B_hi || !C || (split && (!A_lo || !B_lo))) {
+    set_error("bad argument to submat_debug_tc_gemm");
+    return SUBMAT_ERR_INVALID_ARG;
+  }
+  Scratch sc;
+  std::vector<int64_t> off(count);
+  std::vector<int32_t> lds(count, ld), ns(count, n);
+  for (int s = 0; s < count; ++s) off[s] = int64_t(s) * ld * ld;
+  std::vector<int4> items;
+  const int T = (ld + 127) / 128;
+  for (int s = 0; s < count; ++s)
+    for (int a = 0; a < T; ++a)
+      for (int b = 0; b < T; ++b)
+        if (!sym || a <= b) items.push_back(make_int4(s, a, b, 0 | (s << 8)));
+  CUtensorMap maps[4];
+  std::memset(maps, 0, sizeof(maps));
+  const void* srcs[4] = {A_hi, split ? A_lo : A_hi, B_hi, split ? B_lo : B_hi};
+  for (int m = 0; m < 4; ++m)
+    if (make_bucket_map(&maps[m], srcs[m], ld, count) != 0) {
+      set_error("cuTensorMapEncodeTiled failed (map %d)", m);
+      return SUBMAT_ERR_CUDA;
+    }
+  int64_t* d_off; int32_t* d_ld; int32_t* d_n; int4* d_items; CUtensorMap* d_maps; int* d_flags;
+  SM_TRY(sc.put(&d_off, off.data(), off.size() * 8, st));
+  SM_TRY(sc.put(&d_ld, lds.data(), lds.size() * 4, st));
+  SM_TRY(sc.put(&d_n, ns.data(), ns.size() * 4, st));
+  SM_TRY(sc.put(&d_items, items.data(), items.size() * sizeof(int4), st));
+  SM_TRY(sc.put(&d_maps, maps, sizeof(maps), st));
+  SM_TRY(sc.put(&d_flags, nullptr, 16, st));
+  SM_CUDA(cudaMemsetAsync(d_flags, 0, 16, st));
+  if (res2) SM_CUDA(cudaMemsetAsync(res2, 0, sizeof(double) * count, st));
+
+  TcGemmParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.items = d_items;
+  p.nitems = int(items.size());
+  p.maps = d_maps;
+  p.nbucket = 1;
+  p.nmaps = 4;
+  p.na = split ? 2 : 1;
+  p.nb = split ? 2 : 1;
+  p.a_set[0] = 0; p.a_set[1] = 1;
+  p.b_set[0] = 2; p.b_set[1] = 3;
+  if (split) {
+    p.nprod = 3;
+    const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
+    for (int i = 0; i < 3; ++i) { p.prod_a[i] = pa[i]; p.prod_b[i] = pb[i]; p.prod_acc[i] = 0; p.prod_first[i] = i == 0; }
+  } else {
+    p.nprod = 1;
+    p.prod_a[0] = 0; p.prod_b[0] = 0; p.prod_acc[0] = 0; p.prod_first[0] = 1;
+  }
+  p.nacc = 1;
+  p.nstage = tc_pick_stages(p.na, p.nb);
+  p.tmem_cols = 256;
+  p.off = d_off; p.ld = d_ld; p.n = d_n;
+  p.state = nullptr;
+  p.skip_state = -1;
+  p.alpha = 1.0f; p.beta = 0.0f;
+  p.sym = sym;
+  p.out_f32 = C;
+  p.res2 = res2;
+  p.flags = d_flags;
+  p.timeout_cycles = timeout_cycles_for(timeout_s);
+  p.test_skip_arrive = skip_arrive;
+  // the timeout hook needs several tiles per CTA, so it runs on one CTA
+  const int grid = skip_arrive ? 1 : std::min<int>(p.nitems, num_sms());
+  SM_CUDA(launch_tc_gemm(p, grid, st));
+  int fl = 0;
+  SM_CUDA(cudaMemcpyAsync(&fl, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaStreamSynchronize(st));
+  if (fl & FLAG_TIMEOUT) {
+    set_error("a bounded wait in the tensor-core GEMM expired");
+    return SUBMAT_ERR_TIMEOUT;
+  }
+  return SUBMAT_OK;
+}

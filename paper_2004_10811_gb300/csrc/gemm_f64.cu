@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(Args a) {
     for (int j = 0; j < 4; ++j) {
       T x = T(a.alpha) * acc[i][j];
       if (C0b) x = fma(T(a.beta), zc[j], x);
+      if (a.diag != 0.0 && r == c0 + j && r < n) x += T(a.diag);
       v[i][j] = x;
       if (a.res2) {
         const int c = c0 + j;

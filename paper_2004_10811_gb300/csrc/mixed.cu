@@ -1,14 +1,483 @@
-// Mixed-precision path and adjoint (filled in by the tensor-core kernels).
+// Mixed-precision path: BF16 tensor-core Newton-Schulz, then an FP64-anchored
+// correction of the iterate (the paper evaluates sign by FP64
+// eigendecomposition, Section IV-F, and reports low-precision GPU iterations,
+// Section VI-A; this path combines both).
+//
+// Why a correction is needed.  Newton-Schulz never looks at a_j after X_0, and
+// every involution is a fixed point, so rounding errors that anticommute with
+// sign(a) survive all later iterations at full size.  BF16 products leave such
+// errors of order 1e-3 (1e-5 with the three-term split hi*hi + hi*lo + lo*hi).
+// With S~ = S + F, F = F_c + F_a split into the parts that commute /
+// anticommute with S = sign(a):
+//   I - S~^2 = -2 S F_c + O(F^2)              =>  F_c = -1/2 S~ (I - S~^2)
+//   [S~, a] - [F_c, a] = [F_a, a] = (|a| F_a + F_a |a|) S
+// so F_a solves the Lyapunov equation |a| F_a + F_a |a| = C with
+// C = ([S~, a] - [F_c, a]) S~ and |a| ~ H = (S~ a + a S~) / 2 (SPD).  Only
+// I - S~^2 and S~ a must be accurate to ~1e-10 (FP64 products); everything
+// else is a small correction computed with BF16x3 tensor-core products, the
+// Lyapunov equation by conjugate gradients.  One round takes the error from
+// delta to O(delta^2 |a|/gap); from the BF16x3 iterate this is ~1e-10.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "plan.cuh"
+#include "tc_gemm.cuh"
 
 namespace submat {
 
-size_t mixed_bytes_per_elem() { return 3 * 8; }
+long long timeout_cycles_for(double seconds);
+int num_sms();
 
-submat_status Plan::sign_mixed(const double*, double, double*, cudaStream_t) {
-  set_error("mixed precision path not built yet");
-  return SUBMAT_ERR_UNSUPPORTED;
+// bytes of workspace per dense element (see MixedBufs)
+size_t mixed_bytes_per_elem() { return 8 + 8 + 4 + 8 + 8 + 4 + 4 + 5 * 4; }
+
+namespace {
+
+enum MapSet { MS_XH0, MS_XL0, MS_XH1, MS_XL1, MS_YH, MS_YL, MS_AH, MS_AL, MS_HH, MS_HL, MS_COUNT };
+
+struct MixedBufs {
+  double* A;               // a_j (FP64)
+  __nv_bfloat16* X[2][2];  // [parity][hi/lo] Newton-Schulz iterate
+  __nv_bfloat16* Y[2];     // X^2, later reused for other split operands
+  double* S;               // FP64 iterate for the correction
+  double* T;               // FP64 residual products (I - S^2, then S a)
+  __nv_bfloat16* Ah[2];    // split of a
+  __nv_bfloat16* Hh[2];    // split of H
+  float* Fc;               // commuting correction
+  float* cx;               // CG solution
+  float* cr;               // CG residual
+  float* cp;               // CG direction
+  float* cw;               // H * direction
+};
+
+MixedBufs carve(void* ws, int64_t E) {
+  MixedBufs b;
+  char* p = static_cast<char*>(ws);
+  auto take = [&](size_t bytes_per) { char* q = p; p += size_t(E) * bytes_per; return q; };
+  b.A = reinterpret_cast<double*>(take(8));
+  for (int i = 0; i < 2; ++i)
+    for (int k = 0; k < 2; ++k) b.X[i][k] = reinterpret_cast<__nv_bfloat16*>(take(2));
+  for (int k = 0; k < 2; ++k) b.Y[k] = reinterpret_cast<__nv_bfloat16*>(take(2));
+  b.S = reinterpret_cast<double*>(take(8));
+  b.T = reinterpret_cast<double*>(take(8));
+  for (int k = 0; k < 2; ++k) b.Ah[k] = reinterpret_cast<__nv_bfloat16*>(take(2));
+  for (int k = 0; k < 2; ++k) b.Hh[k] = reinterpret_cast<__nv_bfloat16*>(take(2));
+  b.Fc = reinterpret_cast<float*>(take(4));
+  b.cx = reinterpret_cast<float*>(take(4));
+  b.cr = reinterpret_cast<float*>(take(4));
+  b.cp = reinterpret_cast<float*>(take(4));
+  b.cw = reinterpret_cast<float*>(take(4));
+  return b;
 }
+
+__device__ __forceinline__ void split2(double v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
+  const __nv_bfloat16 h = __double2bfloat16(v);
+  hi[i] = h;
+  lo[i] = __double2bfloat16(v - double(__bfloat162float(h)));
+}
+
+#define FOR_SUB_ELEMS(w)                                                                 \
+  const int s = blockIdx.y;                                                              \
+  const int ld = (w).ld[s];                                                              \
+  const int64_t total = int64_t(ld) * ld;                                                \
+  const int64_t base = (w).off[s];                                                       \
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;            \
+       e += int64_t(gridDim.x) * blockDim.x)
+
+// X_0 = a / beta as a BF16 (hi, lo) pair
+__global__ void k_scale_split(WaveDev w, const double* __restrict__ A, const double* __restrict__ beta,
+                              __nv_bfloat16* xh, __nv_bfloat16* xl) {
+  const double ib = 1.0 / beta[blockIdx.y];
+  FOR_SUB_ELEMS(w) split2(A[base + e] * ib, xh, xl, base + e);
+}
+
+// Bring every final iterate to parity 0 and widen it: S = hi + lo (FP64).
+__global__ void k_widen(WaveDev w, const int* __restrict__ par, __nv_bfloat16* x0h, __nv_bfloat16* x0l,
+                        const __nv_bfloat16* __restrict__ x1h, const __nv_bfloat16* __restrict__ x1l,
+                        double* __restrict__ S) {
+  const bool one = par[blockIdx.y] != 0;
+  FOR_SUB_ELEMS(w) {
+    const int64_t i = base + e;
+    __nv_bfloat16 h = one ? x1h[i] : x0h[i];
+    __nv_bfloat16 l = one ? x1l[i] : x0l[i];
+    if (one) { x0h[i] = h; x0l[i] = l; }
+    S[i] = double(__bfloat162float(h)) + double(__bfloat162float(l));
+  }
+}
+
+__global__ void k_split64(WaveDev w, const double* __restrict__ src, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  FOR_SUB_ELEMS(w) split2(src[base + e], hi, lo, base + e);
+}
+
+__global__ void k_split32(WaveDev w, const float* __restrict__ src, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  FOR_SUB_ELEMS(w) split2(double(src[base + e]), hi, lo, base + e);
+}
+
+// For a 32x32 tile pair (a, b), a <= b, with P = S a (FP64) and W = F_c a (FP32):
+//   M = (P - P^T) - (W - W^T)  -> BF16 split (the commutator [S, a] - [F_c, a])
+//   H = (P + P^T) / 2          -> BF16 split
+__global__ void k_comm(WaveDev w, const double* __restrict__ P, const float* __restrict__ W,
+                       __nv_bfloat16* mh, __nv_bfloat16* ml, __nv_bfloat16* hh, __nv_bfloat16* hl) {
+  __shared__ double tp[32][33];
+  __shared__ float tw[32][33];
+  const int s = blockIdx.y;
+  const int ld = w.ld[s];
+  const int64_t base = w.off[s];
+  const int T = ld / 32;
+  const int npair = T * (T + 1) / 2;
+  for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
+    int a = 0, rem = pi;
+    while (rem >= T - a) { rem -= T - a; ++a; }
+    const int b = a + rem;
+    for (int pass = 0; pass < (a == b ? 1 : 2); ++pass) {
+      const int ta = pass ? b : a, tb = pass ? a : b;  // output tile (ta, tb); partner (tb, ta)
+      __syncthreads();
+      for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+        const int64_t src = base + int64_t(tb * 32 + rr) * ld + ta * 32 + threadIdx.x;
+        tp[rr][threadIdx.x] = P[src];
+        tw[rr][threadIdx.x] = W[src];
+      }
+      __syncthreads();
+      for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+        const int64_t i = base + int64_t(ta * 32 + rr) * ld + tb * 32 + threadIdx.x;
+        const double p = P[i], pt = tp[threadIdx.x][rr];
+        const double wv = W[i], wt = tw[threadIdx.x][rr];
+        split2((p - pt) - (wv - wt), mh, ml, i);
+        split2(0.5 * (p + pt), hh, hl, i);
+      }
+    }
+  }
+}
+
+// CG step 1: TP = W + W^T in place (tile pairs), pTp_s = <P, TP>.
+__global__ void k_cg_sym(WaveDev w, float* __restrict__ W, const float* __restrict__ Pd, double* ptp) {
+  __shared__ float ta_[32][33], tb_[32][33];
+  __shared__ double red[32];
+  const int s = blockIdx.y;
+  const int ld = w.ld[s];
+  const int64_t base = w.off[s];
+  const int T = ld / 32;
+  const int npair = T * (T + 1) / 2;
+  double part = 0.0;
+  for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
+    int a = 0, rem = pi;
+    while (rem >= T - a) { rem -= T - a; ++a; }
+    const int b = a + rem;
+    __syncthreads();
+    for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+      ta_[rr][threadIdx.x] = W[base + int64_t(a * 32 + rr) * ld + b * 32 + threadIdx.x];
+      tb_[rr][threadIdx.x] = W[base + int64_t(b * 32 + rr) * ld + a * 32 + threadIdx.x];
+    }
+    __syncthreads();
+    for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+      const int64_t i1 = base + int64_t(a * 32 + rr) * ld + b * 32 + threadIdx.x;
+      const float v1 = ta_[rr][threadIdx.x] + tb_[threadIdx.x][rr];
+      W[i1] = v1;
+      part += double(Pd[i1]) * v1;
+      if (a != b) {
+        const int64_t i2 = base + int64_t(b * 32 + rr) * ld + a * 32 + threadIdx.x;
+        const float v2 = tb_[rr][threadIdx.x] + ta_[threadIdx.x][rr];
+        W[i2] = v2;
+        part += double(Pd[i2]) * v2;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  if ((threadIdx.x & 31) == 0) red[warp] = part;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double t = 0.0;
+    for (int q = 0; q < int(blockDim.x * blockDim.y) / 32; ++q) t += red[q];
+    atomicAdd(&ptp[s], t);
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < int(blockDim.x) / 32; ++q) t += red[q];
+  __syncthreads();
+  return t;
+}
+
+// CG step 2: alpha = rr / pTp; X += alpha P; R -= alpha TP; rr_new = <R, R>.
+__global__ void k_cg_update(WaveDev w, float* __restrict__ X, float* __restrict__ R,
+                            const float* __restrict__ Pd, const float* __restrict__ TP,
+                            const double* rr, const double* ptp, double* rr_new) {
+  __shared__ double red[32];
+  const double den = ptp[blockIdx.y];
+  const float alpha = (den > 0.0 && rr[blockIdx.y] > 0.0) ? float(rr[blockIdx.y] / den) : 0.0f;
+  double part = 0.0;
+  FOR_SUB_ELEMS(w) {
+    const int64_t i = base + e;
+    X[i] = fmaf(alpha, Pd[i], X[i]);
+    const float r = fmaf(-alpha, TP[i], R[i]);
+    R[i] = r;
+    part += double(r) * r;
+  }
+  const double t = block_sum(part, red);
+  if (threadIdx.x == 0) atomicAdd(&rr_new[blockIdx.y], t);
+}
+
+// CG step 3: P = R + (rr_new / rr) P, split for the next product.
+__global__ void k_cg_dir(WaveDev w, const float* __restrict__ R, float* __restrict__ Pd,
+                         const double* rr, const double* rr_new, __nv_bfloat16* ph,
+                         __nv_bfloat16* pl) {
+  const double d = rr[blockIdx.y];
+  const float beta = d > 0.0 ? float(rr_new[blockIdx.y] / d) : 0.0f;
+  FOR_SUB_ELEMS(w) {
+    const int64_t i = base + e;
+    const float p = fmaf(beta, Pd[i], R[i]);
+    Pd[i] = p;
+    split2(double(p), ph, pl, i);
+  }
+}
+
+// CG start: X = 0, R = P = C (already in R), rr = <C, C>, split P.
+__global__ void k_cg_init(WaveDev w, float* __restrict__ X, const float* __restrict__ R,
+                          float* __restrict__ Pd, double* rr, __nv_bfloat16* ph, __nv_bfloat16* pl) {
+  __shared__ double red[32];
+  double part = 0.0;
+  FOR_SUB_ELEMS(w) {
+    const int64_t i = base + e;
+    const float r = R[i];
+    X[i] = 0.0f;
+    Pd[i] = r;
+    split2(double(r), ph, pl, i);
+    part += double(r) * r;
+  }
+  const double t = block_sum(part, red);
+  if (threadIdx.x == 0) atomicAdd(&rr[blockIdx.y], t);
+}
+
+// S <- S - F_c - F_a
+__global__ void k_apply(WaveDev w, double* __restrict__ S, const float* __restrict__ Fc,
+                        const float* __restrict__ Fa) {
+  FOR_SUB_ELEMS(w) {
+    const int64_t i = base + e;
+    S[i] = S[i] - double(Fc[i]) - double(Fa[i]);
+  }
+}
+
+dim3 elem_grid(const Wave& wv) {
+  int64_t bx = (wv.max_ld2 + 256 * 8 - 1) / (256 * 8);
+  bx = std::max<int64_t>(1, std::min<int64_t>(bx, 256));
+  return dim3(unsigned(bx), unsigned(wv.count));
+}
+
+dim3 pair_grid(const Wave& wv) {
+  int64_t t = 1;
+  for (int64_t l : wv.bucket_ld) t = std::max<int64_t>(t, l / 32);
+  int64_t np = t * (t + 1) / 2;
+  return dim3(unsigned(std::min<int64_t>(np, 512)), unsigned(wv.count));
+}
+
+struct MixedState {
+  std::vector<CUtensorMap*> d_maps;  // per wave: [MS_COUNT][nbucket]
+  double* scal = nullptr;            // per-slot CG scalars: rr, ptp, rr_new (3 x max_wave)
+};
+
+}  // namespace
+
+submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream_t st) {
+  MixedBufs b = carve(ws, ws_elems);
+  auto* ms = static_cast<MixedState*>(mixed);
+  if (!ms) {
+    ms = new MixedState();
+    mixed = ms;
+    for (auto& wv : waves) {
+      const int nbk = int(wv.bucket_ld.size());
+      std::vector<CUtensorMap> maps(size_t(MS_COUNT) * nbk);
+      const void* bases[MS_COUNT] = {b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.Y[0],
+                                     b.Y[1],    b.Ah[0],   b.Ah[1],   b.Hh[0],   b.Hh[1]};
+      for (int m = 0; m < MS_COUNT; ++m)
+        for (int k = 0; k < nbk; ++k) {
+          const __nv_bfloat16* base = static_cast<const __nv_bfloat16*>(bases[m]) + wv.bucket_base[k];
+          if (make_bucket_map(&maps[size_t(m) * nbk + k], base, int(wv.bucket_ld[k]),
+                              wv.bucket_count[k]) != 0) {
+            set_error("cuTensorMapEncodeTiled failed");
+            return SUBMAT_ERR_CUDA;
+          }
+        }
+      CUtensorMap* d = nullptr;
+      SM_TRY(alloc(&d, maps.size(), "tensor maps"));
+      SM_CUDA(cudaMemcpyAsync(d, maps.data(), maps.size() * sizeof(CUtensorMap),
+                              cudaMemcpyHostToDevice, st));
+      ms->d_maps.push_back(d);
+    }
+    SM_TRY(alloc(&ms->scal, size_t(3) * max_wave, "CG scalars"));
+  }
+  const long long tmo = timeout_cycles_for(2.0);
+  const int nsm = num_sms();
+  const double floor_thr = 1e-3;
+  double* rr = ms->scal;
+  double* ptp = rr + max_wave;
+  double* rrn = ptp + max_wave;
+
+  for (size_t wi = 0; wi < waves.size(); ++wi) {
+    Wave& wv = waves[wi];
+    const int nbk = int(wv.bucket_ld.size());
+    auto tc = [&](const int4* items, int nitems, int sa0, int sa1, int sb0, int sb1, int sym,
+                  float alpha, float beta) {
+      TcGemmParams p;
+      std::memset(&p, 0, sizeof(p));
+      p.items = items;
+      p.nitems = nitems;
+      p.maps = ms->d_maps[wi];
+      p.nbucket = nbk;
+      p.nmaps = MS_COUNT * nbk;
+      p.na = 2; p.nb = 2;
+      p.a_set[0] = sa0; p.a_set[1] = sa1;
+      p.b_set[0] = sb0; p.b_set[1] = sb1;
+      p.nprod = 3;
+      const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
+      for (int i = 0; i < 3; ++i) { p.prod_a[i] = pa[i]; p.prod_b[i] = pb[i]; p.prod_acc[i] = 0; p.prod_first[i] = i == 0; }
+      p.nacc = 1;
+      p.nstage = tc_pick_stages(2, 2);
+      p.tmem_cols = 256;
+      p.off = wv.dev.off; p.ld = wv.dev.ld; p.n = wv.dev.n;
+      p.state = nullptr;
+      p.skip_state = -1;
+      p.alpha = alpha; p.beta = beta;
+      p.sym = sym;
+      p.flags = d_flags;
+      p.timeout_cycles = tmo;
+      return p;
+    };
+    auto launch = [&](const TcGemmParams& p) -> cudaError_t {
+      return launch_tc_gemm(p, std::min(p.nitems, nsm), st);
+    };
+
+    // ---- assemble and scale (Section III-A step 1) ----
+    SM_CUDA(cudaEventRecord(ev[0], st));
+    SM_TRY(gather_wave(wv, K, mu, b.A, st));
+    const dim3 eg = elem_grid(wv);
+    k_scale_split<<<eg, 256, 0, st>>>(wv.dev, b.A, ns.beta, b.X[0][0], b.X[0][1]);
+    SM_CUDA(cudaGetLastError());
+    SM_CUDA(cudaEventRecord(ev[1], st));
+
+    // ---- BF16x3 Newton-Schulz on the tensor cores ----
+    int cur = 0;
+    for (int k = 0; k < opt.max_iter; ++k) {
+      TcGemmParams g1 = tc(wv.sym128, wv.n_sym128, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
+                           cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0, 1, 1.0f, 0.0f);
+      g1.out_hi = b.Y[0]; g1.out_lo = b.Y[1];
+      g1.res2 = ns.res2;
+      g1.state = ns.state; g1.skip_state = ST_DONE;
+      SM_CUDA(launch(g1));
+      SM_CUDA(launch_ns_update(wv.dev, ns, tol_eff, floor_thr, opt.max_iter, d_flags, st));
+      TcGemmParams g2 = tc(wv.sym128, wv.n_sym128, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
+                           MS_YH, MS_YL, 1, -0.5f, 1.5f);
+      g2.c0_hi = b.X[cur][0]; g2.c0_lo = b.X[cur][1];
+      g2.out_hi = b.X[cur ^ 1][0]; g2.out_lo = b.X[cur ^ 1][1];
+      g2.state = ns.state; g2.skip_state = ST_DONE;
+      SM_CUDA(launch(g2));
+      SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
+      SM_CUDA(launch_ns_post(wv.dev, ns, cur ^ 1, d_active, st));
+      SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SM_CUDA(cudaStreamSynchronize(st));
+      cur ^= 1;
+      if (reinterpret_cast<int*>(h_pinned)[0] == 0) break;
+    }
+    SM_CUDA(cudaEventRecord(ev[2], st));
+
+    // ---- correction rounds ----
+    k_widen<<<eg, 256, 0, st>>>(wv.dev, ns.par, b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.S);
+    SM_CUDA(cudaGetLastError());
+    k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
+    SM_CUDA(cudaGetLastError());
+    const int rounds = std::max(1, opt.refine_rounds);
+    const int cg_iters = 10;
+    for (int rd = 0; rd < rounds; ++rd) {
+      if (rd > 0) {  // the operand split of S for this round
+        k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
+        SM_CUDA(cudaGetLastError());
+      }
+      // T = I - S^2 (FP64)
+      GemmF64Args f{};
+      f.w = wv.dev; f.items = wv.sym64; f.nitems = wv.n_sym64;
+      f.A = b.S; f.B = b.S; f.C0 = nullptr; f.C = b.T;
+      f.alpha = -1.0; f.beta = 0.0; f.diag = 1.0; f.sym = 1;
+      SM_CUDA(launch_gemm_f64(f, st));
+      k_split64<<<eg, 256, 0, st>>>(wv.dev, b.T, b.Y[0], b.Y[1]);
+      SM_CUDA(cudaGetLastError());
+      // F_c = -1/2 S (I - S^2)
+      TcGemmParams g = tc(wv.sym128, wv.n_sym128, MS_XH0, MS_XL0, MS_YH, MS_YL, 1, -0.5f, 0.0f);
+      g.out_f32 = b.Fc;
+      SM_CUDA(launch(g));
+      k_split32<<<eg, 256, 0, st>>>(wv.dev, b.Fc, b.Y[0], b.Y[1]);
+      SM_CUDA(cudaGetLastError());
+      // T = S a (FP64)
+      GemmF64Args f2{};
+      f2.w = wv.dev; f2.items = wv.full64; f2.nitems = wv.n_full64;
+      f2.A = b.S; f2.B = b.A; f2.C0 = nullptr; f2.C = b.T;
+      f2.alpha = 1.0; f2.beta = 0.0; f2.diag = 0.0; f2.sym = 0;
+      SM_CUDA(launch_gemm_f64(f2, st));
+      // W = F_c a
+      TcGemmParams g3 = tc(wv.full128, wv.n_full128, MS_YH, MS_YL, MS_AH, MS_AL, 0, 1.0f, 0.0f);
+      g3.out_f32 = b.cw;
+      SM_CUDA(launch(g3));
+      // M = [S, a] - [F_c, a] (split into Y), H = (S a + a S) / 2 (split)
+      k_comm<<<pair_grid(wv), dim3(32, 8), 0, st>>>(wv.dev, b.T, b.cw, b.Y[0], b.Y[1], b.Hh[0], b.Hh[1]);
+      SM_CUDA(cudaGetLastError());
+      // C = M S (symmetric to first order) -> CG residual
+      TcGemmParams g4 = tc(wv.sym128, wv.n_sym128, MS_YH, MS_YL, MS_XH0, MS_XL0, 1, 1.0f, 0.0f);
+      g4.out_f32 = b.cr;
+      SM_CUDA(launch(g4));
+      // CG on L -> H L + L H
+      SM_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * 3 * max_wave, st));
+      k_cg_init<<<eg, 256, 0, st>>>(wv.dev, b.cx, b.cr, b.cp, rr, b.Y[0], b.Y[1]);
+      SM_CUDA(cudaGetLastError());
+      for (int it = 0; it < cg_iters; ++it) {
+        TcGemmParams gh = tc(wv.full128, wv.n_full128, MS_HH, MS_HL, MS_YH, MS_YL, 0, 1.0f, 0.0f);
+        gh.out_f32 = b.cw;
+        SM_CUDA(launch(gh));
+        SM_CUDA(cudaMemsetAsync(ptp, 0, sizeof(double) * 2 * max_wave, st));  // ptp and rr_new
+        k_cg_sym<<<pair_grid(wv), dim3(32, 8), 0, st>>>(wv.dev, b.cw, b.cp, ptp);
+        SM_CUDA(cudaGetLastError());
+        k_cg_update<<<eg, 256, 0, st>>>(wv.dev, b.cx, b.cr, b.cp, b.cw, rr, ptp, rrn);
+        SM_CUDA(cudaGetLastError());
+        k_cg_dir<<<eg, 256, 0, st>>>(wv.dev, b.cr, b.cp, rr, rrn, b.Y[0], b.Y[1]);
+        SM_CUDA(cudaGetLastError());
+        SM_CUDA(cudaMemcpyAsync(rr, rrn, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
+      }
+      k_apply<<<eg, 256, 0, st>>>(wv.dev, b.S, b.Fc, b.cx);
+      SM_CUDA(cudaGetLastError());
+    }
+    stats.refine_rounds = rounds;
+    SM_CUDA(cudaEventRecord(ev[3], st));
+    // ---- extract (Section III-A step 3): S is at "parity 0" for every submatrix ----
+    SM_CUDA(cudaMemsetAsync(ns.par, 0, sizeof(int) * wv.count, st));
+    SM_CUDA(launch_scatter_f64(g, wv.dev, ns, b.S, b.S, D, d_trpart, nb_max, st));
+    SM_TRY(collect_wave(wv, st));
+    float t01 = 0, t12 = 0, t23 = 0;
+    SM_CUDA(cudaEventElapsedTime(&t01, ev[0], ev[1]));
+    SM_CUDA(cudaEventElapsedTime(&t12, ev[1], ev[2]));
+    SM_CUDA(cudaEventElapsedTime(&t23, ev[2], ev[3]));
+    stats.ms_gather += t01;
+    stats.ms_ns += t12;
+    stats.ms_refine += t23;
+    double fl = 0.0;
+    for (int s = 0; s < wv.count; ++s) {
+      const double n = double(wv.host_n[s]);
+      // per round: 2 FP64 products (4 n^3), 3 + cg_iters split products (2 n^3 each)
+      fl += rounds * (4.0 + 2.0 * (3 + cg_iters)) * n * n * n;
+    }
+    stats.flops_refine += fl;
+  }
+  return SUBMAT_OK;
+}
+
+void free_mixed(void* state) { delete static_cast<MixedState*>(state); }
 
 submat_status Plan::backward(const double*, double, const double*, double*, double*, cudaStream_t) {
   set_error("adjoint not built yet");

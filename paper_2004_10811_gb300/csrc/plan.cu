@@ -58,6 +58,7 @@ static submat_status upload(T** dst, const std::vector<T>& src, cudaStream_t st,
 }
 
 Plan::~Plan() {
+  free_mixed(mixed);
   for (void* p : owned) cudaFree(p);
   if (h_pinned) cudaFreeHost(h_pinned);
   for (auto& e : ev) if (e) cudaEventDestroy(e);
@@ -253,21 +254,40 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
     max_elems = std::max(max_elems, wv.elems);
     max_wave = std::max(max_wave, wv.count);
   }
-  // per-wave maps and work lists
+  // per-wave maps and work lists.  Dense buffers are grouped into size
+  // buckets (equal ld) laid out as [count][ld][ld], so that each bucket is one
+  // 3D tensor for the TMA loads of the tensor-core GEMM.
   for (auto& wv : waves) {
     std::vector<int32_t> sub(wv.count), ld(wv.count), nn(wv.count);
     std::vector<int64_t> off(wv.count);
     std::vector<int2> gitems;
-    std::vector<int4> sym64, full64;
+    std::vector<int4> sym64, full64, sym128, full128;
+    std::vector<int64_t> lds;
+    for (int s = 0; s < wv.count; ++s) lds.push_back(ld_of[wv.first + s]);
+    std::sort(lds.begin(), lds.end());
+    lds.erase(std::unique(lds.begin(), lds.end()), lds.end());
+    if (lds.size() > 255) { set_error("more than 255 size buckets in a wave"); return SUBMAT_ERR_UNSUPPORTED; }
+    wv.bucket_ld.assign(lds.begin(), lds.end());
+    wv.bucket_count.assign(lds.size(), 0);
+    std::vector<int> bucket_of(wv.count), slot_of(wv.count);
+    for (int s = 0; s < wv.count; ++s) {
+      const int b = int(std::lower_bound(lds.begin(), lds.end(), ld_of[wv.first + s]) - lds.begin());
+      bucket_of[s] = b;
+      slot_of[s] = wv.bucket_count[b]++;
+    }
+    wv.bucket_base.assign(lds.size(), 0);
     int64_t o = 0;
+    for (size_t b = 0; b < lds.size(); ++b) {
+      wv.bucket_base[b] = o;
+      o += int64_t(wv.bucket_count[b]) * lds[b] * lds[b];
+    }
     wv.max_ld2 = 0;
     for (int s = 0; s < wv.count; ++s) {
       const int j = wv.first + s;
       sub[s] = j;
       ld[s] = int32_t(ld_of[j]);
       nn[s] = nsub[j];
-      off[s] = o;
-      o += ld_of[j] * ld_of[j];
+      off[s] = wv.bucket_base[bucket_of[s]] + int64_t(slot_of[s]) * ld_of[j] * ld_of[j];
       wv.max_ld2 = std::max(wv.max_ld2, ld_of[j] * ld_of[j]);
       const int nbj = int(row_ptr[j + 1] - row_ptr[j]);
       for (int t = 0; t < nbj; ++t) gitems.push_back(make_int2(s, t));
@@ -276,6 +296,13 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
         for (int b = 0; b < T; ++b) {
           full64.push_back(make_int4(s, a, b, 0));
           if (a <= b) sym64.push_back(make_int4(s, a, b, 0));
+        }
+      const int T2 = int((ld_of[j] + 127) / 128);
+      const int tag = bucket_of[s] | (slot_of[s] << 8);
+      for (int a = 0; a < T2; ++a)
+        for (int b = 0; b < T2; ++b) {
+          full128.push_back(make_int4(s, a, b, tag));
+          if (a <= b) sym128.push_back(make_int4(s, a, b, tag));
         }
     }
     int32_t* d_sub; int32_t* d_ld; int32_t* d_n; int64_t* d_off;
@@ -290,6 +317,10 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
     wv.n_sym64 = int(sym64.size());
     SM_TRY(put(&wv.full64, full64, st, "tile list"));
     wv.n_full64 = int(full64.size());
+    SM_TRY(put(&wv.sym128, sym128, st, "tile list"));
+    wv.n_sym128 = int(sym128.size());
+    SM_TRY(put(&wv.full128, full128, st, "tile list"));
+    wv.n_full128 = int(full128.size());
     wv.host_ld = ld;
     wv.host_n = nn;
     wv.host_off = off;
@@ -571,7 +602,7 @@ submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int
     submat_status s = submat::validate_pattern_public(nblk, block_sizes, row_ptr, col_idx);
     if (s != SUBMAT_OK) return s;
     std::unique_ptr<submat_plan> p(new submat_plan());
-    p->impl.tol_eff = o.tol > 0 ? o.tol : (o.prec == SUBMAT_FP64 ? 1e-14 : (o.prec == SUBMAT_FP32 ? 1e-6 : 3e-3));
+    p->impl.tol_eff = o.tol > 0 ? o.tol : (o.prec == SUBMAT_FP64 ? 1e-14 : (o.prec == SUBMAT_FP32 ? 1e-6 : 2e-5));
     s = p->impl.build(nblk, block_sizes, row_ptr, col_idx, &o, static_cast<cudaStream_t>(stream));
     if (s != SUBMAT_OK) return s;
     *out = p.release();

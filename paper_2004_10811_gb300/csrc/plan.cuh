@@ -15,6 +15,7 @@ submat_status validate_pattern_public(int nblk, const int32_t* bs, const int64_t
                                       const int32_t* ci);
 const char* last_error();
 size_t mixed_bytes_per_elem();
+void free_mixed(void* state);
 
 struct Wave {
   int first = 0;           // first global block column of the wave
@@ -28,6 +29,12 @@ struct Wave {
   int n_sym64 = 0;
   int4* full64 = nullptr;  // all 64x64 tiles
   int n_full64 = 0;
+  int4* sym128 = nullptr;  // 128x128 tiles with ti <= tj: (s, ti, tj, bucket | slot << 8)
+  int n_sym128 = 0;
+  int4* full128 = nullptr;
+  int n_full128 = 0;
+  std::vector<int64_t> bucket_ld, bucket_base;  // size buckets: [count][ld][ld] each
+  std::vector<int> bucket_count;
   std::vector<int32_t> host_ld, host_n;
   std::vector<int64_t> host_off;
   // tensor-core work (filled by the mixed path on first use)

@@ -1,0 +1,520 @@
+// Grouped BF16 tensor-core GEMM for sm_103a: tcgen05.mma with TMEM
+// accumulators, operands staged by TMA (cp.async.bulk.tensor, 128B swizzle),
+// an mbarrier pipeline, and one persistent CTA per SM.
+//
+// Every work item is one 128x128 output tile (s, ti, tj) of
+//     C_s = alpha * sum_p A_{a(p)} B_{b(p)}^T + beta * C0_s
+// over the submatrix batch.  Operands are row-major n x n BF16 arrays stored
+// per size bucket as [count][ld][ld]; B is read as rows (B^T with K major),
+// which equals B for the symmetric operands of Newton-Schulz.  A product table
+// lets one launch sum several slice products into the FP32 accumulator, e.g.
+// the three-term split hi*hi + hi*lo + lo*hi that carries about 16 bits
+// through the tensor cores.
+//
+// Roles (192 threads): warp 0 issues TMA loads, warp 1 owns TMEM and one of
+// its lanes issues the MMAs, warps 2-5 drain the accumulator (one TMEM lane
+// quarter each) and write the tile -- and, for symmetric outputs, its mirror
+// through a shared-memory transpose.  Every mbarrier wait is bounded; on
+// timeout the kernel raises FLAG_TIMEOUT, drains its own copies and MMAs,
+// frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tc_gemm.cuh"
+
+namespace submat {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int TILE_BYTES = BM * BK * 2;  // one 128 x 64 BF16 operand tile
+constexpr int STG_PITCH = 33;            // staged row pitch (32-bit words)
+constexpr uint32_t IDESC = (1u << 4)            // D format: F32
+                           | (1u << 7)          // A format: BF16
+                           | (1u << 10)         // B format: BF16
+                           | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false on timeout or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > limit) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// K-major operand tile with 128-byte swizzle: rows of 128 bytes, 8-row
+// groups 1024 bytes apart; the tile base is 1024-byte aligned.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= uint64_t(1) << 16;                    // leading byte offset (unused here)
+  d |= uint64_t(1024 >> 4) << 32;            // stride byte offset: 8 rows
+  d |= uint64_t(1) << 46;                    // descriptor version
+  d |= uint64_t(2) << 61;                    // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accum));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_split(float o) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(o);
+  const __nv_bfloat16 l = __float2bfloat16_rn(o - __bfloat162float(h));
+  return uint32_t(__bfloat16_as_ushort(h)) | (uint32_t(__bfloat16_as_ushort(l)) << 16);
+}
+
+// write 32 values (one row segment) in the output format
+__device__ __forceinline__ void store_row(const TcGemmParams& p, int64_t idx, const float* o) {
+  if (p.out_f32) {
+    float4* d = reinterpret_cast<float4*>(p.out_f32 + idx);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+  } else {
+    uint32_t hw[16], lw[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const uint32_t a = pack_split(o[2 * q]), b = pack_split(o[2 * q + 1]);
+      hw[q] = (a & 0xFFFFu) | (b << 16);
+      lw[q] = (a >> 16) | (b & 0xFFFF0000u);
+    }
+    uint4* dh = reinterpret_cast<uint4*>(p.out_hi + idx);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dh[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+    if (p.out_lo) {
+      uint4* dl = reinterpret_cast<uint4*>(p.out_lo + idx);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dl[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+    }
+  }
+}
+
+// store o[q] for q in [q_lo, q_hi) only (diagonal tiles of symmetric outputs)
+__device__ __forceinline__ void store_range(const TcGemmParams& p, int64_t idx, const float* o,
+                                            int q_lo, int q_hi) {
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    if (q < q_lo || q >= q_hi) continue;
+    if (p.out_f32) {
+      p.out_f32[idx + q] = o[q];
+    } else {
+      const uint32_t w = pack_split(o[q]);
+      p.out_hi[idx + q] = __ushort_as_bfloat16(static_cast<unsigned short>(w & 0xFFFFu));
+      if (p.out_lo) p.out_lo[idx + q] = __ushort_as_bfloat16(static_cast<unsigned short>(w >> 16));
+    }
+  }
+}
+
+__device__ __forceinline__ void load_c0(const TcGemmParams& p, int64_t idx, float* c) {
+  if (p.c0_f32) {
+    const float4* s = reinterpret_cast<const float4*>(p.c0_f32 + idx);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 v = s[q];
+      c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+    }
+  } else {
+    const uint4* sh = reinterpret_cast<const uint4*>(p.c0_hi + idx);
+    const uint4* sl = p.c0_lo ? reinterpret_cast<const uint4*>(p.c0_lo + idx) : nullptr;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 h = sh[q];
+      const uint4 l = sl ? sl[q] : make_uint4(0, 0, 0, 0);
+      const uint32_t hh[4] = {h.x, h.y, h.z, h.w}, ll[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        c[8 * q + 2 * e] = __uint_as_float(hh[e] << 16) + __uint_as_float(ll[e] << 16);
+        c[8 * q + 2 * e + 1] =
+            __uint_as_float(hh[e] & 0xFFFF0000u) + __uint_as_float(ll[e] & 0xFFFF0000u);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGemmParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  const int nslot = p.na + p.nb;
+  uint8_t* tiles = smem;
+  uint32_t* stg = reinterpret_cast<uint32_t*>(tiles + size_t(p.nstage) * nslot * TILE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + BM * STG_PITCH);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + p.nstage;
+  uint64_t* tfull = empty + p.nstage;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* epi_ok = abort_flag + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < p.nstage; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], BM);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(uint32_t(p.tmem_cols)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const long long limit = p.timeout_cycles;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    for (int m = 0; m < p.nmaps; ++m)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.maps[m])) : "memory");
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t issued = 0, issued_phase = 0;  // per-stage bits
+    bool ok = true;
+    for (int it = blockIdx.x; it < p.nitems && ok; it += gridDim.x) {
+      const int4 item = p.items[it];
+      if (p.state && p.state[item.x] == p.skip_state) continue;
+      const int bucket = item.w & 0xFF, slot = item.w >> 8;
+      const int nk = p.ld[item.x] / BK;
+      const CUtensorMap* mapsb = p.maps + bucket;
+      for (int kb = 0; kb < nk; ++kb) {
+        if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, limit)) { ok = false; break; }
+        uint8_t* st = tiles + size_t(stage) * nslot * TILE_BYTES;
+        mbar_expect_tx(&full[stage], uint32_t(nslot * TILE_BYTES));
+        for (int a = 0; a < p.na; ++a)
+          tma_load_3d(st + a * TILE_BYTES, mapsb + p.a_set[a] * p.nbucket, &full[stage], kb * BK,
+                      item.y * BM, slot);
+        for (int b = 0; b < p.nb; ++b)
+          tma_load_3d(st + (p.na + b) * TILE_BYTES, mapsb + p.b_set[b] * p.nbucket, &full[stage],
+                      kb * BK, item.z * BN, slot);
+        issued |= 1u << stage;
+        issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
+        if (++stage == p.nstage) { stage = 0; phase ^= 1u; }
+      }
+    }
+    if (!ok) {
+      atomicOr(p.flags, FLAG_TIMEOUT);
+      *abort_flag = 1;
+      // let this CTA's copies in flight land before shared memory is released
+      for (int i = 0; i < p.nstage; ++i)
+        if (issued & (1u << i)) {
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&full[i], (issued_phase >> i) & 1u) && clock64() - t0 < limit) {
+          }
+        }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    int stage = 0;
+    uint32_t phase = 0;
+    int tcount = 0;
+    bool ok = true;
+    for (int it = blockIdx.x; it < p.nitems && ok; it += gridDim.x) {
+      const int4 item = p.items[it];
+      if (p.state && p.state[item.x] == p.skip_state) continue;
+      const int nk = p.ld[item.x] / BK;
+      const int ab = tcount & 1;
+      const uint32_t tph = uint32_t(tcount >> 1) & 1u;
+      if (!mbar_wait(&tempty[ab], tph ^ 1u, abort_flag, limit)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t dbase = tmem_base + uint32_t(ab * p.nacc * BN);
+      for (int kb = 0; kb < nk; ++kb) {
+        if (!mbar_wait(&full[stage], phase, abort_flag, limit)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t sb = smem_u32(tiles + size_t(stage) * nslot * TILE_BYTES);
+        for (int pr = 0; pr < p.nprod; ++pr) {
+          const uint64_t ad = sdesc(sb + uint32_t(p.prod_a[pr] * TILE_BYTES));
+          const uint64_t bd = sdesc(sb + uint32_t((p.na + p.prod_b[pr]) * TILE_BYTES));
+          const uint32_t d = dbase + uint32_t(p.prod_acc[pr] * BN);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            umma_bf16(d, ad + uint64_t(2 * k), bd + uint64_t(2 * k),
+                      (kb > 0 || k > 0 || !p.prod_first[pr]) ? 1u : 0u);
+        }
+        umma_commit(&empty[stage]);
+        if (++stage == p.nstage) { stage = 0; phase ^= 1u; }
+      }
+      if (!ok) break;
+      umma_commit(&tfull[ab]);
+      ++tcount;
+    }
+    if (!ok) {
+      atomicOr(p.flags, FLAG_TIMEOUT);
+      *abort_flag = 1;
+    }
+    // every MMA issued by this thread has completed once this commit lands
+    umma_commit(drain);
+    const long long t0 = clock64();
+    while (!mbar_try_wait(drain, 0) && clock64() - t0 < limit) {
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;  // tile row == TMEM lane
+    int tcount = 0;
+    for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
+      const int4 item = p.items[it];
+      const int s = item.x;
+      if (p.state && p.state[s] == p.skip_state) continue;
+      const int ab = tcount & 1;
+      const uint32_t tph = uint32_t(tcount >> 1) & 1u;
+      // one bounded wait, result shared, so the four warps leave together
+      if (threadIdx.x == 64) {
+        const bool got = mbar_wait(&tfull[ab], tph, abort_flag, limit);
+        if (!got) {
+          atomicOr(p.flags, FLAG_TIMEOUT);
+          *abort_flag = 1;
+        }
+        *epi_ok = got ? 1 : 0;
+      }
+      epi_bar();
+      if (!*epi_ok) break;
+      tc_fence_after();
+      float acc[BN];
+      const uint32_t tb = tmem_base + (uint32_t(quarter * 32) << 16) + uint32_t(ab * p.nacc * BN);
+#pragma unroll
+      for (int c = 0; c < BN / 32; ++c) tmem_ld32(tb + uint32_t(c * 32), acc + c * 32);
+      tmem_wait_ld();
+      for (int a = 1; a < p.nacc; ++a) {
+        float tmp[32];
+#pragma unroll
+        for (int c = 0; c < BN / 32; ++c) {
+          tmem_ld32(tb + uint32_t(a * BN + c * 32), tmp);
+          tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 32; ++q) acc[c * 32 + q] += tmp[q];
+        }
+      }
+      tc_fence_before();
+      if (!p.test_skip_arrive) mbar_arrive(&tempty[ab]);
+      ++tcount;
+
+      const int ld = p.ld[s];
+      const int n = p.n[s];
+      const int64_t base = p.off[s];
+      const int rg = item.y * BM + r;
+      // symmetric output: off-diagonal tiles are mirrored; diagonal tiles keep
+      // their upper triangle and take the strict lower one from it, so the
+      // result is exactly symmetric whatever the accumulation order
+      const bool diag_sym = p.sym && item.y == item.z;
+      const bool mirror = p.sym != 0;
+      double part = 0.0;
+#pragma unroll
+      for (int c = 0; c < BN / 32; ++c) {
+        const int cg0 = item.z * BN + c * 32;
+        float o[32];
+        const bool inside = (rg < ld) && (cg0 < ld);
+        if (inside) {
+          float c0[32];
+          const int64_t idx = base + int64_t(rg) * ld + cg0;
+          const bool has_c0 = (p.c0_f32 || p.c0_hi) && p.beta != 0.0f;
+          if (has_c0) load_c0(p, idx, c0);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            float v = p.alpha * acc[c * 32 + q];
+            if (has_c0) v = fmaf(p.beta, c0[q], v);
+            o[q] = v;
+          }
+          if (p.res2) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              const int cg = cg0 + q;
+              const double e = double(o[q]) - ((rg == cg && rg < n) ? 1.0 : 0.0);
+              part += e * e;
+            }
+          }
+          if (diag_sym) store_range(p, idx, o, r - c * 32, 32);
+          else store_row(p, idx, o);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) o[q] = 0.0f;
+        }
+        if (mirror) {
+          // transpose the 128 x 32 chunk through shared memory
+#pragma unroll
+          for (int q = 0; q < 32; ++q) stg[r * STG_PITCH + q] = __float_as_uint(o[q]);
+          epi_bar();
+          const int t = threadIdx.x - 64;
+          const int q = t >> 2, part4 = t & 3;
+          const int mrow = item.z * BN + c * 32 + q;       // row of the mirrored tile
+          const int mcol0 = item.y * BM + part4 * 32;      // its first column
+          if (mrow < ld && mcol0 < ld) {
+            float w[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) w[i] = __uint_as_float(stg[(part4 * 32 + i) * STG_PITCH + q]);
+            if (diag_sym) store_range(p, base + int64_t(mrow) * ld + mcol0, w, 0, c * 32 + q - part4 * 32);
+            else store_row(p, base + int64_t(mrow) * ld + mcol0, w);
+          }
+          epi_bar();
+        }
+      }
+      if (p.res2) {
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o2);
+        if (lane == 0 && part != 0.0) atomicAdd(&p.res2[s], (mirror && !diag_sym) ? 2.0 * part : part);
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(uint32_t(p.tmem_cols)));
+  }
+}
+
+}  // namespace
+
+int tc_smem_bytes(int na, int nb, int nstage) {
+  return 1024 + nstage * (na + nb) * TILE_BYTES + BM * STG_PITCH * 4 + (2 * nstage + 5) * 8 + 32;
+}
+
+int tc_pick_stages(int na, int nb) {
+  const int budget = 227 * 1024;
+  int st = 6;
+  while (st > 2 && tc_smem_bytes(na, nb, st) > budget) --st;
+  return st;
+}
+
+cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st) {
+  if (p.nitems <= 0) return cudaSuccess;
+  const int smem = tc_smem_bytes(p.na, p.nb, p.nstage);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_tc_gemm<<<grid, 192, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// tensor maps
+// ---------------------------------------------------------------------------
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encoder() {
+  static PFN_encodeTiled fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_encodeTiled>(ptr);
+  }
+  return fn;
+}
+
+int make_bucket_map(CUtensorMap* out, const void* base, int ld, int count) {
+  PFN_encodeTiled enc = get_encoder();
+  if (!enc) return -1;
+  const cuuint64_t dims[3] = {cuuint64_t(ld), cuuint64_t(ld), cuuint64_t(count)};
+  const cuuint64_t strides[2] = {cuuint64_t(ld) * 2, cuuint64_t(ld) * ld * 2};
+  const cuuint32_t box[3] = {BK, BM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : int(r);
+}
+
+}  // namespace submat

@@ -1,0 +1,55 @@
+// Grouped BF16 tensor-core GEMM (tc_gemm.cu): parameters and launchers.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace submat {
+
+constexpr int TC_MAX_SLOTS = 8;
+constexpr int TC_MAX_PROD = 16;
+
+struct TcGemmParams {
+  const int4* items;        // (s, ti, tj, bucket | slot << 8), 128 x 128 tiles
+  int nitems;
+  const CUtensorMap* maps;  // device array [set][bucket]
+  int nbucket, nmaps;
+  int na, nb;               // A-side and B-side operand slices per k-block
+  int a_set[TC_MAX_SLOTS];  // tensor-map set of each A slice
+  int b_set[TC_MAX_SLOTS];
+  int nprod, nacc;
+  int prod_a[TC_MAX_PROD], prod_b[TC_MAX_PROD], prod_acc[TC_MAX_PROD], prod_first[TC_MAX_PROD];
+  int nstage, tmem_cols;
+  // wave geometry
+  const int64_t* off;
+  const int32_t* ld;
+  const int32_t* n;
+  const int* state;
+  int skip_state;
+  // epilogue: C = alpha * acc + beta * C0, written as FP32 or as a BF16 (hi, lo) split
+  float alpha, beta;
+  int sym;                        // also write the mirrored tile (items have ti <= tj)
+  float* out_f32;
+  __nv_bfloat16* out_hi;
+  __nv_bfloat16* out_lo;          // may be null: plain BF16 output
+  const float* c0_f32;
+  const __nv_bfloat16* c0_hi;
+  const __nv_bfloat16* c0_lo;
+  double* res2;                   // optional ||C - I_n||_F^2 per submatrix
+  int* flags;
+  long long timeout_cycles;
+  int test_skip_arrive;           // test hook: epilogue withholds its TMEM release
+};
+
+int tc_smem_bytes(int na, int nb, int nstage);
+int tc_pick_stages(int na, int nb);
+cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st);
+// 3D map over a bucket [count][ld][ld] of BF16, box 64 x 128 x 1, 128B swizzle.
+int make_bucket_map(CUtensorMap* out, const void* base, int ld, int count);
+
+}  // namespace submat

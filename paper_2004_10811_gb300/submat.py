@@ -28,6 +28,7 @@ EXPORTS = (
     "submat_options_default", "submat_plan_create", "submat_plan_destroy", "submat_sign",
     "submat_sign_host", "submat_trace", "submat_mu_search", "submat_sign_backward",
     "submat_plan_value_count", "submat_get_stats", "submat_get_sub_stats", "submat_last_error",
+    "submat_debug_tc_gemm",
 )
 
 
@@ -90,11 +91,13 @@ def load(path: str = LIB_PATH):
     lib.submat_plan_value_count.restype = C.c_int64
     lib.submat_get_stats.argtypes = [vp, C.POINTER(Stats)]
     lib.submat_get_sub_stats.argtypes = [vp, i32p, i32p, dp, dp]
+    lib.submat_debug_tc_gemm.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, C.c_int,
+                                         vp, vp, C.c_int, C.c_double, vp]
     lib.submat_last_error.argtypes = []
     lib.submat_last_error.restype = C.c_char_p
     for name in ("submat_plan_create", "submat_plan_destroy", "submat_sign", "submat_sign_host",
                  "submat_trace", "submat_mu_search", "submat_sign_backward", "submat_get_stats",
-                 "submat_get_sub_stats"):
+                 "submat_get_sub_stats", "submat_debug_tc_gemm"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -262,3 +265,23 @@ def make_autograd_sign(plan: Plan):
             return plan.sign_backward(K, ctx.mu, Dbar.contiguous()), None
 
     return SubmatSign.apply
+
+
+def debug_tc_gemm(A_hi, B_hi, A_lo=None, B_lo=None, n=None, sym=False, res2=None, skip_arrive=False,
+                  timeout_s=2.0, stream=None, allow_timeout=False):
+    """Test hook: the grouped BF16 tensor-core GEMM alone (include/submat_debug.h).
+
+    A_*, B_*: CUDA bfloat16 tensors [count, ld, ld]; returns (C float32, status name).
+    """
+    import torch
+    lib = load()
+    count, ld, ld2 = A_hi.shape
+    assert ld == ld2 and A_hi.dtype == torch.bfloat16 and A_hi.is_contiguous()
+    split = A_lo is not None
+    C_ = torch.empty((count, ld, ld), dtype=torch.float32, device=A_hi.device)
+    ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+    st = lib.submat_debug_tc_gemm(count, ld, ld if n is None else int(n), ptr(A_hi), ptr(A_lo),
+                                  ptr(B_hi), ptr(B_lo), int(split), int(bool(sym)), ptr(C_), ptr(res2),
+                                  int(bool(skip_arrive)), float(timeout_s), _stream(stream))
+    _check(st, allow=(8,) if allow_timeout else ())
+    return C_, STATUS[st]

@@ -67,7 +67,7 @@ def test_small_water_several_tiles(pkg):
 def test_waves_match_single_wave(pkg):
     m = small_case(n_mol=40, block=4, r_c=5.5, seed=5)
     one, _t1, s1, _ = run(pkg, m, 0.0)
-    many, _t2, s2, _ = run(pkg, m, 0.0, workspace_cap_bytes=200_000)
+    many, _t2, s2, _ = run(pkg, m, 0.0, workspace_cap_bytes=1_200_000)
     assert s1["waves"] == 1 and s2["waves"] > 3
     assert np.array_equal(one, many)
 

@@ -1,0 +1,68 @@
+"""Parity of the mixed path (BF16x3 tensor-core Newton-Schulz + FP64-anchored
+correction) with the CPU oracle: max|dD| <= 1e-7 and the trace."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_config, random_symmetric_bsr
+from synth.water import make_water
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-7
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2004_10811_gb300 as p
+    return p
+
+
+def run(pkg, m, mu, **kw):
+    import torch
+    K = torch.from_numpy(m.vals).cuda()
+    with pkg.Plan.from_bsr(m, prec="mixed", **kw) as plan:
+        D = plan.sign(K, mu)
+        tr = plan.trace(D)
+        st = plan.stats()
+    return D.cpu().numpy(), tr, st
+
+
+def test_config0_mixed(pkg):
+    m = make_config(0)
+    want = oracle.density_matrix(m, 0.0)
+    got, tr, st = run(pkg, m, 0.0)
+    err = np.max(np.abs(got - want))
+    assert err <= TOL_MIXED, (err, st)
+    assert abs(tr - oracle.trace_bsr(m, want)) / m.n_el <= 1e-9
+    assert st["refine_rounds"] >= 1 and st["iters_max"] < 40
+
+
+@pytest.mark.parametrize("n_mol,block,r_c,seed,mu", [
+    (96, 5, 6.5, 77, 0.05),     # dims ~100-300: several 128-tiles, ragged tails
+    (40, 23, 6.0, 78, 0.0),     # block 23 as in the large workloads
+])
+def test_water_mixed(pkg, n_mol, block, r_c, seed, mu):
+    occ = max(1, block // 5)
+    m = make_water(n_mol, block, r_c, (occ, -1.0, -0.3), (block - occ, 0.3, 1.2), seed=seed)
+    want = oracle.density_matrix(m, mu, workers=4)
+    got, tr, st = run(pkg, m, mu)
+    err = np.max(np.abs(got - want))
+    assert err <= TOL_MIXED, (err, st)
+    assert abs(tr - oracle.trace_bsr(m, want)) / max(1.0, m.n_el) <= 1e-9
+
+
+def test_uneven_blocks_mixed(pkg):
+    m = random_symmetric_bsr([5, 7, 3, 9, 2, 8, 6, 4, 7, 5, 3, 6] * 3, density=0.3, seed=26, scale=0.3)
+    want = oracle.density_matrix(m, 0.1)
+    got, _tr, st = run(pkg, m, 0.1)
+    assert np.max(np.abs(got - want)) <= TOL_MIXED, st
+
+
+def test_one_round_is_enough_from_split_iterate(pkg):
+    m = make_config(0)
+    want = oracle.density_matrix(m, 0.0)
+    got, _tr, _st = run(pkg, m, 0.0, refine_rounds=1)
+    assert np.max(np.abs(got - want)) <= TOL_MIXED

@@ -1,0 +1,81 @@
+"""The grouped tcgen05 BF16 GEMM alone, against torch references of the same
+product (through the C ABI test hook in include/submat_debug.h)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sm():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2004_10811_gb300 import submat
+    return submat
+
+
+def rand_bf16(count, ld, n, seed, sym=False, scale=1.0):
+    import torch
+    g = torch.Generator().manual_seed(seed)
+    x = torch.zeros(count, ld, ld, dtype=torch.float64)
+    x[:, :n, :n] = torch.randn(count, n, n, generator=g, dtype=torch.float64) * scale
+    if sym:
+        x = 0.5 * (x + x.transpose(1, 2))
+    hi = x.to(torch.bfloat16)
+    lo = (x - hi.double()).to(torch.bfloat16)
+    return x, hi.cuda(), lo.cuda()
+
+
+def test_single_tile_plain(sm):
+    _x, a, _ = rand_bf16(1, 128, 128, 1)
+    _y, b, _ = rand_bf16(1, 128, 128, 2)
+    c, st = sm.debug_tc_gemm(a, b)
+    ref = a.double() @ b.double().transpose(1, 2)
+    err = (c.double() - ref).abs().max().item()
+    assert st == "OK" and err < 1e-3 * ref.abs().max().item(), err
+
+
+@pytest.mark.parametrize("count,ld,n", [(3, 320, 300), (2, 640, 577), (5, 64, 40)])
+def test_ragged_batches_plain(sm, count, ld, n):
+    _x, a, _ = rand_bf16(count, ld, n, 3)
+    _y, b, _ = rand_bf16(count, ld, n, 4)
+    c, _ = sm.debug_tc_gemm(a, b)
+    ref = a.double() @ b.double().transpose(1, 2)
+    assert (c.double() - ref).abs().max().item() < 2e-3 * ref.abs().max().item()
+    assert c[:, n:, :].abs().max().item() == 0.0 and c[:, :, n:].abs().max().item() == 0.0
+
+
+def test_split_product_carries_16_bits(sm):
+    x, ah, al = rand_bf16(2, 384, 350, 5)
+    y, bh, bl = rand_bf16(2, 384, 350, 6)
+    c, _ = sm.debug_tc_gemm(ah, bh, al, bl)
+    ref = (x @ y.transpose(1, 2)).cuda()
+    rel = (c.double() - ref).abs().max().item() / ref.abs().max().item()
+    plain, _ = sm.debug_tc_gemm(ah, bh)
+    rel_plain = (plain.double() - ref).abs().max().item() / ref.abs().max().item()
+    assert rel < 2e-5 and rel < rel_plain / 20, (rel, rel_plain)
+
+
+def test_symmetric_mirror_and_residual(sm):
+    import torch
+    x, xh, xl = rand_bf16(3, 448, 430, 7, sym=True, scale=0.05)
+    res = torch.zeros(3, dtype=torch.float64, device="cuda")
+    full, _ = sm.debug_tc_gemm(xh, xh, xl, xl)
+    half, _ = sm.debug_tc_gemm(xh, xh, xl, xl, n=430, sym=True, res2=res)
+    assert torch.equal(half, half.transpose(1, 2))
+    up = torch.triu(torch.ones(448, 448, dtype=torch.bool, device="cuda"))
+    # upper tiles are computed the same way in both launches
+    assert (half - full)[:, up].abs().max().item() < 1e-6
+    eye = torch.zeros(448, 448, dtype=torch.float64, device="cuda")
+    eye[:430, :430] = torch.eye(430, dtype=torch.float64, device="cuda")
+    want = ((half.double() - eye) ** 2).sum(dim=(1, 2))
+    assert torch.allclose(res, want, rtol=1e-9, atol=1e-12)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(sm):
+    _x, a, _ = rand_bf16(1, 512, 512, 8)
+    c, st = sm.debug_tc_gemm(a, a, skip_arrive=True, timeout_s=0.2, allow_timeout=True)
+    assert st == "TIMEOUT"
+    c2, st2 = sm.debug_tc_gemm(a, a)
+    ref = a.double() @ a.double().transpose(1, 2)
+    assert st2 == "OK" and (c2.double() - ref).abs().max().item() < 2e-3 * ref.abs().max().item()
