@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark: seconds per density-matrix build D = 1/2 (I - sign(K - mu I)).
+
+The workload is the 1,024-molecule water-like system with 23 functions per
+molecule (n = 23,552), an 8 Angstrom cutoff and mu = 0 (synthetic, seeded;
+the paper's CP2K water matrices are not available).  One step is one whole
+build: gather, BF16x3 tensor-core Newton-Schulz, FP64-anchored correction,
+scatter -- every submatrix of the system.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (launched by torch.distributed.run)
+every rank builds its own seeded instance of the workload (weak scaling);
+the timed region is bracketed by barriers and the maximum over ranks is used.
+``--impl reference`` times the CPU FP64 oracle (the reference arm) on a
+bounded sample of block columns of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator config index, description)
+    "water1024_b23_rc8": (1, "1024 water-like molecules x 23 functions (n=23552), cutoff 8 A, mu=0"),
+    "water32_b6_rc6": (0, "32 water-like molecules x 6 functions (n=192), cutoff 6 A, mu=0"),
+    "slab4096_b6": (2, "4096-molecule slab (liquid + vapour) x 6 functions, cutoff U[7,10] A, mu=0"),
+    "water2048_b23_rc8": (3, "2048 water-like molecules x 23 functions (n=47104), cutoff 8 A, mu=0"),
+    "water20736_b6_rc9": (4, "20736 water-like molecules x 6 functions (n=124416), cutoff 9 A, gap 0.15"),
+}
+METRIC = "s per D build & TFLOP/s: BF16+refine vs FP64 path, same GB300, max|dD|<=1e-7"
+FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 rate (recipe's nominal table)
+CLASS_NAMES = ["tc_gemm_newton_schulz", "tc_gemm_correction", "simt_gemm_fp64", "gather"]
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def sample_columns(nblk, count):
+    step = max(1, nblk // count)
+    return list(range(0, nblk, step))[:count]
+
+
+def run_oracle_sample(m, cols, workers):
+    import oracle
+    t0 = time.perf_counter()
+    d = oracle.density_matrix(m, m.mu, columns=cols, workers=workers)
+    return d, time.perf_counter() - t0
+
+
+def reference_arm(args, m, desc):
+    """The oracle as it stands, on host cores, a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    workers = min(16, os.cpu_count() or 1)
+    cols = sample_columns(m.nblk, args.cpu_sample)
+    for _ in range(args.warmup):
+        run_oracle_sample(m, cols[: max(1, len(cols) // 4)], workers)
+    times = []
+    for _ in range(args.steps):
+        _d, t = run_oracle_sample(m, cols, workers)
+        times.append(t)
+    per_build = statistics.median(times) * m.nblk / len(cols)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": per_build, "unit": "s/build",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "sampled_block_columns": len(cols)},
+        "cpu_baseline": {"value": per_build, "unit": "s/build", "cores": workers, "kind": "oracle",
+                         "sample": f"{len(cols)} of {m.nblk} block columns per step (numpy eigh per "
+                                   f"submatrix in a {workers}-process pool), scaled to a full build"},
+        "e2e": {"value": per_build, "unit": "s/build", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="water1024_b23_rc8")
+    ap.add_argument("--prec", choices=["mixed", "fp64", "fp32"], default="mixed")
+    ap.add_argument("--cpu-sample", type=int, default=64, help="block columns in the oracle sample")
+    ap.add_argument("--fp64-sample", type=int, default=32, help="block columns timed on the FP64 path")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+
+    cfg_index, desc = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from synth import make_config
+    # weak scaling: each rank builds its own seeded instance of the workload
+    m = make_config(cfg_index, seed=None if rank == 0 else 1000 + cfg_index + 7919 * rank)
+
+    if args.impl == "reference":
+        reference_arm(args, m, desc)
+        return
+
+    import numpy as np
+    import torch
+    import __graft_entry__ as graft
+    graft.build()
+    import paper_2004_10811_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    peaks, peak_src = load_peaks()
+    dev = torch.device("cuda", local)
+    K = torch.from_numpy(m.vals).to(dev)
+    D = torch.empty_like(K)
+    plan = pkg.Plan.from_bsr(m, prec=args.prec, timing=True)
+    for _ in range(args.warmup):
+        plan.sign(K, m.mu, out=D)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region ----
+    acc = {"kernel_ms": [0.0] * 4, "kernel_launches": [0] * 4, "kernel_work": [0.0] * 4,
+           "launches": 0, "flops_ns": 0.0, "flops_refine": 0.0}
+    barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.sign(K, m.mu, out=D)
+            st = plan.stats()
+            for k in ("kernel_ms", "kernel_launches", "kernel_work"):
+                acc[k] = [a + b for a, b in zip(acc[k], st[k])]
+            for k in ("launches", "flops_ns", "flops_refine"):
+                acc[k] += st[k]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    t_dev = e0.elapsed_time(e1) / 1e3
+    if dist is not None:
+        tt = torch.tensor([t_dev], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    clocks = clk.summary()
+    stats = plan.stats()
+    sub = plan.sub_stats()
+
+    # ---- end to end through the host-buffer entry point ----
+    Kh = torch.from_numpy(m.vals).pin_memory()
+    Dh = torch.empty_like(Kh).pin_memory()
+    plan.sign_host(Kh.numpy(), m.mu, out=Dh.numpy())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.sign_host(Kh.numpy(), m.mu, out=Dh.numpy())
+    t_e2e = time.perf_counter() - t0
+    barrier()
+    if dist is not None:
+        tt = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    plan.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    builds = args.steps * world
+    value = t_dev / builds
+    flops_std = (acc["flops_ns"] + acc["flops_refine"]) / args.steps  # per build
+    line = {
+        "metric": METRIC, "value": value, "unit": "s/build", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64" if args.prec == "mixed" else args.prec,
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "prec": args.prec,
+                   "n": int(m.n), "nsub": int(m.nblk), "nnzb": int(m.nnzb),
+                   "sub_dim_min": int(stats["n_min"]), "sub_dim_max": int(stats["n_max"]),
+                   "l2": "inputs larger than L2 (K %.2f GB, workspace %.1f GB)" % (m.vals.nbytes / 1e9,
+                                                                                stats["workspace_bytes"] / 1e9)},
+        "tflops": flops_std / value / 1e12 / world if value > 0 else None,
+        "iters": {"min": int(sub["iters"].min()), "max": int(sub["iters"].max())},
+        "refine": {"rounds": stats["refine_rounds"], "cg_iters": stats["refine_cg_iters"],
+                   "fp64_fallback_submatrices": stats["refine_fallback"]},
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+        "gpu_launches": int(acc["launches"]),
+        "e2e": {"value": t_e2e / builds, "unit": "s/build", "h2d_bytes_per_step": int(m.vals.nbytes),
+                "d2h_bytes_per_step": int(m.vals.nbytes)},
+    }
+
+    # ---- per-kernel-class roofline ----
+    kernels = {}
+    for c in range(4):
+        n = acc["kernel_launches"][c]
+        if n == 0:
+            continue
+        ms = acc["kernel_ms"][c]
+        work = acc["kernel_work"][c]
+        if c == 3:
+            achieved = work / (ms / 1e3) / 1e9
+            unit, peak, bound, psrc = "GB/s", peaks["hbm_gbs"], "hbm", peak_src
+        elif c in (0, 1):
+            achieved = work / (ms / 1e3) / 1e12
+            unit, peak, bound, psrc = "TFLOP/s", peaks["bf16_tflops_sustained"], "tensor", peak_src + " (bf16 sustained)"
+        else:
+            achieved = work / (ms / 1e3) / 1e12
+            unit, peak, bound, psrc = "TFLOP/s", FP64_NOMINAL_GFLOPS / 1e3, "alu", "nominal FP64"
+        kernels[CLASS_NAMES[c]] = {"launches": n, "ms_total": ms, "ms_per_launch": ms / n,
+                                   "share": ms / (1e3 * t_dev), "achieved": achieved, "unit": unit,
+                                   "peak": peak, "peak_source": psrc, "bound": bound,
+                                   "frac": achieved / peak if peak else None}
+    if kernels:
+        dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+        kd = kernels[dom]
+        traffic = None
+        tpath = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tpath):
+            try:
+                tj = json.load(open(tpath))
+                ent = tj.get(args.workload, {}).get(dom)
+                if ent and ent.get("valid", True):
+                    traffic = ent["bytes_per_launch"]
+            except Exception:
+                traffic = None
+        line["roofline"] = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
+                            "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic,
+                            "peak_source": kd["peak_source"]}
+        line["kernels"] = kernels
+
+    # ---- parity on sampled block columns and the CPU oracle baseline ----
+    if not args.no_cpu and world == 1:
+        workers = min(16, os.cpu_count() or 1)
+        cols = sample_columns(m.nblk, args.cpu_sample)
+        want, t_cpu = run_oracle_sample(m, cols, workers)
+        got = Dh.numpy()
+        mask = ~np.isnan(want)
+        line["max_abs_err_vs_oracle"] = float(np.max(np.abs(got[mask] - want[mask])))
+        line["parity_sample"] = f"{len(cols)} of {m.nblk} block columns"
+        line["cpu_baseline"] = {"value": t_cpu * m.nblk / len(cols), "unit": "s/build", "cores": workers,
+                                "kind": "oracle",
+                                "sample": f"{len(cols)} of {m.nblk} block columns (numpy eigh per submatrix, "
+                                          f"{workers}-process pool), time scaled to the full build"}
+
+    # ---- the plain FP64 path on a contiguous chunk of block columns ----
+    if not args.no_fp64 and args.prec == "mixed" and world == 1:
+        nc = min(args.fp64_sample, m.nblk)
+        with pkg.Plan.from_bsr(m, prec="fp64", columns=(0, nc), timing=True) as p64:
+            Dtmp = torch.zeros_like(K)
+            p64.sign(K, m.mu, out=Dtmp)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            p64.sign(K, m.mu, out=Dtmp)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            t64 = f0.elapsed_time(f1) / 1e3
+            s64 = p64.stats()
+        sub_n3 = float(np.sum(sub["dims"].astype(np.float64) ** 3))
+        chunk_n3 = float(np.sum(sub["dims"][:nc].astype(np.float64) ** 3))
+        est = t64 * sub_n3 / chunk_n3
+        line["fp64_path"] = {"s_per_build_est": est, "sample": f"block columns [0, {nc}) timed, scaled by sum n^3",
+                             "chunk_s": t64, "iters_max": int(s64["iters_max"]),
+                             "tflops": s64["flops_ns"] / t64 / 1e12,
+                             "speedup_mixed_vs_fp64": est / value}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

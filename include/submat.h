@@ -77,7 +77,12 @@ typedef struct {
   int symmetrize;              /* 1: return (D + D^T) / 2 on the pattern; 0: column-assembled D */
   size_t workspace_cap_bytes;  /* device workspace cap; 0 = 80 % of free memory at plan time */
   int refine_rounds;           /* mixed path: correction rounds; 0 selects 2 */
-  int reserved[8];             /* must be zero */
+  int timing;                  /* 1: time every GEMM launch with CUDA events (submat_stats
+                                  kernel_* fields); adds one event pair per launch */
+  int col_begin, col_end;      /* evaluate only block columns [col_begin, col_end) of D (one
+                                  contiguous chunk, Section IV-E); 0, 0 = all columns.  The
+                                  other block columns of D are left untouched. */
+  int reserved[5];             /* must be zero */
 } submat_options;
 
 /* Aggregate statistics of the last submat_sign / submat_mu_search call. */
@@ -88,12 +93,25 @@ typedef struct {
   int32_t iters_min, iters_max; /* Newton-Schulz iterations over submatrices */
   int32_t not_converged;   /* submatrices that hit max_iter */
   int32_t refine_rounds;   /* correction rounds run (mixed path) */
+  int32_t refine_cg_iters; /* conjugate-gradient launches over all rounds and waves */
+  int32_t refine_fallback; /* submatrices re-solved in FP64 because the correction did not settle */
   double  sum_n2, sum_n3;  /* sum over submatrices of n_j^2 and n_j^3 */
   double  flops_ns;        /* standard-count Newton-Schulz flops: sum_j 4 n_j^3 iters_j */
   double  flops_refine;    /* standard-count refinement flops */
   double  max_resid;       /* largest final ||X^2 - I||_F / sqrt(n_j) */
   double  ms_gather, ms_ns, ms_refine, ms_scatter; /* phase times (CUDA events) */
   size_t  workspace_bytes; /* device workspace held by the plan */
+  int64_t launches;        /* kernel launches issued by the call */
+  /* Per kernel class, with options.timing = 1 (else zero):
+   *   0 tensor-core GEMM, Newton-Schulz;  1 tensor-core GEMM, correction;
+   *   2 FP64/FP32 SIMT GEMM;  3 gather (assembly) kernel.
+   * kernel_ms: summed launch durations; kernel_work: algorithmic work of those
+   * launches -- flops for 0-2 (2 n^3 per general n x n product, n^2 (n + 1)
+   * per product with a symmetric result, a split product counted once), bytes
+   * moved (8 bytes per dense element written plus 8 per K value read) for 3. */
+  double  kernel_ms[4];
+  int32_t kernel_launches[4];
+  double  kernel_work[4];
 } submat_stats;
 
 /* Fill *opt with defaults (FP64, default tolerances, beta_mode 0). */

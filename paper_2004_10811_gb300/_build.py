@@ -76,7 +76,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed on {cmd[-3]}:\n{r.stderr}")
     if force or jobs or _stale(LIB, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs]
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-Xlinker", "--no-undefined", "-o", LIB, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -14,6 +14,16 @@ namespace submat {
 void set_error(const char* fmt, ...);
 void clear_error();
 
+// Kernel launches issued by this library in this process (all threads).
+void count_launch(int k = 1);
+long long launch_count();
+
+#define SM_KCHECK()                         \
+  do {                                      \
+    ::submat::count_launch();               \
+    SM_CUDA(cudaGetLastError());            \
+  } while (0)
+
 #define SM_CUDA(x)                                                                   \
   do {                                                                               \
     cudaError_t e_ = (x);                                                            \

@@ -155,12 +155,14 @@ __global__ void __launch_bounds__(256) k_gemm_simt(Args a) {
 cudaError_t launch_gemm_f64(const GemmF64Args& a, cudaStream_t st) {
   if (a.nitems <= 0) return cudaSuccess;
   k_gemm_simt<double, GemmF64Args><<<a.nitems, 256, 0, st>>>(a);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_f32(const GemmF32Args& a, cudaStream_t st) {
   if (a.nitems <= 0) return cudaSuccess;
   k_gemm_simt<float, GemmF32Args><<<a.nitems, 256, 0, st>>>(a);
+  count_launch();
   return cudaGetLastError();
 }
 

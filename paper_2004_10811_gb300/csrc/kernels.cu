@@ -2,6 +2,7 @@
 // Newton-Schulz bookkeeping, extraction (scatter) and the trace.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 
@@ -284,6 +285,10 @@ __global__ void k_check_finite(const double* __restrict__ v, int64_t count, int*
 
 }  // namespace
 
+static std::atomic<long long> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 cudaError_t launch_gather(const PatternDev& g, const WaveDev& w, const int2* items, int nitems,
                           int nb_max, const double* K, double mu, double* A, NsStateDev ns,
                           int* flags, cudaStream_t st) {
@@ -295,11 +300,13 @@ cudaError_t launch_gather(const PatternDev& g, const WaveDev& w, const int2* ite
     if (e != cudaSuccess) return e;
   }
   k_gather<<<nitems, 256, smem, st>>>(g, w, items, K, mu, A, ns, flags);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_beta(const WaveDev& w, NsStateDev ns, int beta_mode, cudaStream_t st) {
   k_beta<<<(w.nsub + 255) / 256, 256, 0, st>>>(w, ns, beta_mode);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -313,24 +320,28 @@ static dim3 scale_grid(const WaveDev& w, int64_t max_ld2) {
 cudaError_t launch_scale_f64(const WaveDev& w, const double* A, double* X, const double* beta,
                              int64_t max_ld2, cudaStream_t st) {
   k_scale<double><<<scale_grid(w, max_ld2), 256, 0, st>>>(w, A, X, beta);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_scale_f32(const WaveDev& w, const double* A, float* X, const double* beta,
                              int64_t max_ld2, cudaStream_t st) {
   k_scale<float><<<scale_grid(w, max_ld2), 256, 0, st>>>(w, A, X, beta);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_ns_update(const WaveDev& w, NsStateDev ns, double tol, double floor_thr,
                              int max_iter, int* flags, cudaStream_t st) {
   k_ns_update<<<(w.nsub + 255) / 256, 256, 0, st>>>(w, ns, tol, floor_thr, max_iter, flags);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_ns_post(const WaveDev& w, NsStateDev ns, int par_new, int* d_active,
                            cudaStream_t st) {
   k_ns_post<<<(w.nsub + 255) / 256, 256, 0, st>>>(w, ns, par_new, d_active);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -345,6 +356,7 @@ static cudaError_t scatter_impl(const PatternDev& g, const WaveDev& w, NsStateDe
     if (e != cudaSuccess) return e;
   }
   k_scatter<T><<<w.nsub, 256, smem, st>>>(g, w, ns, buf0, buf1, D, trpart);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -363,9 +375,11 @@ cudaError_t launch_scatter_f32(const PatternDev& g, const WaveDev& w, NsStateDev
 cudaError_t launch_trace(const PatternDev& g, int nblk, const double* D, double* part,
                          double* out, cudaStream_t st) {
   k_diag_sums<<<(nblk + 255) / 256, 256, 0, st>>>(g, nblk, D, part);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_reduce_fixed<<<1, 1024, 0, st>>>(part, nblk, out);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -373,6 +387,7 @@ cudaError_t launch_symmetrize_impl(const PatternDev& g, int64_t nnzb, const doub
                                    double* Dout, const int64_t* rowof, cudaStream_t st) {
   if (nnzb <= 0) return cudaSuccess;
   k_symmetrize<<<unsigned(nnzb), 64, 0, st>>>(g, nnzb, Din, Dout, rowof);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -381,6 +396,7 @@ cudaError_t launch_check_finite(const double* v, int64_t count, int* flags, cuda
   int64_t blocks = (count + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   k_check_finite<<<unsigned(blocks), 256, 0, st>>>(v, count, flags);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -155,10 +155,12 @@ __global__ void k_comm(WaveDev w, const double* __restrict__ P, const float* __r
 }
 
 // CG step 1: TP = W + W^T in place (tile pairs), pTp_s = <P, TP>.
-__global__ void k_cg_sym(WaveDev w, float* __restrict__ W, const float* __restrict__ Pd, double* ptp) {
+__global__ void k_cg_sym(WaveDev w, float* __restrict__ W, const float* __restrict__ Pd, double* ptp,
+                         const int* __restrict__ cg_done) {
   __shared__ float ta_[32][33], tb_[32][33];
   __shared__ double red[32];
   const int s = blockIdx.y;
+  if (cg_done[s]) return;
   const int ld = w.ld[s];
   const int64_t base = w.off[s];
   const int T = ld / 32;
@@ -212,8 +214,11 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // CG step 2: alpha = rr / pTp; X += alpha P; R -= alpha TP; rr_new = <R, R>.
 __global__ void k_cg_update(WaveDev w, float* __restrict__ X, float* __restrict__ R,
                             const float* __restrict__ Pd, const float* __restrict__ TP,
-                            const double* rr, const double* ptp, double* rr_new) {
+                            const double* rr, const double* ptp, double* rr_new,
+                            const int* __restrict__ cg_done, int* cg_count) {
   __shared__ double red[32];
+  if (cg_done[blockIdx.y]) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ++cg_count[blockIdx.y];
   const double den = ptp[blockIdx.y];
   const float alpha = (den > 0.0 && rr[blockIdx.y] > 0.0) ? float(rr[blockIdx.y] / den) : 0.0f;
   double part = 0.0;
@@ -231,7 +236,8 @@ __global__ void k_cg_update(WaveDev w, float* __restrict__ X, float* __restrict_
 // CG step 3: P = R + (rr_new / rr) P, split for the next product.
 __global__ void k_cg_dir(WaveDev w, const float* __restrict__ R, float* __restrict__ Pd,
                          const double* rr, const double* rr_new, __nv_bfloat16* ph,
-                         __nv_bfloat16* pl) {
+                         __nv_bfloat16* pl, const int* __restrict__ cg_done) {
+  if (cg_done[blockIdx.y]) return;
   const double d = rr[blockIdx.y];
   const float beta = d > 0.0 ? float(rr_new[blockIdx.y] / d) : 0.0f;
   FOR_SUB_ELEMS(w) {
@@ -259,13 +265,74 @@ __global__ void k_cg_init(WaveDev w, float* __restrict__ X, const float* __restr
   if (threadIdx.x == 0) atomicAdd(&rr[blockIdx.y], t);
 }
 
-// S <- S - F_c - F_a
+// After the direction update: a submatrix whose relative CG residual
+// sqrt(rr / rr0) fell below tol stops (its later CG launches return at once).
+// Counts the submatrices still iterating.
+__global__ void k_cg_check(int nsub, const double* rr, const double* rr0, int* cg_done, double tol2,
+                           int* d_active) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int active = 0;
+  if (s < nsub && !cg_done[s]) {
+    if (!(rr[s] > tol2 * rr0[s])) cg_done[s] = 1;
+    else active = 1;
+  }
+  active = __syncthreads_count(active);
+  if (threadIdx.x == 0 && active) atomicAdd(d_active, active);
+}
+
+// S <- S - F_c - F_a, and corr_s = max |F_c + F_a| (bits of a non-negative double)
 __global__ void k_apply(WaveDev w, double* __restrict__ S, const float* __restrict__ Fc,
-                        const float* __restrict__ Fa) {
+                        const float* __restrict__ Fa, unsigned long long* corr) {
+  __shared__ double red[32];
+  double mx = 0.0;
   FOR_SUB_ELEMS(w) {
     const int64_t i = base + e;
-    S[i] = S[i] - double(Fc[i]) - double(Fa[i]);
+    const double f = double(Fc[i]) + double(Fa[i]);
+    S[i] = S[i] - f;
+    mx = fmax(mx, fabs(f));
   }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < int(blockDim.x) / 32; ++q) t = fmax(t, red[q]);
+    atomicMax(&corr[blockIdx.y], (unsigned long long)__double_as_longlong(t));
+  }
+}
+
+// Submatrices whose last correction was still large, or whose Lyapunov solve
+// did not converge (a gap far smaller than the spectral radius), are
+// re-solved by FP64 Newton-Schulz: state ACTIVE for those, DONE for the rest.
+__global__ void k_pick_fallback(WaveDev w, NsStateDev ns, const unsigned long long* corr,
+                                const double* rr, const double* rr0, double corr_tol,
+                                double cg_tol2, int* fallback_flag, int* d_count) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int pick = 0;
+  if (s < w.nsub) {
+    const double c = __longlong_as_double((long long)corr[s]);
+    const bool bad = !(c <= corr_tol) || (rr[s] > cg_tol2 * rr0[s]);
+    fallback_flag[s] = bad ? 1 : 0;
+    ns.par[s] = 0;
+    if (bad) {
+      ns.state[s] = ST_ACTIVE;
+      ns.res2[s] = 0.0;
+      ns.rprev[s] = 1e300;
+      pick = 1;
+    } else {
+      ns.state[s] = ST_DONE;
+    }
+  }
+  pick = __syncthreads_count(pick);
+  if (threadIdx.x == 0 && pick) atomicAdd(d_count, pick);
+}
+
+// X_0 = a / beta in FP64 for the submatrices picked for the fallback
+__global__ void k_scale_picked(WaveDev w, const int* __restrict__ pick, const double* __restrict__ A,
+                               const double* __restrict__ beta, double* __restrict__ X) {
+  if (!pick[blockIdx.y]) return;
+  const double ib = 1.0 / beta[blockIdx.y];
+  FOR_SUB_ELEMS(w) X[base + e] = A[base + e] * ib;
 }
 
 dim3 elem_grid(const Wave& wv) {
@@ -283,7 +350,11 @@ dim3 pair_grid(const Wave& wv) {
 
 struct MixedState {
   std::vector<CUtensorMap*> d_maps;  // per wave: [MS_COUNT][nbucket]
-  double* scal = nullptr;            // per-slot CG scalars: rr, ptp, rr_new (3 x max_wave)
+  double* scal = nullptr;            // per-slot scalars: rr, ptp, rr_new, rr0 (4 x max_wave)
+  int* cg_done = nullptr;            // per slot
+  int* cg_count = nullptr;           // per slot: CG iterations run (all rounds)
+  int* pick = nullptr;               // per slot: FP64 fallback
+  unsigned long long* corr = nullptr;  // per slot: max |correction| of the last round
 };
 
 }  // namespace
@@ -314,7 +385,11 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
                               cudaMemcpyHostToDevice, st));
       ms->d_maps.push_back(d);
     }
-    SM_TRY(alloc(&ms->scal, size_t(3) * max_wave, "CG scalars"));
+    SM_TRY(alloc(&ms->scal, size_t(4) * max_wave, "CG scalars"));
+    SM_TRY(alloc(&ms->cg_done, size_t(max_wave), "CG flags"));
+    SM_TRY(alloc(&ms->cg_count, size_t(max_wave), "CG counts"));
+    SM_TRY(alloc(&ms->pick, size_t(max_wave), "fallback flags"));
+    SM_TRY(alloc(&ms->corr, size_t(max_wave), "correction sizes"));
   }
   const long long tmo = timeout_cycles_for(2.0);
   const int nsm = num_sms();
@@ -322,6 +397,8 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
   double* rr = ms->scal;
   double* ptp = rr + max_wave;
   double* rrn = ptp + max_wave;
+  double* rr0 = rrn + max_wave;
+  int fallback_total = 0;
 
   for (size_t wi = 0; wi < waves.size(); ++wi) {
     Wave& wv = waves[wi];
@@ -353,8 +430,20 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       p.timeout_cycles = tmo;
       return p;
     };
+    int tc_class = KC_TC_NS;
     auto launch = [&](const TcGemmParams& p) -> cudaError_t {
-      return launch_tc_gemm(p, std::min(p.nitems, nsm), st);
+      size_t tk;
+      if (timer.start(tc_class, st, &tk) != SUBMAT_OK) return cudaErrorUnknown;
+      cudaError_t e = launch_tc_gemm(p, std::min(p.nitems, nsm), st);
+      if (e == cudaSuccess && timer.stop(tk, st) != SUBMAT_OK) return cudaErrorUnknown;
+      return e;
+    };
+    auto f64 = [&](const GemmF64Args& a) -> cudaError_t {
+      size_t tk;
+      if (timer.start(KC_SIMT, st, &tk) != SUBMAT_OK) return cudaErrorUnknown;
+      cudaError_t e = launch_gemm_f64(a, st);
+      if (e == cudaSuccess && timer.stop(tk, st) != SUBMAT_OK) return cudaErrorUnknown;
+      return e;
     };
 
     // ---- assemble and scale (Section III-A step 1) ----
@@ -362,7 +451,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     SM_TRY(gather_wave(wv, K, mu, b.A, st));
     const dim3 eg = elem_grid(wv);
     k_scale_split<<<eg, 256, 0, st>>>(wv.dev, b.A, ns.beta, b.X[0][0], b.X[0][1]);
-    SM_CUDA(cudaGetLastError());
+    SM_KCHECK();
     SM_CUDA(cudaEventRecord(ev[1], st));
 
     // ---- BF16x3 Newton-Schulz on the tensor cores ----
@@ -391,73 +480,113 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     SM_CUDA(cudaEventRecord(ev[2], st));
 
     // ---- correction rounds ----
+    tc_class = KC_TC_REF;
+    std::vector<int> lp_iters(wv.count);
+    SM_CUDA(cudaMemcpyAsync(lp_iters.data(), ns.iters, sizeof(int) * wv.count, cudaMemcpyDeviceToHost, st));
+    SM_CUDA(cudaMemsetAsync(ms->cg_count, 0, sizeof(int) * max_wave, st));
     k_widen<<<eg, 256, 0, st>>>(wv.dev, ns.par, b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.S);
-    SM_CUDA(cudaGetLastError());
+    SM_KCHECK();
     k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
-    SM_CUDA(cudaGetLastError());
+    SM_KCHECK();
     const int rounds = std::max(1, opt.refine_rounds);
-    const int cg_iters = 10;
+    const int cg_max = 60;          // CG cap per round
+    const double cg_tol = 1e-4;     // relative residual that ends CG for a submatrix
+    const double cg_bad = 1e-2;     // above this after cg_max the submatrix falls back
+    const double corr_tol = 1e-8;   // largest acceptable last-round correction
+    int cg_total = 0;
     for (int rd = 0; rd < rounds; ++rd) {
       if (rd > 0) {  // the operand split of S for this round
         k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
-        SM_CUDA(cudaGetLastError());
+        SM_KCHECK();
       }
       // T = I - S^2 (FP64)
       GemmF64Args f{};
       f.w = wv.dev; f.items = wv.sym64; f.nitems = wv.n_sym64;
       f.A = b.S; f.B = b.S; f.C0 = nullptr; f.C = b.T;
       f.alpha = -1.0; f.beta = 0.0; f.diag = 1.0; f.sym = 1;
-      SM_CUDA(launch_gemm_f64(f, st));
+      SM_CUDA(f64(f));
       k_split64<<<eg, 256, 0, st>>>(wv.dev, b.T, b.Y[0], b.Y[1]);
-      SM_CUDA(cudaGetLastError());
+      SM_KCHECK();
       // F_c = -1/2 S (I - S^2)
       TcGemmParams g = tc(wv.sym128, wv.n_sym128, MS_XH0, MS_XL0, MS_YH, MS_YL, 1, -0.5f, 0.0f);
       g.out_f32 = b.Fc;
       SM_CUDA(launch(g));
       k_split32<<<eg, 256, 0, st>>>(wv.dev, b.Fc, b.Y[0], b.Y[1]);
-      SM_CUDA(cudaGetLastError());
+      SM_KCHECK();
       // T = S a (FP64)
       GemmF64Args f2{};
       f2.w = wv.dev; f2.items = wv.full64; f2.nitems = wv.n_full64;
       f2.A = b.S; f2.B = b.A; f2.C0 = nullptr; f2.C = b.T;
       f2.alpha = 1.0; f2.beta = 0.0; f2.diag = 0.0; f2.sym = 0;
-      SM_CUDA(launch_gemm_f64(f2, st));
+      SM_CUDA(f64(f2));
       // W = F_c a
       TcGemmParams g3 = tc(wv.full128, wv.n_full128, MS_YH, MS_YL, MS_AH, MS_AL, 0, 1.0f, 0.0f);
       g3.out_f32 = b.cw;
       SM_CUDA(launch(g3));
       // M = [S, a] - [F_c, a] (split into Y), H = (S a + a S) / 2 (split)
       k_comm<<<pair_grid(wv), dim3(32, 8), 0, st>>>(wv.dev, b.T, b.cw, b.Y[0], b.Y[1], b.Hh[0], b.Hh[1]);
-      SM_CUDA(cudaGetLastError());
+      SM_KCHECK();
       // C = M S (symmetric to first order) -> CG residual
       TcGemmParams g4 = tc(wv.sym128, wv.n_sym128, MS_YH, MS_YL, MS_XH0, MS_XL0, 1, 1.0f, 0.0f);
       g4.out_f32 = b.cr;
       SM_CUDA(launch(g4));
-      // CG on L -> H L + L H
-      SM_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * 3 * max_wave, st));
+      // CG on L -> H L + L H, per submatrix until the relative residual is below cg_tol
+      SM_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * 4 * max_wave, st));
+      SM_CUDA(cudaMemsetAsync(ms->cg_done, 0, sizeof(int) * max_wave, st));
       k_cg_init<<<eg, 256, 0, st>>>(wv.dev, b.cx, b.cr, b.cp, rr, b.Y[0], b.Y[1]);
-      SM_CUDA(cudaGetLastError());
-      for (int it = 0; it < cg_iters; ++it) {
+      SM_KCHECK();
+      SM_CUDA(cudaMemcpyAsync(rr0, rr, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
+      for (int it = 0; it < cg_max; ++it) {
         TcGemmParams gh = tc(wv.full128, wv.n_full128, MS_HH, MS_HL, MS_YH, MS_YL, 0, 1.0f, 0.0f);
         gh.out_f32 = b.cw;
+        gh.state = ms->cg_done; gh.skip_state = 1;
         SM_CUDA(launch(gh));
         SM_CUDA(cudaMemsetAsync(ptp, 0, sizeof(double) * 2 * max_wave, st));  // ptp and rr_new
-        k_cg_sym<<<pair_grid(wv), dim3(32, 8), 0, st>>>(wv.dev, b.cw, b.cp, ptp);
-        SM_CUDA(cudaGetLastError());
-        k_cg_update<<<eg, 256, 0, st>>>(wv.dev, b.cx, b.cr, b.cp, b.cw, rr, ptp, rrn);
-        SM_CUDA(cudaGetLastError());
-        k_cg_dir<<<eg, 256, 0, st>>>(wv.dev, b.cr, b.cp, rr, rrn, b.Y[0], b.Y[1]);
-        SM_CUDA(cudaGetLastError());
+        k_cg_sym<<<pair_grid(wv), dim3(32, 8), 0, st>>>(wv.dev, b.cw, b.cp, ptp, ms->cg_done);
+        SM_KCHECK();
+        k_cg_update<<<eg, 256, 0, st>>>(wv.dev, b.cx, b.cr, b.cp, b.cw, rr, ptp, rrn, ms->cg_done,
+                                        ms->cg_count);
+        SM_KCHECK();
+        k_cg_dir<<<eg, 256, 0, st>>>(wv.dev, b.cr, b.cp, rr, rrn, b.Y[0], b.Y[1], ms->cg_done);
+        SM_KCHECK();
         SM_CUDA(cudaMemcpyAsync(rr, rrn, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
+        cg_total += 1;
+        if ((it + 1) % 4 == 0) {
+          SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
+          k_cg_check<<<(wv.count + 255) / 256, 256, 0, st>>>(wv.count, rr, rr0, ms->cg_done,
+                                                             cg_tol * cg_tol, d_active);
+          SM_KCHECK();
+          SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+          SM_CUDA(cudaStreamSynchronize(st));
+          if (reinterpret_cast<int*>(h_pinned)[0] == 0) break;
+        }
       }
-      k_apply<<<eg, 256, 0, st>>>(wv.dev, b.S, b.Fc, b.cx);
-      SM_CUDA(cudaGetLastError());
+      SM_CUDA(cudaMemsetAsync(ms->corr, 0, sizeof(unsigned long long) * max_wave, st));
+      k_apply<<<eg, 256, 0, st>>>(wv.dev, b.S, b.Fc, b.cx, ms->corr);
+      SM_KCHECK();
+    }
+    // ---- FP64 Newton-Schulz for the submatrices the correction could not settle ----
+    SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
+    k_pick_fallback<<<(wv.count + 255) / 256, 256, 0, st>>>(wv.dev, ns, ms->corr, rr, rr0, corr_tol,
+                                                            cg_bad * cg_bad, ms->pick, d_active);
+    SM_KCHECK();
+    SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SM_CUDA(cudaStreamSynchronize(st));
+    const int npick = reinterpret_cast<int*>(h_pinned)[0];
+    fallback_total += npick;
+    double* outS0 = b.S;
+    double* outS1 = b.S;
+    if (npick > 0) {
+      k_scale_picked<<<eg, 256, 0, st>>>(wv.dev, ms->pick, b.A, ns.beta, b.S);
+      SM_KCHECK();
+      // ping-pong between S and T; A serves as the X^2 buffer
+      SM_TRY((ns_simt<double, GemmF64Args>(wv, b.S, b.T, b.A, 1e-14, 1e-9, st, launch_gemm_f64)));
+      outS1 = b.T;
     }
     stats.refine_rounds = rounds;
     SM_CUDA(cudaEventRecord(ev[3], st));
-    // ---- extract (Section III-A step 3): S is at "parity 0" for every submatrix ----
-    SM_CUDA(cudaMemsetAsync(ns.par, 0, sizeof(int) * wv.count, st));
-    SM_CUDA(launch_scatter_f64(g, wv.dev, ns, b.S, b.S, D, d_trpart, nb_max, st));
+    // ---- extract (Section III-A step 3); ns.par picks S or, for fallbacks, S/T ----
+    SM_CUDA(launch_scatter_f64(g, wv.dev, ns, outS0, outS1, D, d_trpart, nb_max, st));
     SM_TRY(collect_wave(wv, st));
     float t01 = 0, t12 = 0, t23 = 0;
     SM_CUDA(cudaEventElapsedTime(&t01, ev[0], ev[1]));
@@ -466,13 +595,30 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     stats.ms_gather += t01;
     stats.ms_ns += t12;
     stats.ms_refine += t23;
+    std::vector<int> cgc(wv.count);
+    SM_CUDA(cudaMemcpyAsync(cgc.data(), ms->cg_count, sizeof(int) * wv.count, cudaMemcpyDeviceToHost, st));
+    SM_CUDA(cudaStreamSynchronize(st));
     double fl = 0.0;
     for (int s = 0; s < wv.count; ++s) {
       const double n = double(wv.host_n[s]);
-      // per round: 2 FP64 products (4 n^3), 3 + cg_iters split products (2 n^3 each)
-      fl += rounds * (4.0 + 2.0 * (3 + cg_iters)) * n * n * n;
+      // per round: 2 FP64 products (4 n^3 standard count) and 3 split products
+      // (6 n^3); per CG iteration one split product (2 n^3)
+      fl += (rounds * 10.0 + 2.0 * cgc[s]) * n * n * n;
     }
     stats.flops_refine += fl;
+    stats.refine_cg_iters += cg_total;
+    for (int s = 0; s < wv.count; ++s) {
+      const double n = double(wv.host_n[s]);
+      const double n3 = n * n * n;
+      const int extra = res_iters[wv.first + s] - lp_iters[s];  // FP64 fallback iterations
+      // algorithmic flops: a product with a symmetric result needs n^2 (n + 1),
+      // a general one 2 n^3; the three-term split counts once
+      const double sym = n * n * (n + 1.0);
+      stats.kernel_work[KC_TC_NS] += 2.0 * sym * lp_iters[s];
+      stats.kernel_work[KC_TC_REF] += (2.0 * sym + 2.0 * n3) * rounds + 2.0 * n3 * cgc[s];
+      stats.kernel_work[KC_SIMT] += (sym + 2.0 * n3) * rounds + 2.0 * sym * extra;
+    }
+    stats.refine_fallback = fallback_total;
   }
   return SUBMAT_OK;
 }

@@ -49,35 +49,11 @@ submat_status dev_alloc(void** p, size_t bytes, const char* what) {
   return SUBMAT_OK;
 }
 
-template <typename T>
-static submat_status upload(T** dst, const std::vector<T>& src, cudaStream_t st, const char* what) {
-  SM_TRY(dev_alloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T), what));
-  if (!src.empty())
-    SM_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-  return SUBMAT_OK;
-}
-
 Plan::~Plan() {
   free_mixed(mixed);
   for (void* p : owned) cudaFree(p);
   if (h_pinned) cudaFreeHost(h_pinned);
   for (auto& e : ev) if (e) cudaEventDestroy(e);
-}
-
-template <typename T>
-submat_status Plan::alloc(T** p, size_t count, const char* what) {
-  void* q = nullptr;
-  SM_TRY(dev_alloc(&q, count * sizeof(T), what));
-  if (q) owned.push_back(q);
-  *p = static_cast<T*>(q);
-  return SUBMAT_OK;
-}
-
-template <typename T>
-submat_status Plan::put(T** p, const std::vector<T>& v, cudaStream_t st, const char* what) {
-  SM_TRY(upload(p, v, st, what));
-  if (*p) owned.push_back(*p);
-  return SUBMAT_OK;
 }
 
 // bytes of workspace per dense element for each precision
@@ -87,6 +63,47 @@ static size_t bytes_per_elem(int prec) {
     case SUBMAT_FP32: return 8 + 3 * 4;             // A (FP64) + X ping-pong + X^2
     default: return mixed_bytes_per_elem();
   }
+}
+
+// ---------------------------------------------------------------------------
+// per-launch timing
+// ---------------------------------------------------------------------------
+
+KernelTimer::~KernelTimer() {
+  for (auto e : pool) cudaEventDestroy(e);
+}
+
+submat_status KernelTimer::start(int cls, cudaStream_t st, size_t* tok) {
+  *tok = size_t(-1);
+  if (!on) return SUBMAT_OK;
+  while (pool.size() < used + 2) {
+    cudaEvent_t e;
+    SM_CUDA(cudaEventCreate(&e));
+    pool.push_back(e);
+  }
+  *tok = used;
+  marks.emplace_back(cls, used);
+  SM_CUDA(cudaEventRecord(pool[used], st));
+  used += 2;
+  return SUBMAT_OK;
+}
+
+submat_status KernelTimer::stop(size_t tok, cudaStream_t st) {
+  if (!on || tok == size_t(-1)) return SUBMAT_OK;
+  SM_CUDA(cudaEventRecord(pool[tok + 1], st));
+  return SUBMAT_OK;
+}
+
+submat_status KernelTimer::collect(double* ms, int32_t* count) {
+  for (auto& m : marks) {
+    float t = 0.0f;
+    SM_CUDA(cudaEventElapsedTime(&t, pool[m.second], pool[m.second + 1]));
+    ms[m.first] += t;
+    count[m.first] += 1;
+  }
+  marks.clear();
+  used = 0;
+  return SUBMAT_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -223,12 +240,14 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
   std::vector<int64_t> ld_of(nblk);
   for (int j = 0; j < nblk; ++j) ld_of[j] = (nsub[j] + 63) / 64 * 64;
   waves.clear();
+  col_lo = opt.col_end > opt.col_begin ? opt.col_begin : 0;
+  col_hi = opt.col_end > opt.col_begin ? opt.col_end : nblk;
   {
-    int first = 0;
-    while (first < nblk) {
+    int first = col_lo;
+    while (first < col_hi) {
       int64_t elems = 0;
       int cnt = 0;
-      while (first + cnt < nblk) {
+      while (first + cnt < col_hi) {
         const int64_t e = ld_of[first + cnt] * ld_of[first + cnt];
         if (cnt > 0 && size_t(elems + e) * bpe > cap) break;
         if (cnt == 0 && size_t(e) * bpe > cap) {
@@ -346,6 +365,23 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
   SM_TRY(alloc(&d_scalar, 8, "scalars"));
   SM_CUDA(cudaMallocHost(&h_pinned, 64));
   for (auto& e : ev) SM_CUDA(cudaEventCreate(&e));
+  timer.on = opt.timing != 0;
+  if (timer.on) {
+    // K values each submatrix reads: the stored blocks inside N(j) x N(j)
+    gather_bytes.assign(nblk, 0.0);
+    for (int j = 0; j < nblk; ++j) {
+      double acc = 0.0;
+      for (int64_t t = row_ptr[j]; t < row_ptr[j + 1]; ++t) {
+        const int i = col[t];
+        int64_t a = row_ptr[j], e = row_ptr[j + 1];
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+          while (a < e && col[a] < col[q]) ++a;
+          if (a < e && col[a] == col[q]) acc += double(bs[i]) * bs[col[q]];
+        }
+      }
+      gather_bytes[j] = 8.0 * acc;
+    }
+  }
   res_iters.assign(nblk, 0);
   res_resid.assign(nblk, 0.0);
   res_beta.assign(nblk, 0.0);
@@ -368,7 +404,13 @@ submat_status Plan::read_flags(cudaStream_t st, int* out) {
 submat_status Plan::gather_wave(Wave& wv, const double* K, double mu, double* A, cudaStream_t st) {
   SM_CUDA(cudaMemsetAsync(ns.gersh, 0, sizeof(unsigned long long) * wv.count, st));
   SM_CUDA(cudaMemsetAsync(ns.fro2, 0, sizeof(double) * wv.count, st));
+  size_t tk;
+  SM_TRY(timer.start(KC_GATHER, st, &tk));
   SM_CUDA(launch_gather(g, wv.dev, wv.gather_items, wv.n_gather, nb_max, K, mu, A, ns, d_flags, st));
+  SM_TRY(timer.stop(tk, st));
+  if (timer.on)
+    for (int s = 0; s < wv.count; ++s)
+      stats.kernel_work[KC_GATHER] += 8.0 * double(wv.host_ld[s]) * wv.host_ld[s] + gather_bytes[wv.first + s];
   int fl = 0;
   SM_TRY(read_flags(st, &fl));
   if (fl & FLAG_NONFINITE) {
@@ -412,12 +454,17 @@ submat_status Plan::ns_simt(const Wave& wv, T* buf0, T* buf1, T* Y, double tol, 
     a1.A = bufs[cur]; a1.B = bufs[cur]; a1.C0 = nullptr; a1.C = Y;
     a1.alpha = 1.0; a1.beta = 0.0; a1.sym = 1; a1.res2 = ns.res2;
     a1.state = ns.state; a1.skip_state = ST_DONE;
+    size_t tk1, tk2;
+    SM_TRY(timer.start(KC_SIMT, st, &tk1));
     SM_CUDA(gemm(a1, st));
+    SM_TRY(timer.stop(tk1, st));
     SM_CUDA(launch_ns_update(wv.dev, ns, tol, floor_thr, opt.max_iter, d_flags, st));
     Args a2 = a1;
     a2.B = Y; a2.C0 = bufs[cur]; a2.C = bufs[cur ^ 1];
     a2.alpha = -0.5; a2.beta = 1.5; a2.res2 = nullptr;
+    SM_TRY(timer.start(KC_SIMT, st, &tk2));
     SM_CUDA(gemm(a2, st));
+    SM_TRY(timer.stop(tk2, st));
     SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
     SM_CUDA(launch_ns_post(wv.dev, ns, cur ^ 1, d_active, st));
     SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -481,19 +528,29 @@ submat_status Plan::add_phase_times() {
 
 void Plan::reset_stats() {
   std::memset(&stats, 0, sizeof(stats));
-  stats.nsub = nblk;
-  stats.n_min = n_min;
-  stats.n_max = n_max;
+  stats.nsub = col_hi - col_lo;
+  int nmin = INT32_MAX, nmax = 0;
+  double s2 = 0.0, s3 = 0.0;
+  for (int j = col_lo; j < col_hi; ++j) {
+    const double n = nsub[j];
+    nmin = std::min(nmin, nsub[j]);
+    nmax = std::max(nmax, nsub[j]);
+    s2 += n * n;
+    s3 += n * n * n;
+  }
+  stats.n_min = nmin == INT32_MAX ? 0 : nmin;
+  stats.n_max = nmax;
   stats.waves = int(waves.size());
-  stats.sum_n2 = sum_n2;
-  stats.sum_n3 = sum_n3;
+  stats.sum_n2 = s2;
+  stats.sum_n3 = s3;
   stats.workspace_bytes = ws_bytes;
+  launches_at_start = launch_count();
 }
 
 void Plan::finish_stats() {
   int imin = INT32_MAX, imax = 0, nc = 0;
   double flops = 0.0, rmax = 0.0;
-  for (int j = 0; j < nblk; ++j) {
+  for (int j = col_lo; j < col_hi; ++j) {
     imin = std::min(imin, res_iters[j]);
     imax = std::max(imax, res_iters[j]);
     nc += res_notconv[j];
@@ -505,6 +562,17 @@ void Plan::finish_stats() {
   stats.not_converged = nc;
   stats.flops_ns = flops;
   stats.max_resid = rmax;
+  stats.launches = launch_count() - launches_at_start;
+  if (timer.on) {
+    timer.collect(stats.kernel_ms, stats.kernel_launches);
+    if (opt.prec != SUBMAT_MIXED_BF16_REFINE) {
+      // two symmetric products per iteration: n^2 (n + 1) flops each
+      for (int j = col_lo; j < col_hi; ++j) {
+        const double n = nsub[j];
+        stats.kernel_work[KC_SIMT] += 2.0 * n * n * (n + 1.0) * res_iters[j];
+      }
+    }
+  }
 }
 
 submat_status Plan::sign(const double* K, double mu, double* D, cudaStream_t st) {
@@ -597,6 +665,10 @@ submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int
     }
     for (int r : o.reserved)
       if (r != 0) { submat::set_error("reserved option fields must be zero"); return SUBMAT_ERR_INVALID_ARG; }
+    if (o.col_begin < 0 || o.col_end < 0 || o.col_end > nblk || (o.col_end > 0 && o.col_begin >= o.col_end)) {
+      submat::set_error("bad column range [%d, %d) for %d block columns", o.col_begin, o.col_end, nblk);
+      return SUBMAT_ERR_INVALID_ARG;
+    }
     if (o.max_iter == 0) o.max_iter = 100;
     if (o.refine_rounds == 0) o.refine_rounds = 2;
     submat_status s = submat::validate_pattern_public(nblk, block_sizes, row_ptr, col_idx);

@@ -41,6 +41,20 @@ struct Wave {
   void* tc = nullptr;
 };
 
+// Event pairs around kernel launches, grouped in classes (submat_stats kernel_*).
+struct KernelTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, size_t>> marks;  // (class, index of the start event)
+  ~KernelTimer();
+  submat_status start(int cls, cudaStream_t st, size_t* tok);
+  submat_status stop(size_t tok, cudaStream_t st);
+  submat_status collect(double* ms, int32_t* count);  // after a stream sync
+};
+
+enum KernelClass { KC_TC_NS = 0, KC_TC_REF = 1, KC_SIMT = 2, KC_GATHER = 3 };
+
 struct Plan {
   ~Plan();
 
@@ -52,6 +66,7 @@ struct Plan {
   std::vector<int32_t> bs, col, locoff, tpos, nsub, koff, diagpos;
   std::vector<int64_t> row_ptr, valptr, rowof;
   int nb_max = 0, n_max = 0, n_min = 0;
+  int col_lo = 0, col_hi = 0;      // evaluated block columns
   double sum_n2 = 0, sum_n3 = 0;
 
   // device
@@ -79,6 +94,9 @@ struct Plan {
   std::vector<int> res_iters, res_notconv;
   std::vector<double> res_resid, res_beta;
   submat_stats stats{};
+  KernelTimer timer;
+  long long launches_at_start = 0;
+  std::vector<double> gather_bytes;  // per block column (timing only)
 
   template <typename T>
   submat_status alloc(T** p, size_t count, const char* what);
@@ -109,5 +127,25 @@ struct Plan {
   submat_status ns_simt(const Wave& wv, T* buf0, T* buf1, T* Y, double tol, double floor_thr,
                         cudaStream_t st, cudaError_t (*gemm)(const Args&, cudaStream_t));
 };
+
+template <typename T>
+submat_status Plan::alloc(T** p, size_t count, const char* what) {
+  void* q = nullptr;
+  SM_TRY(dev_alloc(&q, count * sizeof(T), what));
+  if (q) owned.push_back(q);
+  *p = static_cast<T*>(q);
+  return SUBMAT_OK;
+}
+
+template <typename T>
+submat_status Plan::put(T** p, const std::vector<T>& v, cudaStream_t st, const char* what) {
+  void* q = nullptr;
+  SM_TRY(dev_alloc(&q, v.size() * sizeof(T), what));
+  if (q) owned.push_back(q);
+  *p = static_cast<T*>(q);
+  if (!v.empty())
+    SM_CUDA(cudaMemcpyAsync(q, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return SUBMAT_OK;
+}
 
 }  // namespace submat

@@ -479,6 +479,7 @@ cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   k_tc_gemm<<<grid, 192, smem, st>>>(p);
+  count_launch();
   return cudaGetLastError();
 }
 

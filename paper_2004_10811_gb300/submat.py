@@ -47,7 +47,8 @@ class Options(C.Structure):
     _fields_ = [
         ("prec", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("beta_mode", C.c_int),
         ("symmetrize", C.c_int), ("workspace_cap_bytes", C.c_size_t),
-        ("refine_rounds", C.c_int), ("reserved", C.c_int * 8),
+        ("refine_rounds", C.c_int), ("timing", C.c_int), ("col_begin", C.c_int), ("col_end", C.c_int),
+        ("reserved", C.c_int * 5),
     ]
 
 
@@ -55,14 +56,20 @@ class Stats(C.Structure):
     _fields_ = [
         ("nsub", C.c_int32), ("n_min", C.c_int32), ("n_max", C.c_int32), ("waves", C.c_int32),
         ("iters_min", C.c_int32), ("iters_max", C.c_int32), ("not_converged", C.c_int32),
-        ("refine_rounds", C.c_int32), ("sum_n2", C.c_double), ("sum_n3", C.c_double),
+        ("refine_rounds", C.c_int32), ("refine_cg_iters", C.c_int32), ("refine_fallback", C.c_int32),
+        ("sum_n2", C.c_double), ("sum_n3", C.c_double),
         ("flops_ns", C.c_double), ("flops_refine", C.c_double), ("max_resid", C.c_double),
         ("ms_gather", C.c_double), ("ms_ns", C.c_double), ("ms_refine", C.c_double),
-        ("ms_scatter", C.c_double), ("workspace_bytes", C.c_size_t),
+        ("ms_scatter", C.c_double), ("workspace_bytes", C.c_size_t), ("launches", C.c_int64),
+        ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int32 * 4), ("kernel_work", C.c_double * 4),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if hasattr(v, "__len__") else v
+        return out
 
 
 _lib = None
@@ -139,7 +146,7 @@ class Plan:
 
     def __init__(self, block_sizes, row_ptr, col_idx, prec="fp64", tol=0.0, max_iter=0,
                  beta_mode=0, symmetrize=False, workspace_cap_bytes=0, refine_rounds=0,
-                 stream=None):
+                 timing=False, columns=None, stream=None):
         lib = load()
         self._lib = lib
         self.block_sizes = np.ascontiguousarray(block_sizes, dtype=np.int32)
@@ -154,6 +161,9 @@ class Plan:
         opt.symmetrize = int(bool(symmetrize))
         opt.workspace_cap_bytes = int(workspace_cap_bytes)
         opt.refine_rounds = int(refine_rounds)
+        opt.timing = int(bool(timing))
+        if columns is not None:
+            opt.col_begin, opt.col_end = int(columns[0]), int(columns[1])
         self.options = opt
         h = C.c_void_p()
         _check(lib.submat_plan_create(len(self.block_sizes), _ptr(self.block_sizes, C.c_int32),
