@@ -210,6 +210,35 @@ submat_status submat_get_stats(const submat_plan* plan, submat_stats* out);
 submat_status submat_get_sub_stats(const submat_plan* plan, int32_t* dims, int32_t* iters,
                                    double* resid, double* beta);
 
+/*
+ * Dense one-matrix evaluation that allocates nothing (the paper has no
+ * counterpart; it is a convenience of this library).
+ *
+ *   D = 1/2 (I - sign(K - mu I))  for one dense symmetric n x n matrix K,
+ *
+ * by the same scaled FP64 Newton-Schulz iteration and kernels as the FP64
+ * path, for callers that may not call cudaMalloc or cudaMallocHost: codes
+ * that reserve the whole device for their own memory pool, allocators that
+ * forbid foreign allocations, and time steps in which an allocation's
+ * implicit device synchronisation is not acceptable.
+ *   n         1 <= n <= SUBMAT_NOALLOC_MAX_N; larger n is rejected with
+ *             INVALID_ARG
+ *   K_dev     device double[n * n], row-major (caller-owned)
+ *   D_dev     device double[n * n], row-major (caller-owned output)
+ *   iters_out host int or NULL: Newton-Schulz iterations taken
+ * All scratch (6 MiB) is one file-scope device array that every GPU loading
+ * the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture on the device.  Every call shares the
+ * array and it keeps the previous call's contents, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race; serialise
+ * them.  The call synchronises `stream`.
+ * Returns OK, INVALID_ARG, NONFINITE, NOT_CONVERGED (D written), CUDA.
+ */
+#define SUBMAT_NOALLOC_MAX_N 512
+submat_status submat_dense_sign_noalloc(int n, const double* K_dev, double mu, double* D_dev,
+                                        int* iters_out, void* stream);
+
 /* Message of the last failure on this thread ("" if none). */
 const char* submat_last_error(void);
 

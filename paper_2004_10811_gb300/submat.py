@@ -28,7 +28,7 @@ EXPORTS = (
     "submat_options_default", "submat_plan_create", "submat_plan_destroy", "submat_sign",
     "submat_sign_host", "submat_trace", "submat_mu_search", "submat_sign_backward",
     "submat_plan_value_count", "submat_get_stats", "submat_get_sub_stats", "submat_last_error",
-    "submat_debug_tc_gemm",
+    "submat_debug_tc_gemm", "submat_dense_sign_noalloc",
 )
 
 
@@ -100,11 +100,12 @@ def load(path: str = LIB_PATH):
     lib.submat_get_sub_stats.argtypes = [vp, i32p, i32p, dp, dp]
     lib.submat_debug_tc_gemm.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, C.c_int,
                                          vp, vp, C.c_int, C.c_double, vp]
+    lib.submat_dense_sign_noalloc.argtypes = [C.c_int, vp, C.c_double, vp, C.POINTER(C.c_int), vp]
     lib.submat_last_error.argtypes = []
     lib.submat_last_error.restype = C.c_char_p
     for name in ("submat_plan_create", "submat_plan_destroy", "submat_sign", "submat_sign_host",
                  "submat_trace", "submat_mu_search", "submat_sign_backward", "submat_get_stats",
-                 "submat_get_sub_stats", "submat_debug_tc_gemm"):
+                 "submat_get_sub_stats", "submat_debug_tc_gemm", "submat_dense_sign_noalloc"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -295,3 +296,21 @@ def debug_tc_gemm(A_hi, B_hi, A_lo=None, B_lo=None, n=None, sym=False, res2=None
                                   int(bool(skip_arrive)), float(timeout_s), _stream(stream))
     _check(st, allow=(8,) if allow_timeout else ())
     return C_, STATUS[st]
+
+
+NOALLOC_MAX_N = 512
+
+
+def dense_sign_noalloc(K, mu, out=None, stream=None):
+    """D = 1/2 (I - sign(K - mu I)) for one dense n x n CUDA float64 matrix,
+    through the entry point that allocates no memory (n <= 512).
+    Returns (D, iterations)."""
+    import torch
+    lib = load()
+    n = int(K.shape[0])
+    if out is None:
+        out = torch.empty_like(K)
+    it = C.c_int()
+    _check(lib.submat_dense_sign_noalloc(n, _devptr(K, "K"), float(mu), _devptr(out, "D"),
+                                         C.byref(it), _stream(stream)))
+    return out, it.value
