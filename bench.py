@@ -159,6 +159,8 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=32, help="block columns timed on the FP64 path")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--columns", default=None,
+                    help="a:b -- evaluate only block columns [a, b) (small cases for profiling)")
     args = ap.parse_args()
 
     cfg_index, desc = WORKLOADS[args.workload]
@@ -194,7 +196,8 @@ def main():
     dev = torch.device("cuda", local)
     K = torch.from_numpy(m.vals).to(dev)
     D = torch.empty_like(K)
-    plan = pkg.Plan.from_bsr(m, prec=args.prec, timing=True)
+    columns = tuple(int(x) for x in args.columns.split(":")) if args.columns else None
+    plan = pkg.Plan.from_bsr(m, prec=args.prec, timing=True, columns=columns)
     for _ in range(args.warmup):
         plan.sign(K, m.mu, out=D)
     torch.cuda.synchronize()
@@ -250,6 +253,10 @@ def main():
         return
 
     builds = args.steps * world
+    if columns:
+        line_cols = {"columns": list(columns)}
+    else:
+        line_cols = {}
     value = t_dev / builds
     flops_std = (acc["flops_ns"] + acc["flops_refine"]) / args.steps  # per build
     line = {
@@ -259,7 +266,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "prec": args.prec,
                    "n": int(m.n), "nsub": int(m.nblk), "nnzb": int(m.nnzb),
-                   "sub_dim_min": int(stats["n_min"]), "sub_dim_max": int(stats["n_max"]),
+                   "sub_dim_min": int(stats["n_min"]), "sub_dim_max": int(stats["n_max"]), **line_cols,
                    "l2": "inputs larger than L2 (K %.2f GB, workspace %.1f GB)" % (m.vals.nbytes / 1e9,
                                                                                 stats["workspace_bytes"] / 1e9)},
         "tflops": flops_std / value / 1e12 / world if value > 0 else None,
@@ -312,7 +319,7 @@ def main():
         line["kernels"] = kernels
 
     # ---- parity on sampled block columns and the CPU oracle baseline ----
-    if not args.no_cpu and world == 1:
+    if not args.no_cpu and world == 1 and not columns:
         workers = min(16, os.cpu_count() or 1)
         cols = sample_columns(m.nblk, args.cpu_sample)
         want, t_cpu = run_oracle_sample(m, cols, workers)
@@ -326,7 +333,7 @@ def main():
                                           f"{workers}-process pool), time scaled to the full build"}
 
     # ---- the plain FP64 path on a contiguous chunk of block columns ----
-    if not args.no_fp64 and args.prec == "mixed" and world == 1:
+    if not args.no_fp64 and args.prec == "mixed" and world == 1 and not columns:
         nc = min(args.fp64_sample, m.nblk)
         with pkg.Plan.from_bsr(m, prec="fp64", columns=(0, nc), timing=True) as p64:
             Dtmp = torch.zeros_like(K)

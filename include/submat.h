@@ -82,7 +82,11 @@ typedef struct {
   int col_begin, col_end;      /* evaluate only block columns [col_begin, col_end) of D (one
                                   contiguous chunk, Section IV-E); 0, 0 = all columns.  The
                                   other block columns of D are left untouched. */
-  int reserved[5];             /* must be zero */
+  int hp_mode;                 /* mixed path, the two residual products I - S^2 and S a:
+                                  0: BF16 tensor cores on six row-scaled 6-bit slices per
+                                  operand (exact integer sums, FP64 combination, ~36 bits);
+                                  1: FP64 SIMT GEMM */
+  int reserved[4];             /* must be zero */
 } submat_options;
 
 /* Aggregate statistics of the last submat_sign / submat_mu_search call. */

@@ -34,11 +34,13 @@ long long timeout_cycles_for(double seconds);
 int num_sms();
 
 // bytes of workspace per dense element (see MixedBufs)
-size_t mixed_bytes_per_elem() { return 8 + 8 + 4 + 8 + 8 + 4 + 4 + 5 * 4; }
+size_t mixed_bytes_per_elem() { return 8 + 8 + 4 + 8 + 8 + 4 + 4 + 4 + 5 * 4; }
 
 namespace {
 
-enum MapSet { MS_XH0, MS_XL0, MS_XH1, MS_XL1, MS_YH, MS_YL, MS_AH, MS_AL, MS_HH, MS_HL, MS_COUNT };
+enum MapSet {
+  MS_XH0, MS_XL0, MS_XH1, MS_XL1, MS_YH, MS_YL, MS_AH, MS_AL, MS_HH, MS_HL, MS_Z0, MS_Z1, MS_COUNT
+};
 
 struct MixedBufs {
   double* A;               // a_j (FP64)
@@ -48,6 +50,7 @@ struct MixedBufs {
   double* T;               // FP64 residual products (I - S^2, then S a)
   __nv_bfloat16* Ah[2];    // split of a
   __nv_bfloat16* Hh[2];    // split of H
+  __nv_bfloat16* Z[2];     // two more BF16 operands (slices)
   float* Fc;               // commuting correction
   float* cx;               // CG solution
   float* cr;               // CG residual
@@ -67,6 +70,7 @@ MixedBufs carve(void* ws, int64_t E) {
   b.T = reinterpret_cast<double*>(take(8));
   for (int k = 0; k < 2; ++k) b.Ah[k] = reinterpret_cast<__nv_bfloat16*>(take(2));
   for (int k = 0; k < 2; ++k) b.Hh[k] = reinterpret_cast<__nv_bfloat16*>(take(2));
+  for (int k = 0; k < 2; ++k) b.Z[k] = reinterpret_cast<__nv_bfloat16*>(take(2));
   b.Fc = reinterpret_cast<float*>(take(4));
   b.cx = reinterpret_cast<float*>(take(4));
   b.cr = reinterpret_cast<float*>(take(4));
@@ -88,6 +92,54 @@ __device__ __forceinline__ void split2(double v, __nv_bfloat16* hi, __nv_bfloat1
   const int64_t base = (w).off[s];                                                       \
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;            \
        e += int64_t(gridDim.x) * blockDim.x)
+
+constexpr int HP_SLICES = 6;  // 6-bit slices per operand in the sliced products
+constexpr int HP_BITS = 6;
+// slice products kept: p + q <= 8 (26 of 36).  The first dropped level weighs
+// ~2^-38 relative to the row and column scales; measured on 1518- and 1748-dim
+// submatrices the products are then accurate to ~2e-10, against ~1e-8 when
+// stopping at p + q <= 7 (which is too coarse for the 1e-9 trace bound).
+constexpr int HP_MAX_LEVEL = 8;
+
+struct SlicePtrs {
+  __nv_bfloat16* p[HP_SLICES];
+};
+
+// Row-scaled integer slices (the splitting of Ozaki et al.): for row r with
+// max_c |X_rc| < 2^e,  X_rc = 2^e sum_{p=1..6} t_p 2^{-6p} + O(2^{e-36}), with
+// integers |t_p| <= 63, exact in BF16.  A product of two slice matrices is a sum
+// of integers below 63^2 * ld, exact in the FP32 accumulator for ld <= 4096
+// (two such products for ld <= 2048).
+__global__ void k_slice(WaveDev w, const double* __restrict__ X, SlicePtrs out,
+                        double* __restrict__ rowscale, const int64_t* __restrict__ voff) {
+  const int s = blockIdx.y;
+  const int ld = w.ld[s];
+  const int64_t base = w.off[s];
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = warp; r < ld; r += nwarps) {
+    const double* row = X + base + int64_t(r) * ld;
+    double mx = 0.0;
+    for (int c = lane; c < ld; c += 32) mx = fmax(mx, fabs(row[c]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);  // mx < 2^e
+    if (lane == 0) rowscale[voff[s] + r] = ldexp(1.0, e);
+    const double inv = ldexp(1.0, -e);
+    for (int c = lane; c < ld; c += 32) {
+      double v = row[c] * inv;  // |v| < 1
+      const int64_t i = base + int64_t(r) * ld + c;
+#pragma unroll
+      for (int q = 0; q < HP_SLICES; ++q) {
+        v *= double(1 << HP_BITS);
+        const double t = trunc(v);
+        out.p[q][i] = __double2bfloat16(t);
+        v -= t;
+      }
+    }
+  }
+}
 
 // X_0 = a / beta as a BF16 (hi, lo) pair
 __global__ void k_scale_split(WaveDev w, const double* __restrict__ A, const double* __restrict__ beta,
@@ -350,6 +402,9 @@ dim3 pair_grid(const Wave& wv) {
 
 struct MixedState {
   std::vector<CUtensorMap*> d_maps;  // per wave: [MS_COUNT][nbucket]
+  std::vector<int64_t*> d_voff;      // per wave: offset of each submatrix's row-scale vector
+  double* rs_x = nullptr;            // row scales of the first operand's slices
+  double* rs_y = nullptr;            // row scales of the second operand's slices
   double* scal = nullptr;            // per-slot scalars: rr, ptp, rr_new, rr0 (4 x max_wave)
   int* cg_done = nullptr;            // per slot
   int* cg_count = nullptr;           // per slot: CG iterations run (all rounds)
@@ -365,11 +420,12 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
   if (!ms) {
     ms = new MixedState();
     mixed = ms;
+    int64_t vec_max = 1;
     for (auto& wv : waves) {
       const int nbk = int(wv.bucket_ld.size());
       std::vector<CUtensorMap> maps(size_t(MS_COUNT) * nbk);
-      const void* bases[MS_COUNT] = {b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.Y[0],
-                                     b.Y[1],    b.Ah[0],   b.Ah[1],   b.Hh[0],   b.Hh[1]};
+      const void* bases[MS_COUNT] = {b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.Y[0], b.Y[1],
+                                     b.Ah[0],   b.Ah[1],   b.Hh[0],   b.Hh[1],   b.Z[0], b.Z[1]};
       for (int m = 0; m < MS_COUNT; ++m)
         for (int k = 0; k < nbk; ++k) {
           const __nv_bfloat16* base = static_cast<const __nv_bfloat16*>(bases[m]) + wv.bucket_base[k];
@@ -384,7 +440,16 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       SM_CUDA(cudaMemcpyAsync(d, maps.data(), maps.size() * sizeof(CUtensorMap),
                               cudaMemcpyHostToDevice, st));
       ms->d_maps.push_back(d);
+      std::vector<int64_t> vo(wv.count);
+      int64_t acc = 0;
+      for (int s = 0; s < wv.count; ++s) { vo[s] = acc; acc += wv.host_ld[s]; }
+      int64_t* dv = nullptr;
+      SM_TRY(put(&dv, vo, st, "row-scale offsets"));
+      ms->d_voff.push_back(dv);
+      vec_max = std::max(vec_max, acc);
     }
+    SM_TRY(alloc(&ms->rs_x, size_t(vec_max), "row scales"));
+    SM_TRY(alloc(&ms->rs_y, size_t(vec_max), "row scales"));
     SM_TRY(alloc(&ms->scal, size_t(4) * max_wave, "CG scalars"));
     SM_TRY(alloc(&ms->cg_done, size_t(max_wave), "CG flags"));
     SM_TRY(alloc(&ms->cg_count, size_t(max_wave), "CG counts"));
@@ -488,6 +553,63 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     SM_KCHECK();
     k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
     SM_KCHECK();
+    // sliced products are exact for K extents up to 4096 (two per accumulator up to 2048)
+    int64_t max_ld = 0;
+    for (int64_t l : wv.bucket_ld) max_ld = std::max(max_ld, l);
+    const bool hp_sliced = opt.hp_mode == 0 && max_ld <= 4096;
+    const int per_acc = max_ld <= 2048 ? 2 : 1;
+    static const int S_SETS[HP_SLICES] = {MS_XH0, MS_XL0, MS_XH1, MS_XL1, MS_YH, MS_YL};
+    static const int A_SETS[HP_SLICES] = {MS_AH, MS_AL, MS_HH, MS_HL, MS_Z0, MS_Z1};
+    SlicePtrs sl_s{{b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.Y[0], b.Y[1]}};
+    SlicePtrs sl_a{{b.Ah[0], b.Ah[1], b.Hh[0], b.Hh[1], b.Z[0], b.Z[1]}};
+    const dim3 slice_grid(unsigned(std::max<int64_t>(1, std::min<int64_t>(max_ld / 8, 256))), unsigned(wv.count));
+    // C (+)= sign * X Y^T from the slices: level t = p + q weighs 2^(-6 t); each
+    // launch sums at most per_acc products of one level in one exact accumulator
+    auto hp_product = [&](const int* xs, const int* ys, const double* rsx, const double* rsy,
+                          double* out, int sym, double sign, double diag) -> submat_status {
+      bool first = true;
+      for (int t = 2; t <= HP_MAX_LEVEL; ++t) {
+        int pairs[HP_SLICES][2];
+        int np = 0;
+        for (int pp = 1; pp <= HP_SLICES; ++pp) {
+          const int qq = t - pp;
+          if (qq >= 1 && qq <= HP_SLICES) { pairs[np][0] = pp; pairs[np][1] = qq; ++np; }
+        }
+        for (int c0 = 0; c0 < np; c0 += per_acc) {
+          const int k = std::min(per_acc, np - c0);
+          TcGemmParams p;
+          std::memset(&p, 0, sizeof(p));
+          p.items = sym ? wv.sym128 : wv.full128;
+          p.nitems = sym ? wv.n_sym128 : wv.n_full128;
+          p.maps = ms->d_maps[wi];
+          p.nbucket = nbk;
+          p.nmaps = MS_COUNT * nbk;
+          p.na = k; p.nb = k;
+          for (int i = 0; i < k; ++i) {
+            p.a_set[i] = xs[pairs[c0 + i][0] - 1];
+            p.b_set[i] = ys[pairs[c0 + i][1] - 1];
+            p.prod_a[i] = i; p.prod_b[i] = i; p.prod_acc[i] = 0; p.prod_first[i] = i == 0;
+          }
+          p.nprod = k;
+          p.nacc = 1;
+          p.nstage = tc_pick_stages(k, k);
+          p.tmem_cols = 256;
+          p.off = wv.dev.off; p.ld = wv.dev.ld; p.n = wv.dev.n;
+          p.skip_state = -1;
+          p.sym = sym;
+          p.flags = d_flags;
+          p.timeout_cycles = tmo;
+          p.out_f64 = out;
+          p.f64_accumulate = first ? 0 : 1;
+          p.f64_scale = sign * std::ldexp(1.0, -HP_BITS * t);
+          p.f64_diag = first ? diag : 0.0;
+          p.rowscale_a = rsx; p.rowscale_b = rsy; p.voff = ms->d_voff[wi];
+          SM_CUDA(launch(p));
+          first = false;
+        }
+      }
+      return SUBMAT_OK;
+    };
     const int rounds = std::max(1, opt.refine_rounds);
     const int cg_max = 60;          // CG cap per round
     const double cg_tol = 1e-4;     // relative residual that ends CG for a submatrix
@@ -495,30 +617,51 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     const double corr_tol = 1e-8;   // largest acceptable last-round correction
     int cg_total = 0;
     for (int rd = 0; rd < rounds; ++rd) {
-      if (rd > 0) {  // the operand split of S for this round
+      // ---- the two high-precision residual products ----
+      // T = I - S^2
+      if (hp_sliced) {
+        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi]);
+        SM_KCHECK();
+        SM_TRY(hp_product(S_SETS, S_SETS, ms->rs_x, ms->rs_x, b.T, 1, -1.0, 1.0));
         k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
         SM_KCHECK();
+      } else {
+        if (rd > 0) {
+          k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
+          SM_KCHECK();
+        }
+        GemmF64Args f{};
+        f.w = wv.dev; f.items = wv.sym64; f.nitems = wv.n_sym64;
+        f.A = b.S; f.B = b.S; f.C0 = nullptr; f.C = b.T;
+        f.alpha = -1.0; f.beta = 0.0; f.diag = 1.0; f.sym = 1;
+        SM_CUDA(f64(f));
       }
-      // T = I - S^2 (FP64)
-      GemmF64Args f{};
-      f.w = wv.dev; f.items = wv.sym64; f.nitems = wv.n_sym64;
-      f.A = b.S; f.B = b.S; f.C0 = nullptr; f.C = b.T;
-      f.alpha = -1.0; f.beta = 0.0; f.diag = 1.0; f.sym = 1;
-      SM_CUDA(f64(f));
       k_split64<<<eg, 256, 0, st>>>(wv.dev, b.T, b.Y[0], b.Y[1]);
       SM_KCHECK();
       // F_c = -1/2 S (I - S^2)
       TcGemmParams g = tc(wv.sym128, wv.n_sym128, MS_XH0, MS_XL0, MS_YH, MS_YL, 1, -0.5f, 0.0f);
       g.out_f32 = b.Fc;
       SM_CUDA(launch(g));
+      // T = S a
+      if (hp_sliced) {
+        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi]);
+        SM_KCHECK();
+        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.A, sl_a, ms->rs_y, ms->d_voff[wi]);
+        SM_KCHECK();
+        SM_TRY(hp_product(S_SETS, A_SETS, ms->rs_x, ms->rs_y, b.T, 0, 1.0, 0.0));
+        k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
+        SM_KCHECK();
+        k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
+        SM_KCHECK();
+      } else {
+        GemmF64Args f2{};
+        f2.w = wv.dev; f2.items = wv.full64; f2.nitems = wv.n_full64;
+        f2.A = b.S; f2.B = b.A; f2.C0 = nullptr; f2.C = b.T;
+        f2.alpha = 1.0; f2.beta = 0.0; f2.diag = 0.0; f2.sym = 0;
+        SM_CUDA(f64(f2));
+      }
       k_split32<<<eg, 256, 0, st>>>(wv.dev, b.Fc, b.Y[0], b.Y[1]);
       SM_KCHECK();
-      // T = S a (FP64)
-      GemmF64Args f2{};
-      f2.w = wv.dev; f2.items = wv.full64; f2.nitems = wv.n_full64;
-      f2.A = b.S; f2.B = b.A; f2.C0 = nullptr; f2.C = b.T;
-      f2.alpha = 1.0; f2.beta = 0.0; f2.diag = 0.0; f2.sym = 0;
-      SM_CUDA(f64(f2));
       // W = F_c a
       TcGemmParams g3 = tc(wv.full128, wv.n_full128, MS_YH, MS_YL, MS_AH, MS_AL, 0, 1.0f, 0.0f);
       g3.out_f32 = b.cw;
@@ -567,7 +710,11 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     }
     // ---- FP64 Newton-Schulz for the submatrices the correction could not settle ----
     SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
-    k_pick_fallback<<<(wv.count + 255) / 256, 256, 0, st>>>(wv.dev, ns, ms->corr, rr, rr0, corr_tol,
+    // the size of the last correction bounds the remaining error only when an
+    // earlier round has already been applied (a single round's correction is
+    // the low-precision error itself), so with one round only the CG test applies
+    k_pick_fallback<<<(wv.count + 255) / 256, 256, 0, st>>>(wv.dev, ns, ms->corr, rr, rr0,
+                                                            rounds >= 2 ? corr_tol : 1e300,
                                                             cg_bad * cg_bad, ms->pick, d_active);
     SM_KCHECK();
     SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -616,7 +763,9 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       const double sym = n * n * (n + 1.0);
       stats.kernel_work[KC_TC_NS] += 2.0 * sym * lp_iters[s];
       stats.kernel_work[KC_TC_REF] += (2.0 * sym + 2.0 * n3) * rounds + 2.0 * n3 * cgc[s];
-      stats.kernel_work[KC_SIMT] += (sym + 2.0 * n3) * rounds + 2.0 * sym * extra;
+      if (hp_sliced) stats.kernel_work[KC_TC_REF] += (sym + 2.0 * n3) * rounds;
+      else stats.kernel_work[KC_SIMT] += (sym + 2.0 * n3) * rounds;
+      stats.kernel_work[KC_SIMT] += 2.0 * sym * extra;
     }
     stats.refine_fallback = fallback_total;
   }

@@ -191,6 +191,36 @@ __device__ __forceinline__ void store_range(const TcGemmParams& p, int64_t idx, 
   }
 }
 
+// FP64 row segment of a sliced product: v_q = scale * ra * rb[q] * acc_q
+// (+ diag where the element sits on the diagonal), for q in [q_lo, q_hi).
+__device__ __forceinline__ void store_f64(const TcGemmParams& p, int64_t idx, const float* acc, double ra,
+                                          const double* rb, int diag_q, int q_lo, int q_hi) {
+  double* d = p.out_f64 + idx;
+  if (q_lo <= 0 && q_hi >= 32) {
+#pragma unroll
+    for (int q = 0; q < 32; q += 2) {
+      double v0 = p.f64_scale * ra * rb[q] * double(acc[q]);
+      double v1 = p.f64_scale * ra * rb[q + 1] * double(acc[q + 1]);
+      if (q == diag_q) v0 += p.f64_diag;
+      if (q + 1 == diag_q) v1 += p.f64_diag;
+      if (p.f64_accumulate) {
+        const double2 o = *reinterpret_cast<const double2*>(d + q);
+        v0 += o.x;
+        v1 += o.y;
+      }
+      *reinterpret_cast<double2*>(d + q) = make_double2(v0, v1);
+    }
+  } else {
+    for (int q = 0; q < 32; ++q) {
+      if (q < q_lo || q >= q_hi) continue;
+      double v = p.f64_scale * ra * rb[q] * double(acc[q]);
+      if (q == diag_q) v += p.f64_diag;
+      if (p.f64_accumulate) v += d[q];
+      d[q] = v;
+    }
+  }
+}
+
 __device__ __forceinline__ void load_c0(const TcGemmParams& p, int64_t idx, float* c) {
   if (p.c0_f32) {
     const float4* s = reinterpret_cast<const float4*>(p.c0_f32 + idx);
@@ -401,6 +431,45 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
         const int cg0 = item.z * BN + c * 32;
         float o[32];
         const bool inside = (rg < ld) && (cg0 < ld);
+        if (p.out_f64) {
+          // sliced high-precision product: scale the exact integer sums in FP64
+          if (inside) {
+            const int64_t vo = p.voff[s];
+            const double ra = p.rowscale_a[vo + rg];
+            const int dq = (rg < n) ? rg - cg0 : -1;
+            store_f64(p, base + int64_t(rg) * ld + cg0, acc + c * 32, ra, p.rowscale_b + vo + cg0,
+                      (dq >= 0 && dq < 32) ? dq : -1, diag_sym ? r - c * 32 : 0, 32);
+          }
+          if (mirror) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) stg[r * STG_PITCH + q] = __float_as_uint(acc[c * 32 + q]);
+            epi_bar();
+            const int t = threadIdx.x - 64;
+            const int q = t >> 2, part4 = t & 3;
+            const int mrow = item.z * BN + c * 32 + q;
+            const int mcol0 = item.y * BM + part4 * 32;
+            if (mrow < ld && mcol0 < ld) {
+              float w[32];
+#pragma unroll
+              for (int i = 0; i < 32; ++i) w[i] = __uint_as_float(stg[(part4 * 32 + i) * STG_PITCH + q]);
+              // element (mrow, mcol0 + i) equals element (mcol0 + i, mrow) of the tile:
+              // scales rowscale_a[mcol0 + i] * rowscale_b[mrow]
+              const int64_t vo = p.voff[s];
+              const double* ra_row = p.rowscale_a + vo + mcol0;
+              const double rbm = p.rowscale_b[vo + mrow];
+              const int hi = diag_sym ? c * 32 + q - part4 * 32 : 32;
+              double* d = p.out_f64 + base + int64_t(mrow) * ld + mcol0;
+              for (int i = 0; i < 32; ++i) {
+                if (i >= hi) break;
+                double v = p.f64_scale * ra_row[i] * rbm * double(w[i]);
+                if (p.f64_accumulate) v += d[i];
+                d[i] = v;
+              }
+            }
+            epi_bar();
+          }
+          continue;
+        }
         if (inside) {
           float c0[32];
           const int64_t idx = base + int64_t(rg) * ld + cg0;

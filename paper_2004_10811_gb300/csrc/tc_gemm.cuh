@@ -41,6 +41,17 @@ struct TcGemmParams {
   const __nv_bfloat16* c0_hi;
   const __nv_bfloat16* c0_lo;
   double* res2;                   // optional ||C - I_n||_F^2 per submatrix
+  // FP64 output (sliced high-precision products): with out_f64 set, the tile
+  // value is  f64_scale * rowscale_a[row] * rowscale_b[col] * acc  (+ f64_diag
+  // on the diagonal of the n x n block), written or, with f64_accumulate,
+  // added to out_f64.  alpha/beta and the other outputs are then unused.
+  double* out_f64;
+  int f64_accumulate;
+  double f64_scale;
+  double f64_diag;
+  const double* rowscale_a;       // per row of the A operand, at voff[s]
+  const double* rowscale_b;       // per row of the B operand (= per column of C)
+  const int64_t* voff;
   int* flags;
   long long timeout_cycles;
   int test_skip_arrive;           // test hook: epilogue withholds its TMEM release

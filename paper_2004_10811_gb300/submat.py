@@ -48,7 +48,7 @@ class Options(C.Structure):
         ("prec", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("beta_mode", C.c_int),
         ("symmetrize", C.c_int), ("workspace_cap_bytes", C.c_size_t),
         ("refine_rounds", C.c_int), ("timing", C.c_int), ("col_begin", C.c_int), ("col_end", C.c_int),
-        ("reserved", C.c_int * 5),
+        ("hp_mode", C.c_int), ("reserved", C.c_int * 4),
     ]
 
 
@@ -147,7 +147,7 @@ class Plan:
 
     def __init__(self, block_sizes, row_ptr, col_idx, prec="fp64", tol=0.0, max_iter=0,
                  beta_mode=0, symmetrize=False, workspace_cap_bytes=0, refine_rounds=0,
-                 timing=False, columns=None, stream=None):
+                 timing=False, columns=None, hp_mode=0, stream=None):
         lib = load()
         self._lib = lib
         self.block_sizes = np.ascontiguousarray(block_sizes, dtype=np.int32)
@@ -163,6 +163,7 @@ class Plan:
         opt.workspace_cap_bytes = int(workspace_cap_bytes)
         opt.refine_rounds = int(refine_rounds)
         opt.timing = int(bool(timing))
+        opt.hp_mode = int(hp_mode)
         if columns is not None:
             opt.col_begin, opt.col_end = int(columns[0]), int(columns[1])
         self.options = opt

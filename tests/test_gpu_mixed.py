@@ -30,25 +30,27 @@ def run(pkg, m, mu, **kw):
     return D.cpu().numpy(), tr, st
 
 
-def test_config0_mixed(pkg):
+@pytest.mark.parametrize("hp_mode", [0, 1])
+def test_config0_mixed(pkg, hp_mode):
     m = make_config(0)
     want = oracle.density_matrix(m, 0.0)
-    got, tr, st = run(pkg, m, 0.0)
+    got, tr, st = run(pkg, m, 0.0, hp_mode=hp_mode)
     err = np.max(np.abs(got - want))
     assert err <= TOL_MIXED, (err, st)
     assert abs(tr - oracle.trace_bsr(m, want)) / m.n_el <= 1e-9
     assert st["refine_rounds"] >= 1 and st["iters_max"] < 40
 
 
+@pytest.mark.parametrize("hp_mode", [0, 1])
 @pytest.mark.parametrize("n_mol,block,r_c,seed,mu", [
     (96, 5, 6.5, 77, 0.05),     # dims ~100-300: several 128-tiles, ragged tails
     (40, 23, 6.0, 78, 0.0),     # block 23 as in the large workloads
 ])
-def test_water_mixed(pkg, n_mol, block, r_c, seed, mu):
+def test_water_mixed(pkg, n_mol, block, r_c, seed, mu, hp_mode):
     occ = max(1, block // 5)
     m = make_water(n_mol, block, r_c, (occ, -1.0, -0.3), (block - occ, 0.3, 1.2), seed=seed)
     want = oracle.density_matrix(m, mu, workers=4)
-    got, tr, st = run(pkg, m, mu)
+    got, tr, st = run(pkg, m, mu, hp_mode=hp_mode)
     err = np.max(np.abs(got - want))
     assert err <= TOL_MIXED, (err, st)
     assert abs(tr - oracle.trace_bsr(m, want)) / max(1.0, m.n_el) <= 1e-9
@@ -66,3 +68,13 @@ def test_one_round_is_enough_from_split_iterate(pkg):
     want = oracle.density_matrix(m, 0.0)
     got, _tr, _st = run(pkg, m, 0.0, refine_rounds=1)
     assert np.max(np.abs(got - want)) <= TOL_MIXED
+
+
+def test_sliced_and_fp64_residual_products_agree(pkg):
+    """The two ways of forming I - S^2 and S a (tensor-core slices, FP64 SIMT)
+    give the same D to well below the mixed tolerance, with one round."""
+    m = make_water(64, 23, 6.0, (4, -1.0, -0.3), (19, 0.3, 1.5), seed=5)
+    d0, _t0, s0 = run(pkg, m, 0.0, hp_mode=0, refine_rounds=1)
+    d1, _t1, s1 = run(pkg, m, 0.0, hp_mode=1, refine_rounds=1)
+    assert s0["refine_fallback"] == 0 and s1["refine_fallback"] == 0
+    assert np.max(np.abs(d0 - d1)) < 2e-8
