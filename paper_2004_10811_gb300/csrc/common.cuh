@@ -145,4 +145,32 @@ struct GemmF32Args {
 };
 cudaError_t launch_gemm_f32(const GemmF32Args& a, cudaStream_t st);
 
+#ifdef __CUDACC__
+// FP64 -> FP32 by truncating the mantissa with integer operations (GB300's
+// FP64 pipe is ~60x slower than its FP32 pipe, so the bulk kernels avoid it).
+// Relative error < 2^-23; values below 2^-126 become 0.  Only used where the
+// result feeds a 16-bit split or another low-precision step.
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned sign = unsigned(b >> 63);
+  const int ex = int((b >> 52) & 0x7FF) - 1023;
+  if (ex < -126) return sign ? -0.0f : 0.0f;
+  if (ex > 127) return sign ? -3.402823466e38f : 3.402823466e38f;
+  const unsigned mant = unsigned((b >> 29) & 0x7FFFFFu);
+  return __uint_as_float((sign << 31) | (unsigned(ex + 127) << 23) | mant);
+}
+
+// FP32 -> FP64 exactly, with integer operations
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0) return 0.0;  // zero (subnormal floats do not occur here)
+  const unsigned long long b = (static_cast<unsigned long long>(u >> 31) << 63) |
+                               (static_cast<unsigned long long>(e - 127 + 1023) << 52) |
+                               (static_cast<unsigned long long>(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double(static_cast<long long>(b));
+}
+
+#endif
+
 }  // namespace submat

@@ -79,10 +79,14 @@ MixedBufs carve(void* ws, int64_t E) {
   return b;
 }
 
-__device__ __forceinline__ void split2(double v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
-  const __nv_bfloat16 h = __double2bfloat16(v);
+__device__ __forceinline__ void split2f(float v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
   hi[i] = h;
-  lo[i] = __double2bfloat16(v - double(__bfloat162float(h)));
+  lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__device__ __forceinline__ void split2(double v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
+  split2f(d2f_trunc(v), hi, lo, i);
 }
 
 #define FOR_SUB_ELEMS(w)                                                                 \
@@ -111,41 +115,68 @@ struct SlicePtrs {
 // of integers below 63^2 * ld, exact in the FP32 accumulator for ld <= 4096
 // (two such products for ld <= 2048).
 __global__ void k_slice(WaveDev w, const double* __restrict__ X, SlicePtrs out,
-                        double* __restrict__ rowscale, const int64_t* __restrict__ voff) {
+                        int* __restrict__ rowexp, const int64_t* __restrict__ voff) {
   const int s = blockIdx.y;
   const int ld = w.ld[s];
   const int64_t base = w.off[s];
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const unsigned long long* Xb = reinterpret_cast<const unsigned long long*>(X);
   for (int r = warp; r < ld; r += nwarps) {
-    const double* row = X + base + int64_t(r) * ld;
-    double mx = 0.0;
-    for (int c = lane; c < ld; c += 32) mx = fmax(mx, fabs(row[c]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);  // mx < 2^e
-    if (lane == 0) rowscale[voff[s] + r] = ldexp(1.0, e);
-    const double inv = ldexp(1.0, -e);
+    const unsigned long long* row = Xb + base + int64_t(r) * ld;
+    // the largest |x| of the row, compared as bit patterns
+    unsigned long long mb = 0;
+    for (int c = lane; c < ld; c += 32) mb = max(mb, row[c] & 0x7FFFFFFFFFFFFFFFull);
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    const int e = mb ? int(mb >> 52) - 1023 + 1 : 0;  // max |x| < 2^e
+    if (lane == 0) rowexp[voff[s] + r] = e;
     for (int c = lane; c < ld; c += 32) {
-      double v = row[c] * inv;  // |v| < 1
+      const unsigned long long b = row[c];
+      const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+      const int ex = int(a >> 52) - 1023;
+      // fixed = trunc(|x| 2^(36 - e)) = mantissa * 2^(ex - 16 - e), ex < e
+      unsigned long long fixed = 0;
+      const int sh = e - ex + 16;  // right shift, >= 17
+      if ((a >> 52) != 0 && sh < 64)
+        fixed = ((a & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh;
+      const bool neg = (b >> 63) != 0;
       const int64_t i = base + int64_t(r) * ld + c;
 #pragma unroll
       for (int q = 0; q < HP_SLICES; ++q) {
-        v *= double(1 << HP_BITS);
-        const double t = trunc(v);
-        out.p[q][i] = __double2bfloat16(t);
-        v -= t;
+        const int d = int((fixed >> (HP_BITS * (HP_SLICES - 1 - q))) & ((1u << HP_BITS) - 1));
+        out.p[q][i] = __int2bfloat16_rn(neg ? -d : d);
       }
     }
+  }
+}
+
+// T = sign * I * 2^(e_row + f_col - 6 L) + diag * I_n   (I: the exact int64 sum)
+__global__ void k_hp_finalize(WaveDev w, double* __restrict__ T, const int* __restrict__ ex,
+                              const int* __restrict__ ey, const int64_t* __restrict__ voff,
+                              double sign, double diag) {
+  const int s = blockIdx.y;
+  const int ld = w.ld[s];
+  const int n = w.n[s];
+  const int64_t base = w.off[s];
+  const int64_t vo = voff[s];
+  long long* I = reinterpret_cast<long long*>(T);
+  const int64_t total = int64_t(ld) * ld;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int r = int(e / ld), c = int(e - int64_t(r) * ld);
+    const int k = ex[vo + r] + ey[vo + c] - HP_BITS * HP_MAX_LEVEL;
+    double v = sign * ldexp(double(I[base + e]), k);
+    if (r == c && r < n) v += diag;
+    T[base + e] = v;
   }
 }
 
 // X_0 = a / beta as a BF16 (hi, lo) pair
 __global__ void k_scale_split(WaveDev w, const double* __restrict__ A, const double* __restrict__ beta,
                               __nv_bfloat16* xh, __nv_bfloat16* xl) {
-  const double ib = 1.0 / beta[blockIdx.y];
-  FOR_SUB_ELEMS(w) split2(A[base + e] * ib, xh, xl, base + e);
+  const float ib = float(1.0 / beta[blockIdx.y]);
+  FOR_SUB_ELEMS(w) split2f(d2f_trunc(A[base + e]) * ib, xh, xl, base + e);
 }
 
 // Bring every final iterate to parity 0 and widen it: S = hi + lo (FP64).
@@ -158,7 +189,7 @@ __global__ void k_widen(WaveDev w, const int* __restrict__ par, __nv_bfloat16* x
     __nv_bfloat16 h = one ? x1h[i] : x0h[i];
     __nv_bfloat16 l = one ? x1l[i] : x0l[i];
     if (one) { x0h[i] = h; x0l[i] = l; }
-    S[i] = double(__bfloat162float(h)) + double(__bfloat162float(l));
+    S[i] = f2d_exact(__bfloat162float(h) + __bfloat162float(l));  // exact: exponents 8+ apart
   }
 }
 
@@ -167,7 +198,7 @@ __global__ void k_split64(WaveDev w, const double* __restrict__ src, __nv_bfloat
 }
 
 __global__ void k_split32(WaveDev w, const float* __restrict__ src, __nv_bfloat16* hi, __nv_bfloat16* lo) {
-  FOR_SUB_ELEMS(w) split2(double(src[base + e]), hi, lo, base + e);
+  FOR_SUB_ELEMS(w) split2f(src[base + e], hi, lo, base + e);
 }
 
 // For a 32x32 tile pair (a, b), a <= b, with P = S a (FP64) and W = F_c a (FP32):
@@ -198,9 +229,10 @@ __global__ void k_comm(WaveDev w, const double* __restrict__ P, const float* __r
       for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
         const int64_t i = base + int64_t(ta * 32 + rr) * ld + tb * 32 + threadIdx.x;
         const double p = P[i], pt = tp[threadIdx.x][rr];
-        const double wv = W[i], wt = tw[threadIdx.x][rr];
-        split2((p - pt) - (wv - wt), mh, ml, i);
-        split2(0.5 * (p + pt), hh, hl, i);
+        const float wv = W[i], wt = tw[threadIdx.x][rr];
+        // p - pt cancels to O(delta): the one FP64 operation; the rest in FP32
+        split2f(d2f_trunc(p - pt) - (wv - wt), mh, ml, i);
+        split2f(0.5f * (d2f_trunc(p) + d2f_trunc(pt)), hh, hl, i);
       }
     }
   }
@@ -217,7 +249,7 @@ __global__ void k_cg_sym(WaveDev w, float* __restrict__ W, const float* __restri
   const int64_t base = w.off[s];
   const int T = ld / 32;
   const int npair = T * (T + 1) / 2;
-  double part = 0.0;
+  float part = 0.0f;
   for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
     int a = 0, rem = pi;
     while (rem >= T - a) { rem -= T - a; ++a; }
@@ -232,18 +264,18 @@ __global__ void k_cg_sym(WaveDev w, float* __restrict__ W, const float* __restri
       const int64_t i1 = base + int64_t(a * 32 + rr) * ld + b * 32 + threadIdx.x;
       const float v1 = ta_[rr][threadIdx.x] + tb_[threadIdx.x][rr];
       W[i1] = v1;
-      part += double(Pd[i1]) * v1;
+      part = fmaf(Pd[i1], v1, part);
       if (a != b) {
         const int64_t i2 = base + int64_t(b * 32 + rr) * ld + a * 32 + threadIdx.x;
         const float v2 = tb_[rr][threadIdx.x] + ta_[threadIdx.x][rr];
         W[i2] = v2;
-        part += double(Pd[i2]) * v2;
+        part = fmaf(Pd[i2], v2, part);
       }
     }
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-  if ((threadIdx.x & 31) == 0) red[warp] = part;
+  if ((threadIdx.x & 31) == 0) red[warp] = double(part);
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     double t = 0.0;
@@ -252,9 +284,9 @@ __global__ void k_cg_sym(WaveDev w, float* __restrict__ W, const float* __restri
   }
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
+__device__ __forceinline__ double block_sum(float v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = double(v);
   __syncthreads();
   double t = 0.0;
   if (threadIdx.x == 0)
@@ -273,13 +305,13 @@ __global__ void k_cg_update(WaveDev w, float* __restrict__ X, float* __restrict_
   if (blockIdx.x == 0 && threadIdx.x == 0) ++cg_count[blockIdx.y];
   const double den = ptp[blockIdx.y];
   const float alpha = (den > 0.0 && rr[blockIdx.y] > 0.0) ? float(rr[blockIdx.y] / den) : 0.0f;
-  double part = 0.0;
+  float part = 0.0f;
   FOR_SUB_ELEMS(w) {
     const int64_t i = base + e;
     X[i] = fmaf(alpha, Pd[i], X[i]);
     const float r = fmaf(-alpha, TP[i], R[i]);
     R[i] = r;
-    part += double(r) * r;
+    part = fmaf(r, r, part);
   }
   const double t = block_sum(part, red);
   if (threadIdx.x == 0) atomicAdd(&rr_new[blockIdx.y], t);
@@ -296,7 +328,7 @@ __global__ void k_cg_dir(WaveDev w, const float* __restrict__ R, float* __restri
     const int64_t i = base + e;
     const float p = fmaf(beta, Pd[i], R[i]);
     Pd[i] = p;
-    split2(double(p), ph, pl, i);
+    split2f(p, ph, pl, i);
   }
 }
 
@@ -304,14 +336,14 @@ __global__ void k_cg_dir(WaveDev w, const float* __restrict__ R, float* __restri
 __global__ void k_cg_init(WaveDev w, float* __restrict__ X, const float* __restrict__ R,
                           float* __restrict__ Pd, double* rr, __nv_bfloat16* ph, __nv_bfloat16* pl) {
   __shared__ double red[32];
-  double part = 0.0;
+  float part = 0.0f;
   FOR_SUB_ELEMS(w) {
     const int64_t i = base + e;
     const float r = R[i];
     X[i] = 0.0f;
     Pd[i] = r;
-    split2(double(r), ph, pl, i);
-    part += double(r) * r;
+    split2f(r, ph, pl, i);
+    part = fmaf(r, r, part);
   }
   const double t = block_sum(part, red);
   if (threadIdx.x == 0) atomicAdd(&rr[blockIdx.y], t);
@@ -336,15 +368,15 @@ __global__ void k_cg_check(int nsub, const double* rr, const double* rr0, int* c
 __global__ void k_apply(WaveDev w, double* __restrict__ S, const float* __restrict__ Fc,
                         const float* __restrict__ Fa, unsigned long long* corr) {
   __shared__ double red[32];
-  double mx = 0.0;
+  float mx = 0.0f;
   FOR_SUB_ELEMS(w) {
     const int64_t i = base + e;
-    const double f = double(Fc[i]) + double(Fa[i]);
-    S[i] = S[i] - f;
-    mx = fmax(mx, fabs(f));
+    const float f = Fc[i] + Fa[i];
+    S[i] = S[i] - f2d_exact(f);
+    mx = fmaxf(mx, fabsf(f));
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = double(mx);
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -403,8 +435,8 @@ dim3 pair_grid(const Wave& wv) {
 struct MixedState {
   std::vector<CUtensorMap*> d_maps;  // per wave: [MS_COUNT][nbucket]
   std::vector<int64_t*> d_voff;      // per wave: offset of each submatrix's row-scale vector
-  double* rs_x = nullptr;            // row scales of the first operand's slices
-  double* rs_y = nullptr;            // row scales of the second operand's slices
+  int* rs_x = nullptr;               // row exponents of the first operand's slices
+  int* rs_y = nullptr;               // row exponents of the second operand's slices
   double* scal = nullptr;            // per-slot scalars: rr, ptp, rr_new, rr0 (4 x max_wave)
   int* cg_done = nullptr;            // per slot
   int* cg_count = nullptr;           // per slot: CG iterations run (all rounds)
@@ -565,7 +597,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     const dim3 slice_grid(unsigned(std::max<int64_t>(1, std::min<int64_t>(max_ld / 8, 256))), unsigned(wv.count));
     // C (+)= sign * X Y^T from the slices: level t = p + q weighs 2^(-6 t); each
     // launch sums at most per_acc products of one level in one exact accumulator
-    auto hp_product = [&](const int* xs, const int* ys, const double* rsx, const double* rsy,
+    auto hp_product = [&](const int* xs, const int* ys, const int* ex, const int* ey,
                           double* out, int sym, double sign, double diag) -> submat_status {
       bool first = true;
       for (int t = 2; t <= HP_MAX_LEVEL; ++t) {
@@ -599,20 +631,21 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
           p.sym = sym;
           p.flags = d_flags;
           p.timeout_cycles = tmo;
-          p.out_f64 = out;
+          p.out_i64 = reinterpret_cast<long long*>(out);
+          p.i64_shift = HP_BITS * (HP_MAX_LEVEL - t);
           p.f64_accumulate = first ? 0 : 1;
-          p.f64_scale = sign * std::ldexp(1.0, -HP_BITS * t);
-          p.f64_diag = first ? diag : 0.0;
-          p.rowscale_a = rsx; p.rowscale_b = rsy; p.voff = ms->d_voff[wi];
           SM_CUDA(launch(p));
           first = false;
         }
       }
+      k_hp_finalize<<<eg, 256, 0, st>>>(wv.dev, out, ex, ey, ms->d_voff[wi], sign, diag);
+      SM_KCHECK();
       return SUBMAT_OK;
     };
     const int rounds = std::max(1, opt.refine_rounds);
     const int cg_max = 60;          // CG cap per round
-    const double cg_tol = 1e-4;     // relative residual that ends CG for a submatrix
+    const double cg_tol = 1e-4;     // relative residual that ends CG for a submatrix (round 1)
+    const double cg_tol_later = 1e-2;  // later rounds correct an O(1e-9) error: 1e-2 suffices
     const double cg_bad = 1e-2;     // above this after cg_max the submatrix falls back
     const double corr_tol = 1e-8;   // largest acceptable last-round correction
     int cg_total = 0;
@@ -696,8 +729,9 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         cg_total += 1;
         if ((it + 1) % 4 == 0) {
           SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
+          const double tol_r = rd == 0 ? cg_tol : cg_tol_later;
           k_cg_check<<<(wv.count + 255) / 256, 256, 0, st>>>(wv.count, rr, rr0, ms->cg_done,
-                                                             cg_tol * cg_tol, d_active);
+                                                             tol_r * tol_r, d_active);
           SM_KCHECK();
           SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
           SM_CUDA(cudaStreamSynchronize(st));

@@ -211,6 +211,7 @@ __device__ __forceinline__ void store_f64(const TcGemmParams& p, int64_t idx, co
       *reinterpret_cast<double2*>(d + q) = make_double2(v0, v1);
     }
   } else {
+#pragma unroll
     for (int q = 0; q < 32; ++q) {
       if (q < q_lo || q >= q_hi) continue;
       double v = p.f64_scale * ra * rb[q] * double(acc[q]);
@@ -431,6 +432,58 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
         const int cg0 = item.z * BN + c * 32;
         float o[32];
         const bool inside = (rg < ld) && (cg0 < ld);
+        if (p.out_i64) {
+          // exact integer sums of slice products, accumulated in 64-bit integers
+          const long long mul = 1LL << p.i64_shift;
+          if (inside) {
+            long long* d = p.out_i64 + base + int64_t(rg) * ld + cg0;
+            const int q_lo = diag_sym ? r - c * 32 : 0;
+            if (q_lo <= 0) {
+#pragma unroll
+              for (int q = 0; q < 32; q += 2) {
+                long long v0 = (long long)__float2int_rn(acc[c * 32 + q]) * mul;
+                long long v1 = (long long)__float2int_rn(acc[c * 32 + q + 1]) * mul;
+                if (p.f64_accumulate) {
+                  const longlong2 o = *reinterpret_cast<const longlong2*>(d + q);
+                  v0 += o.x;
+                  v1 += o.y;
+                }
+                *reinterpret_cast<longlong2*>(d + q) = make_longlong2(v0, v1);
+              }
+            } else {
+#pragma unroll
+              for (int q = 0; q < 32; ++q) {
+                if (q >= q_lo) {
+                  long long v = (long long)__float2int_rn(acc[c * 32 + q]) * mul;
+                  if (p.f64_accumulate) v += d[q];
+                  d[q] = v;
+                }
+              }
+            }
+          }
+          if (mirror) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) stg[r * STG_PITCH + q] = __float_as_uint(acc[c * 32 + q]);
+            epi_bar();
+            const int t = threadIdx.x - 64;
+            const int q = t >> 2, part4 = t & 3;
+            const int mrow = item.z * BN + c * 32 + q;
+            const int mcol0 = item.y * BM + part4 * 32;
+            if (mrow < ld && mcol0 < ld) {
+              const int hi = diag_sym ? c * 32 + q - part4 * 32 : 32;
+              long long* d = p.out_i64 + base + int64_t(mrow) * ld + mcol0;
+#pragma unroll
+              for (int i = 0; i < 32; ++i) {
+                if (i >= hi) continue;
+                long long v = (long long)__float2int_rn(__uint_as_float(stg[(part4 * 32 + i) * STG_PITCH + q])) * mul;
+                if (p.f64_accumulate) v += d[i];
+                d[i] = v;
+              }
+            }
+            epi_bar();
+          }
+          continue;
+        }
         if (p.out_f64) {
           // sliced high-precision product: scale the exact integer sums in FP64
           if (inside) {
@@ -459,8 +512,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
               const double rbm = p.rowscale_b[vo + mrow];
               const int hi = diag_sym ? c * 32 + q - part4 * 32 : 32;
               double* d = p.out_f64 + base + int64_t(mrow) * ld + mcol0;
+#pragma unroll
               for (int i = 0; i < 32; ++i) {
-                if (i >= hi) break;
+                if (i >= hi) continue;
                 double v = p.f64_scale * ra_row[i] * rbm * double(w[i]);
                 if (p.f64_accumulate) v += d[i];
                 d[i] = v;
@@ -482,12 +536,14 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
             o[q] = v;
           }
           if (p.res2) {
+            float pc = 0.0f;
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
               const int cg = cg0 + q;
-              const double e = double(o[q]) - ((rg == cg && rg < n) ? 1.0 : 0.0);
-              part += e * e;
+              const float e = o[q] - ((rg == cg && rg < n) ? 1.0f : 0.0f);
+              pc = fmaf(e, e, pc);
             }
+            part += double(pc);
           }
           if (diag_sym) store_range(p, idx, o, r - c * 32, 32);
           else store_row(p, idx, o);

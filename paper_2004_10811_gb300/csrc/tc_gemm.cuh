@@ -52,6 +52,11 @@ struct TcGemmParams {
   const double* rowscale_a;       // per row of the A operand, at voff[s]
   const double* rowscale_b;       // per row of the B operand (= per column of C)
   const int64_t* voff;
+  // Exact integer output (sliced products): with out_i64 set, the tile value is
+  // the integer accumulator times 2^i64_shift, written or (f64_accumulate)
+  // added to out_i64; row/column scales are applied later in FP64.
+  long long* out_i64;
+  int i64_shift;
   int* flags;
   long long timeout_cycles;
   int test_skip_arrive;           // test hook: epilogue withholds its TMEM release
