@@ -808,9 +808,4 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
 
 void free_mixed(void* state) { delete static_cast<MixedState*>(state); }
 
-submat_status Plan::backward(const double*, double, const double*, double*, double*, cudaStream_t) {
-  set_error("adjoint not built yet");
-  return SUBMAT_ERR_UNSUPPORTED;
-}
-
 }  // namespace submat

@@ -151,6 +151,111 @@ static int64_t find_block(const std::vector<int64_t>& rp, const std::vector<int3
   return int64_t(it - ci.begin());
 }
 
+// Split the evaluated block columns into waves whose dense buffers (bpe bytes
+// per element) fit `cap`, and build each wave's maps and work lists.
+submat_status Plan::build_waves(size_t bpe, size_t cap, std::vector<Wave>& waves, cudaStream_t st) {
+  std::vector<int64_t> ld_of(nblk);
+  for (int j = 0; j < nblk; ++j) ld_of[j] = (nsub[j] + 63) / 64 * 64;
+  waves.clear();
+  {
+    int first = col_lo;
+    while (first < col_hi) {
+      int64_t elems = 0;
+      int cnt = 0;
+      while (first + cnt < col_hi) {
+        const int64_t e = ld_of[first + cnt] * ld_of[first + cnt];
+        if (cnt > 0 && size_t(elems + e) * bpe > cap) break;
+        if (cnt == 0 && size_t(e) * bpe > cap) {
+          set_error("one submatrix (dim %d) needs %zu bytes > workspace cap %zu", nsub[first],
+                    size_t(e) * bpe, cap);
+          return SUBMAT_ERR_OOM;
+        }
+        elems += e;
+        ++cnt;
+        if (cnt >= 65535) break;  // grid.y limit of the scaling kernel
+      }
+      Wave wv;
+      wv.first = first;
+      wv.count = cnt;
+      wv.elems = elems;
+      waves.push_back(wv);
+      first += cnt;
+    }
+  }
+  // per-wave maps and work lists.  Dense buffers are grouped into size
+  // buckets (equal ld) laid out as [count][ld][ld], so that each bucket is one
+  // 3D tensor for the TMA loads of the tensor-core GEMM.
+  for (auto& wv : waves) {
+    std::vector<int32_t> sub(wv.count), ld(wv.count), nn(wv.count);
+    std::vector<int64_t> off(wv.count);
+    std::vector<int2> gitems;
+    std::vector<int4> sym64, full64, sym128, full128;
+    std::vector<int64_t> lds;
+    for (int s = 0; s < wv.count; ++s) lds.push_back(ld_of[wv.first + s]);
+    std::sort(lds.begin(), lds.end());
+    lds.erase(std::unique(lds.begin(), lds.end()), lds.end());
+    if (lds.size() > 255) { set_error("more than 255 size buckets in a wave"); return SUBMAT_ERR_UNSUPPORTED; }
+    wv.bucket_ld.assign(lds.begin(), lds.end());
+    wv.bucket_count.assign(lds.size(), 0);
+    std::vector<int> bucket_of(wv.count), slot_of(wv.count);
+    for (int s = 0; s < wv.count; ++s) {
+      const int b = int(std::lower_bound(lds.begin(), lds.end(), ld_of[wv.first + s]) - lds.begin());
+      bucket_of[s] = b;
+      slot_of[s] = wv.bucket_count[b]++;
+    }
+    wv.bucket_base.assign(lds.size(), 0);
+    int64_t o = 0;
+    for (size_t b = 0; b < lds.size(); ++b) {
+      wv.bucket_base[b] = o;
+      o += int64_t(wv.bucket_count[b]) * lds[b] * lds[b];
+    }
+    wv.max_ld2 = 0;
+    for (int s = 0; s < wv.count; ++s) {
+      const int j = wv.first + s;
+      sub[s] = j;
+      ld[s] = int32_t(ld_of[j]);
+      nn[s] = nsub[j];
+      off[s] = wv.bucket_base[bucket_of[s]] + int64_t(slot_of[s]) * ld_of[j] * ld_of[j];
+      wv.max_ld2 = std::max(wv.max_ld2, ld_of[j] * ld_of[j]);
+      const int nbj = int(row_ptr[j + 1] - row_ptr[j]);
+      for (int t = 0; t < nbj; ++t) gitems.push_back(make_int2(s, t));
+      const int T = int(ld_of[j] / 64);
+      for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+          full64.push_back(make_int4(s, a, b, 0));
+          if (a <= b) sym64.push_back(make_int4(s, a, b, 0));
+        }
+      const int T2 = int((ld_of[j] + 127) / 128);
+      const int tag = bucket_of[s] | (slot_of[s] << 8);
+      for (int a = 0; a < T2; ++a)
+        for (int b = 0; b < T2; ++b) {
+          full128.push_back(make_int4(s, a, b, tag));
+          if (a <= b) sym128.push_back(make_int4(s, a, b, tag));
+        }
+    }
+    int32_t* d_sub; int32_t* d_ld; int32_t* d_n; int64_t* d_off;
+    SM_TRY(put(&d_sub, sub, st, "wave submatrices"));
+    SM_TRY(put(&d_ld, ld, st, "wave ld"));
+    SM_TRY(put(&d_n, nn, st, "wave dims"));
+    SM_TRY(put(&d_off, off, st, "wave offsets"));
+    wv.dev = WaveDev{wv.count, d_sub, d_off, d_ld, d_n};
+    SM_TRY(put(&wv.gather_items, gitems, st, "gather items"));
+    wv.n_gather = int(gitems.size());
+    SM_TRY(put(&wv.sym64, sym64, st, "tile list"));
+    wv.n_sym64 = int(sym64.size());
+    SM_TRY(put(&wv.full64, full64, st, "tile list"));
+    wv.n_full64 = int(full64.size());
+    SM_TRY(put(&wv.sym128, sym128, st, "tile list"));
+    wv.n_sym128 = int(sym128.size());
+    SM_TRY(put(&wv.full128, full128, st, "tile list"));
+    wv.n_full128 = int(full128.size());
+    wv.host_ld = ld;
+    wv.host_n = nn;
+    wv.host_off = off;
+  }
+  return SUBMAT_OK;
+}
+
 submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, const int32_t* ci_,
                           const submat_options* o, cudaStream_t st) {
   nblk = nblk_;
@@ -237,112 +342,14 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
     SM_CUDA(cudaMemGetInfo(&fre, &tot));
     cap = size_t(double(fre) * 0.8);
   }
-  std::vector<int64_t> ld_of(nblk);
-  for (int j = 0; j < nblk; ++j) ld_of[j] = (nsub[j] + 63) / 64 * 64;
-  waves.clear();
   col_lo = opt.col_end > opt.col_begin ? opt.col_begin : 0;
   col_hi = opt.col_end > opt.col_begin ? opt.col_end : nblk;
-  {
-    int first = col_lo;
-    while (first < col_hi) {
-      int64_t elems = 0;
-      int cnt = 0;
-      while (first + cnt < col_hi) {
-        const int64_t e = ld_of[first + cnt] * ld_of[first + cnt];
-        if (cnt > 0 && size_t(elems + e) * bpe > cap) break;
-        if (cnt == 0 && size_t(e) * bpe > cap) {
-          set_error("one submatrix (dim %d) needs %zu bytes > workspace cap %zu", nsub[first],
-                    size_t(e) * bpe, cap);
-          return SUBMAT_ERR_OOM;
-        }
-        elems += e;
-        ++cnt;
-        if (cnt >= 65535) break;  // grid.y limit of the scaling kernel
-      }
-      Wave wv;
-      wv.first = first;
-      wv.count = cnt;
-      wv.elems = elems;
-      waves.push_back(wv);
-      first += cnt;
-    }
-  }
+  SM_TRY(build_waves(bpe, cap, waves, st));
   int64_t max_elems = 0;
   max_wave = 0;
   for (auto& wv : waves) {
     max_elems = std::max(max_elems, wv.elems);
     max_wave = std::max(max_wave, wv.count);
-  }
-  // per-wave maps and work lists.  Dense buffers are grouped into size
-  // buckets (equal ld) laid out as [count][ld][ld], so that each bucket is one
-  // 3D tensor for the TMA loads of the tensor-core GEMM.
-  for (auto& wv : waves) {
-    std::vector<int32_t> sub(wv.count), ld(wv.count), nn(wv.count);
-    std::vector<int64_t> off(wv.count);
-    std::vector<int2> gitems;
-    std::vector<int4> sym64, full64, sym128, full128;
-    std::vector<int64_t> lds;
-    for (int s = 0; s < wv.count; ++s) lds.push_back(ld_of[wv.first + s]);
-    std::sort(lds.begin(), lds.end());
-    lds.erase(std::unique(lds.begin(), lds.end()), lds.end());
-    if (lds.size() > 255) { set_error("more than 255 size buckets in a wave"); return SUBMAT_ERR_UNSUPPORTED; }
-    wv.bucket_ld.assign(lds.begin(), lds.end());
-    wv.bucket_count.assign(lds.size(), 0);
-    std::vector<int> bucket_of(wv.count), slot_of(wv.count);
-    for (int s = 0; s < wv.count; ++s) {
-      const int b = int(std::lower_bound(lds.begin(), lds.end(), ld_of[wv.first + s]) - lds.begin());
-      bucket_of[s] = b;
-      slot_of[s] = wv.bucket_count[b]++;
-    }
-    wv.bucket_base.assign(lds.size(), 0);
-    int64_t o = 0;
-    for (size_t b = 0; b < lds.size(); ++b) {
-      wv.bucket_base[b] = o;
-      o += int64_t(wv.bucket_count[b]) * lds[b] * lds[b];
-    }
-    wv.max_ld2 = 0;
-    for (int s = 0; s < wv.count; ++s) {
-      const int j = wv.first + s;
-      sub[s] = j;
-      ld[s] = int32_t(ld_of[j]);
-      nn[s] = nsub[j];
-      off[s] = wv.bucket_base[bucket_of[s]] + int64_t(slot_of[s]) * ld_of[j] * ld_of[j];
-      wv.max_ld2 = std::max(wv.max_ld2, ld_of[j] * ld_of[j]);
-      const int nbj = int(row_ptr[j + 1] - row_ptr[j]);
-      for (int t = 0; t < nbj; ++t) gitems.push_back(make_int2(s, t));
-      const int T = int(ld_of[j] / 64);
-      for (int a = 0; a < T; ++a)
-        for (int b = 0; b < T; ++b) {
-          full64.push_back(make_int4(s, a, b, 0));
-          if (a <= b) sym64.push_back(make_int4(s, a, b, 0));
-        }
-      const int T2 = int((ld_of[j] + 127) / 128);
-      const int tag = bucket_of[s] | (slot_of[s] << 8);
-      for (int a = 0; a < T2; ++a)
-        for (int b = 0; b < T2; ++b) {
-          full128.push_back(make_int4(s, a, b, tag));
-          if (a <= b) sym128.push_back(make_int4(s, a, b, tag));
-        }
-    }
-    int32_t* d_sub; int32_t* d_ld; int32_t* d_n; int64_t* d_off;
-    SM_TRY(put(&d_sub, sub, st, "wave submatrices"));
-    SM_TRY(put(&d_ld, ld, st, "wave ld"));
-    SM_TRY(put(&d_n, nn, st, "wave dims"));
-    SM_TRY(put(&d_off, off, st, "wave offsets"));
-    wv.dev = WaveDev{wv.count, d_sub, d_off, d_ld, d_n};
-    SM_TRY(put(&wv.gather_items, gitems, st, "gather items"));
-    wv.n_gather = int(gitems.size());
-    SM_TRY(put(&wv.sym64, sym64, st, "tile list"));
-    wv.n_sym64 = int(sym64.size());
-    SM_TRY(put(&wv.full64, full64, st, "tile list"));
-    wv.n_full64 = int(full64.size());
-    SM_TRY(put(&wv.sym128, sym128, st, "tile list"));
-    wv.n_sym128 = int(sym128.size());
-    SM_TRY(put(&wv.full128, full128, st, "tile list"));
-    wv.n_full128 = int(full128.size());
-    wv.host_ld = ld;
-    wv.host_n = nn;
-    wv.host_off = off;
   }
   // workspace
   ws_elems = max_elems;
@@ -350,15 +357,11 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
   SM_TRY(dev_alloc(&ws, ws_bytes, "workspace"));
   if (ws) owned.push_back(ws);
   // Newton-Schulz state (per wave slot) and per-block results
-  SM_TRY(alloc(&ns.state, max_wave, "ns state"));
-  SM_TRY(alloc(&ns.iters, max_wave, "ns iters"));
-  SM_TRY(alloc(&ns.par, max_wave, "ns parity"));
-  SM_TRY(alloc(&ns.notconv, max_wave, "ns flags"));
-  SM_TRY(alloc(&ns.res2, max_wave, "ns residual"));
-  SM_TRY(alloc(&ns.rprev, max_wave, "ns residual"));
-  SM_TRY(alloc(&ns.beta, max_wave, "ns beta"));
-  SM_TRY(alloc(&ns.gersh, max_wave, "ns gersh"));
-  SM_TRY(alloc(&ns.fro2, max_wave, "ns fro"));
+  {
+    const int want = max_wave;
+    max_wave = 0;
+    SM_TRY(grow_ns_state(want));
+  }
   SM_TRY(alloc(&d_flags, 4, "flags"));
   SM_TRY(alloc(&d_active, 1, "active count"));
   SM_TRY(alloc(&d_trpart, size_t(nblk), "trace partials"));
@@ -387,6 +390,22 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
   res_beta.assign(nblk, 0.0);
   res_notconv.assign(nblk, 0);
   SM_CUDA(cudaStreamSynchronize(st));
+  return SUBMAT_OK;
+}
+
+// Per-slot Newton-Schulz state for waves of up to `count` submatrices.
+submat_status Plan::grow_ns_state(int count) {
+  if (count <= max_wave && ns.state) return SUBMAT_OK;
+  SM_TRY(alloc(&ns.state, count, "ns state"));
+  SM_TRY(alloc(&ns.iters, count, "ns iters"));
+  SM_TRY(alloc(&ns.par, count, "ns parity"));
+  SM_TRY(alloc(&ns.notconv, count, "ns flags"));
+  SM_TRY(alloc(&ns.res2, count, "ns residual"));
+  SM_TRY(alloc(&ns.rprev, count, "ns residual"));
+  SM_TRY(alloc(&ns.beta, count, "ns beta"));
+  SM_TRY(alloc(&ns.gersh, count, "ns gersh"));
+  SM_TRY(alloc(&ns.fro2, count, "ns fro"));
+  max_wave = std::max(max_wave, count);
   return SUBMAT_OK;
 }
 

@@ -89,6 +89,13 @@ struct Plan {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<void*> owned;
   void* mixed = nullptr;       // mixed-path state (mixed.cu)
+  // adjoint: its own waves and workspace (six dense buffers per submatrix)
+  std::vector<Wave> bwaves;
+  int max_bwave = 0;
+  void* bws = nullptr;
+  int64_t bws_elems = 0;
+  double* d_dnpart = nullptr;
+  double dn_acc = 0.0;
 
   // results of the last evaluation (per global block column)
   std::vector<int> res_iters, res_notconv;
@@ -123,6 +130,11 @@ struct Plan {
   submat_status sign_fp64(const double* K, double mu, double* D, cudaStream_t st);
   submat_status sign_fp32(const double* K, double mu, double* D, cudaStream_t st);
   submat_status sign_mixed(const double* K, double mu, double* D, cudaStream_t st);
+  submat_status build_waves(size_t bpe, size_t cap, std::vector<Wave>& out, cudaStream_t st);
+  template <typename T>
+  submat_status backward_wave(Wave& wv, const double* K, double mu, const double* Dbar, double* Kbar,
+                              double* dn_part, void* bws, cudaStream_t st);
+  submat_status grow_ns_state(int count);
   template <typename T, typename Args>
   submat_status ns_simt(const Wave& wv, T* buf0, T* buf1, T* Y, double tol, double floor_thr,
                         cudaStream_t st, cudaError_t (*gemm)(const Args&, cudaStream_t));

@@ -1,0 +1,66 @@
+"""mu search (canonical adaptation, Section IV-G) on the GPU against the
+oracle's Algorithm 1 on stored eigendecompositions."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_config
+from synth.water import make_water
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2004_10811_gb300 as p
+    return p
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_target_on_a_plateau_is_met(pkg, prec):
+    """N_el equal to the electron count inside the gap: the search lands in
+    the gap from a start outside it and meets the relative tolerance."""
+    import torch
+    m = make_config(0)
+    dec = oracle.decompose_all(m, 0.0)
+    n_target = oracle.n_elec_alg1(dec, 0.0)
+    K = torch.from_numpy(m.vals).cuda()
+    with pkg.Plan.from_bsr(m, prec=prec) as plan:
+        mu, D, status = plan.mu_search(K, n_target, mu0=0.9, tol=1e-9, max_steps=80)
+        tr = plan.trace(D)
+    assert status == "OK"
+    assert abs(tr - n_target) <= 1e-9 * n_target
+    # the oracle agrees that this mu is in the plateau
+    assert abs(oracle.n_elec_alg1(dec, mu) - n_target) <= 1e-9 * n_target
+
+
+def test_target_between_plateaus_reports_the_step(pkg):
+    """N_el = 96 while the gap plateau holds 96 + O(1e-8): at T = 0 the count
+    jumps over N_el at an eigenvalue of some submatrix.  The GPU search
+    certifies the jump (MU_NO_ROOT) at the location Algorithm 1 finds."""
+    import torch
+    m = make_config(0)
+    dec = oracle.decompose_all(m, 0.0)
+    plateau = oracle.n_elec_alg1(dec, 0.0)
+    assert plateau > m.n_el  # the truncation error of the method puts it above 96
+    K = torch.from_numpy(m.vals).cuda()
+    with pkg.Plan.from_bsr(m, prec="fp64") as plan:
+        mu, _D, status = plan.mu_search(K, m.n_el, mu0=0.0, tol=1e-12, max_steps=80)
+    assert status == "MU_NO_ROOT"
+    mu_o, _n, _steps, (lo, hi) = oracle.mu_search_alg1(dec, m.n_el, -3.0, 3.0, tol=1e-11)
+    assert abs(mu - mu_o) < 1e-8
+    assert oracle.n_elec_alg1(dec, mu - 1e-7) < m.n_el < oracle.n_elec_alg1(dec, mu + 1e-7)
+
+
+def test_trace_parity_at_fixed_mu(pkg):
+    """|Tr D_gpu - Tr D_oracle| / N_el <= 1e-9 at the same mu."""
+    import torch
+    m = make_water(48, 6, 6.0, (3, -1.0, -0.3), (3, 0.3, 1.0), seed=12)
+    for mu in (-0.1, 0.0, 0.2):
+        want = oracle.trace_bsr(m, oracle.density_matrix(m, mu))
+        with pkg.Plan.from_bsr(m, prec="mixed") as plan:
+            D = plan.sign(torch.from_numpy(m.vals).cuda(), mu)
+            tr = plan.trace(D)
+        assert abs(tr - want) / m.n_el <= 1e-9
