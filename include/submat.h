@@ -71,12 +71,18 @@ typedef struct {
                                   0 selects 1e-14 for FP64, 1e-6 for FP32, 2e-5 for the
                                   BF16x3 stage of the mixed path */
   int max_iter;                /* Newton-Schulz iteration cap; 0 selects 100 */
-  int beta_mode;               /* X_0 = a / beta.  0: beta = min(max row abs-sum, ||a||_F)
-                                  (a guaranteed bound on the spectral radius);
-                                  1: beta = 1.05 x a power-iteration estimate */
+  int beta_mode;               /* X_0 = a / beta.  0 (default): beta = 1.05 x a 20-step
+                                  power-iteration estimate of the spectral radius when that
+                                  is below the bound of mode 1 (any beta > rho / sqrt(3)
+                                  converges; a tighter beta saves iterations);
+                                  1: beta = min(max row abs-sum, ||a||_F) >= rho(a) only */
   int symmetrize;              /* 1: return (D + D^T) / 2 on the pattern; 0: column-assembled D */
   size_t workspace_cap_bytes;  /* device workspace cap; 0 = 80 % of free memory at plan time */
-  int refine_rounds;           /* mixed path: correction rounds; 0 selects 2 */
+  int refine_rounds;           /* mixed path: correction rounds; 0 selects 1.  With one
+                                  round a submatrix is accepted when its Lyapunov solve
+                                  converged (which bounds |a|/gap); with two or more the last
+                                  correction must be below 1e-8.  Others are re-solved in
+                                  FP64 (submat_stats.refine_fallback). */
   int timing;                  /* 1: time every GEMM launch with CUDA events (submat_stats
                                   kernel_* fields); adds one event pair per launch */
   int col_begin, col_end;      /* evaluate only block columns [col_begin, col_end) of D (one

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -105,6 +106,18 @@ cudaError_t launch_trace(const PatternDev& g, int nblk, const double* D, double*
 cudaError_t launch_symmetrize_impl(const PatternDev& g, int64_t nnzb, const double* Din,
                                    double* Dout, const int64_t* rowof, cudaStream_t st);
 cudaError_t launch_check_finite(const double* v, int64_t count, int* flags, cudaStream_t st);
+// power iteration: rho[s] ~ rho(X_s) (a lower bound converging to it)
+cudaError_t launch_power_bf16(const WaveDev& w, const __nv_bfloat16* X, int iters, const int* state,
+                              double* rho, int max_ld, cudaStream_t st);
+cudaError_t launch_power_f64(const WaveDev& w, const double* X, int iters, const int* state, double* rho,
+                             int max_ld, cudaStream_t st);
+cudaError_t launch_power_f32(const WaveDev& w, const float* X, int iters, const int* state, double* rho,
+                             int max_ld, cudaStream_t st);
+cudaError_t launch_rescale_f64(const WaveDev& w, double* X, const double* rho, double* beta,
+                               const int* state, int64_t max_ld2, cudaStream_t st);
+cudaError_t launch_reset_rprev(const WaveDev& w, NsStateDev ns, cudaStream_t st);
+cudaError_t launch_rescale_f32(const WaveDev& w, float* X, const double* rho, double* beta,
+                               const int* state, int64_t max_ld2, cudaStream_t st);
 
 // ---- FP64 GEMM (gemm_f64.cu) ----
 // C = alpha * A * B + beta * C0 on every listed 64x64 tile (s, ti, tj);

@@ -2,6 +2,8 @@
 // Newton-Schulz bookkeeping, extraction (scatter) and the trace.
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+
 #include <atomic>
 #include <cmath>
 #include <cstdint>
@@ -285,7 +287,136 @@ __global__ void k_check_finite(const double* __restrict__ v, int64_t count, int*
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, FLAG_NONFINITE);
 }
 
+// ||X v|| / ||v|| after `iters` power steps: a lower bound on rho(X) that
+// converges to it.  One CTA per submatrix; v lives in shared memory.
+// Deterministic start vector (a fixed hash of the index).
+template <typename T>
+__global__ void __launch_bounds__(1024) k_power(WaveDev w, const T* __restrict__ X, int iters,
+                                                const int* __restrict__ state, double* __restrict__ rho) {
+  extern __shared__ float pv[];  // v[ld], y[ld]
+  __shared__ float red[32];
+  const int s = blockIdx.x;
+  if (state && state[s] == ST_DONE) { if (threadIdx.x == 0) rho[s] = 0.0; return; }
+  const int ld = w.ld[s];
+  const int n = w.n[s];
+  const T* Xs = X + w.off[s];
+  float* v = pv;
+  float* y = pv + ld;
+  for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+    unsigned h = unsigned(i) * 2654435761u + 12345u;
+    h ^= h >> 15;
+    v[i] = i < n ? 0.5f + float(h & 0xFFFF) / 65536.0f : 0.0f;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  float est = 0.0f;
+  for (int it = 0; it < iters; ++it) {
+    float yy = 0.0f, vv = 0.0f;
+    for (int r = warp; r < n; r += nw) {
+      const T* row = Xs + int64_t(r) * ld;
+      float acc = 0.0f;
+      for (int c = lane; c < n; c += 32) acc = fmaf(float(row[c]), v[c], acc);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) y[r] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { yy = fmaf(y[i], y[i], yy); vv = fmaf(v[i], v[i], vv); }
+    for (int o = 16; o > 0; o >>= 1) { yy += __shfl_xor_sync(0xffffffffu, yy, o); vv += __shfl_xor_sync(0xffffffffu, vv, o); }
+    if (lane == 0) { red[warp] = yy; }
+    __syncthreads();
+    float ysum = 0.0f;
+    for (int q = 0; q < nw; ++q) ysum += red[q];
+    __syncthreads();
+    if (lane == 0) red[warp] = vv;
+    __syncthreads();
+    float vsum = 0.0f;
+    for (int q = 0; q < nw; ++q) vsum += red[q];
+    est = vsum > 0.0f ? sqrtf(ysum / vsum) : 0.0f;
+    const float inv = ysum > 0.0f ? rsqrtf(ysum) : 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = y[i] * inv;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rho[s] = double(est);
+}
+
 }  // namespace
+
+static dim3 scale_grid(const WaveDev& w, int64_t max_ld2) {
+  int64_t bx = (max_ld2 + 256 * 8 - 1) / (256 * 8);
+  if (bx > 512) bx = 512;
+  if (bx < 1) bx = 1;
+  return dim3(unsigned(bx), unsigned(w.nsub));
+}
+
+template <typename T>
+static cudaError_t power_impl(const WaveDev& w, const T* X, int iters, const int* state, double* rho,
+                              int max_ld, cudaStream_t st) {
+  const size_t smem = size_t(2 * max_ld) * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_power<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  k_power<T><<<w.nsub, 1024, smem, st>>>(w, X, iters, state, rho);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_power_bf16(const WaveDev& w, const __nv_bfloat16* X, int iters, const int* state,
+                              double* rho, int max_ld, cudaStream_t st) {
+  return power_impl(w, X, iters, state, rho, max_ld, st);
+}
+cudaError_t launch_power_f64(const WaveDev& w, const double* X, int iters, const int* state, double* rho,
+                             int max_ld, cudaStream_t st) {
+  return power_impl(w, X, iters, state, rho, max_ld, st);
+}
+cudaError_t launch_power_f32(const WaveDev& w, const float* X, int iters, const int* state, double* rho,
+                             int max_ld, cudaStream_t st) {
+  return power_impl(w, X, iters, state, rho, max_ld, st);
+}
+
+// X <- f_s X with f_s = 1 / (1.05 rho_s) when that tightens the scale; beta_s
+// follows.  rho_s is the power estimate of rho(X) (X = a / beta_s).
+template <typename T>
+__global__ void k_rescale(WaveDev w, T* __restrict__ X, const double* __restrict__ rho,
+                          double* __restrict__ beta, const int* __restrict__ state) {
+  const int s = blockIdx.y;
+  if (state && state[s] == ST_DONE) return;
+  const double r = rho[s];
+  if (!(r > 0.0) || r * 1.05 >= 1.0) return;  // keep the guaranteed bound
+  const double f = 1.0 / (1.05 * r);
+  if (threadIdx.x == 0 && blockIdx.x == 0) beta[s] = beta[s] / f;
+  const int ld = w.ld[s];
+  const int64_t total = int64_t(ld) * ld;
+  const int64_t off = w.off[s];
+  const T fs = T(f);
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x)
+    X[off + e] = X[off + e] * fs;
+}
+
+cudaError_t launch_rescale_f64(const WaveDev& w, double* X, const double* rho, double* beta,
+                               const int* state, int64_t max_ld2, cudaStream_t st) {
+  k_rescale<double><<<scale_grid(w, max_ld2), 256, 0, st>>>(w, X, rho, beta, state);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_rescale_f32(const WaveDev& w, float* X, const double* rho, double* beta,
+                               const int* state, int64_t max_ld2, cudaStream_t st) {
+  k_rescale<float><<<scale_grid(w, max_ld2), 256, 0, st>>>(w, X, rho, beta, state);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_reset_rprev(WaveDev w, NsStateDev ns) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < w.nsub) ns.rprev[s] = 1e300;
+}
+
+cudaError_t launch_reset_rprev(const WaveDev& w, NsStateDev ns, cudaStream_t st) {
+  k_reset_rprev<<<(w.nsub + 255) / 256, 256, 0, st>>>(w, ns);
+  count_launch();
+  return cudaGetLastError();
+}
 
 static std::atomic<long long> g_launches{0};
 void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -310,13 +441,6 @@ cudaError_t launch_beta(const WaveDev& w, NsStateDev ns, int beta_mode, cudaStre
   k_beta<<<(w.nsub + 255) / 256, 256, 0, st>>>(w, ns, beta_mode);
   count_launch();
   return cudaGetLastError();
-}
-
-static dim3 scale_grid(const WaveDev& w, int64_t max_ld2) {
-  int64_t bx = (max_ld2 + 256 * 8 - 1) / (256 * 8);
-  if (bx > 512) bx = 512;
-  if (bx < 1) bx = 1;
-  return dim3(unsigned(bx), unsigned(w.nsub));
 }
 
 cudaError_t launch_scale_f64(const WaveDev& w, const double* A, double* X, const double* beta,

@@ -179,6 +179,23 @@ __global__ void k_scale_split(WaveDev w, const double* __restrict__ A, const dou
   FOR_SUB_ELEMS(w) split2f(d2f_trunc(A[base + e]) * ib, xh, xl, base + e);
 }
 
+// X <- f X on the split pair (re-split), f = 1 / (1.05 rho) when it tightens
+// the scale; beta follows
+__global__ void k_rescale_split(WaveDev w, __nv_bfloat16* xh, __nv_bfloat16* xl, const double* rho,
+                                double* beta, const int* state) {
+  const int sb = blockIdx.y;
+  if (state[sb] == ST_DONE) return;
+  const double r = rho[sb];
+  if (!(r > 0.0) || r * 1.05 >= 1.0) return;
+  const double f = 1.0 / (1.05 * r);
+  if (threadIdx.x == 0 && blockIdx.x == 0) beta[sb] = beta[sb] / f;
+  const float ff = float(f);
+  FOR_SUB_ELEMS(w) {
+    const int64_t i = base + e;
+    split2f((__bfloat162float(xh[i]) + __bfloat162float(xl[i])) * ff, xh, xl, i);
+  }
+}
+
 // Bring every final iterate to parity 0 and widen it: S = hi + lo (FP64).
 __global__ void k_widen(WaveDev w, const int* __restrict__ par, __nv_bfloat16* x0h, __nv_bfloat16* x0l,
                         const __nv_bfloat16* __restrict__ x1h, const __nv_bfloat16* __restrict__ x1l,
@@ -549,6 +566,13 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     const dim3 eg = elem_grid(wv);
     k_scale_split<<<eg, 256, 0, st>>>(wv.dev, b.A, ns.beta, b.X[0][0], b.X[0][1]);
     SM_KCHECK();
+    if (opt.beta_mode == 0) {
+      // tighter scale: beta = 1.05 x a power estimate of rho(a) (fewer iterations)
+      SM_CUDA(launch_power_bf16(wv.dev, b.X[0][0], kPowerIters, ns.state, ns.rprev, max_ld(wv), st));
+      k_rescale_split<<<eg, 256, 0, st>>>(wv.dev, b.X[0][0], b.X[0][1], ns.rprev, ns.beta, ns.state);
+      SM_KCHECK();
+      SM_CUDA(launch_reset_rprev(wv.dev, ns, st));
+    }
     SM_CUDA(cudaEventRecord(ev[1], st));
 
     // ---- BF16x3 Newton-Schulz on the tensor cores ----
@@ -747,9 +771,12 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     // the size of the last correction bounds the remaining error only when an
     // earlier round has already been applied (a single round's correction is
     // the low-precision error itself), so with one round only the CG test applies
-    k_pick_fallback<<<(wv.count + 255) / 256, 256, 0, st>>>(wv.dev, ns, ms->corr, rr, rr0,
-                                                            rounds >= 2 ? corr_tol : 1e300,
-                                                            cg_bad * cg_bad, ms->pick, d_active);
+    // With one round, CG reaching cg_tol within cg_max iterations bounds
+    // |a|/gap (<~ 150), so the remaining error delta^2 |a|/gap + delta cg_tol is
+    // below ~2e-8 for delta <= 1e-5: accept then, with a delta cap of 1e-4.
+    k_pick_fallback<<<(wv.count + 255) / 256, 256, 0, st>>>(
+        wv.dev, ns, ms->corr, rr, rr0, rounds >= 2 ? corr_tol : 1e-4,
+        rounds >= 2 ? cg_bad * cg_bad : cg_tol * cg_tol * 1.0001, ms->pick, d_active);
     SM_KCHECK();
     SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     SM_CUDA(cudaStreamSynchronize(st));

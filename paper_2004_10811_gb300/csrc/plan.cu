@@ -413,6 +413,12 @@ submat_status Plan::grow_ns_state(int count) {
 // sign evaluation
 // ---------------------------------------------------------------------------
 
+int max_ld(const Wave& wv) {
+  int64_t m = 64;
+  for (int64_t l : wv.bucket_ld) m = std::max(m, l);
+  return int(m);
+}
+
 submat_status Plan::read_flags(cudaStream_t st, int* out) {
   SM_CUDA(cudaMemcpyAsync(h_pinned, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
   SM_CUDA(cudaStreamSynchronize(st));
@@ -502,6 +508,11 @@ submat_status Plan::sign_fp64(const double* K, double mu, double* D, cudaStream_
     SM_CUDA(cudaEventRecord(ev[0], st));
     SM_TRY(gather_wave(wv, K, mu, B0, st));
     SM_CUDA(launch_scale_f64(wv.dev, B0, B0, ns.beta, wv.max_ld2, st));
+    if (opt.beta_mode == 0) {
+      SM_CUDA(launch_power_f64(wv.dev, B0, kPowerIters, ns.state, ns.rprev, max_ld(wv), st));
+      SM_CUDA(launch_rescale_f64(wv.dev, B0, ns.rprev, ns.beta, ns.state, wv.max_ld2, st));
+      SM_CUDA(launch_reset_rprev(wv.dev, ns, st));
+    }
     SM_CUDA(cudaEventRecord(ev[1], st));
     SM_TRY((ns_simt<double, GemmF64Args>(wv, B0, B1, Y, tol_eff, 1e-9, st, launch_gemm_f64)));
     SM_CUDA(cudaEventRecord(ev[2], st));
@@ -522,6 +533,11 @@ submat_status Plan::sign_fp32(const double* K, double mu, double* D, cudaStream_
     SM_CUDA(cudaEventRecord(ev[0], st));
     SM_TRY(gather_wave(wv, K, mu, A, st));
     SM_CUDA(launch_scale_f32(wv.dev, A, B0, ns.beta, wv.max_ld2, st));
+    if (opt.beta_mode == 0) {
+      SM_CUDA(launch_power_f32(wv.dev, B0, kPowerIters, ns.state, ns.rprev, max_ld(wv), st));
+      SM_CUDA(launch_rescale_f32(wv.dev, B0, ns.rprev, ns.beta, ns.state, wv.max_ld2, st));
+      SM_CUDA(launch_reset_rprev(wv.dev, ns, st));
+    }
     SM_CUDA(cudaEventRecord(ev[1], st));
     SM_TRY((ns_simt<float, GemmF32Args>(wv, B0, B1, Y, tol_eff, 1e-4, st, launch_gemm_f32)));
     SM_CUDA(cudaEventRecord(ev[2], st));
@@ -689,7 +705,7 @@ submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int
       return SUBMAT_ERR_INVALID_ARG;
     }
     if (o.max_iter == 0) o.max_iter = 100;
-    if (o.refine_rounds == 0) o.refine_rounds = 2;
+    if (o.refine_rounds == 0) o.refine_rounds = 1;
     submat_status s = submat::validate_pattern_public(nblk, block_sizes, row_ptr, col_idx);
     if (s != SUBMAT_OK) return s;
     std::unique_ptr<submat_plan> p(new submat_plan());

@@ -15,6 +15,7 @@ submat_status validate_pattern_public(int nblk, const int32_t* bs, const int64_t
                                       const int32_t* ci);
 const char* last_error();
 size_t mixed_bytes_per_elem();
+constexpr int kPowerIters = 20;  // power steps of the spectral estimate
 void free_mixed(void* state);
 
 struct Wave {
@@ -54,6 +55,8 @@ struct KernelTimer {
 };
 
 enum KernelClass { KC_TC_NS = 0, KC_TC_REF = 1, KC_SIMT = 2, KC_GATHER = 3 };
+
+int max_ld(const Wave& wv);
 
 struct Plan {
   ~Plan();
