@@ -151,6 +151,37 @@ __global__ void k_slice(WaveDev w, const double* __restrict__ X, SlicePtrs out,
   }
 }
 
+// (+-) I * 2^k as a double with integer operations only: round-to-nearest of
+// the 64-bit integer to 53 bits, exponent set directly (k within the normal
+// range for the values produced here).
+__device__ __forceinline__ double i64_to_f64_scaled(long long I, int k, bool negate) {
+  if (I == 0) return 0.0;
+  unsigned long long sign = 0;
+  unsigned long long a = static_cast<unsigned long long>(I);
+  if (I < 0) { sign = 1; a = 0ull - a; }
+  if (negate) sign ^= 1;
+  const int lz = __clzll(static_cast<long long>(a));
+  const int msb = 63 - lz;              // value = a * 2^k, a in [2^msb, 2^(msb+1))
+  unsigned long long mant;
+  int ex = msb + k;
+  if (msb <= 52) {
+    mant = a << (52 - msb);
+  } else {
+    const int sh = msb - 52;
+    const unsigned long long rem = a & ((1ull << sh) - 1);
+    const unsigned long long half = 1ull << (sh - 1);
+    mant = a >> sh;
+    if (rem > half || (rem == half && (mant & 1))) {
+      ++mant;
+      if (mant >> 53) { mant >>= 1; ++ex; }
+    }
+  }
+  if (ex + 1023 <= 0) return 0.0;  // below the normal range: flush
+  const unsigned long long bits = (sign << 63) | (static_cast<unsigned long long>(ex + 1023) << 52) |
+                                  (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
 // T = sign * I * 2^(e_row + f_col - 6 L) + diag * I_n   (I: the exact int64 sum)
 __global__ void k_hp_finalize(WaveDev w, double* __restrict__ T, const int* __restrict__ ex,
                               const int* __restrict__ ey, const int64_t* __restrict__ voff,
@@ -166,7 +197,7 @@ __global__ void k_hp_finalize(WaveDev w, double* __restrict__ T, const int* __re
        e += int64_t(gridDim.x) * blockDim.x) {
     const int r = int(e / ld), c = int(e - int64_t(r) * ld);
     const int k = ex[vo + r] + ey[vo + c] - HP_BITS * HP_MAX_LEVEL;
-    double v = sign * ldexp(double(I[base + e]), k);
+    double v = i64_to_f64_scaled(I[base + e], k, sign < 0.0);
     if (r == c && r < n) v += diag;
     T[base + e] = v;
   }
@@ -679,7 +710,9 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       if (hp_sliced) {
         k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi]);
         SM_KCHECK();
-        SM_TRY(hp_product(S_SETS, S_SETS, ms->rs_x, ms->rs_x, b.T, 1, -1.0, 1.0));
+        // all tiles: the integer sums are exact, so the result is exactly
+        // symmetric without the mirror pass (which costs more than the tiles)
+        SM_TRY(hp_product(S_SETS, S_SETS, ms->rs_x, ms->rs_x, b.T, 0, -1.0, 1.0));
         k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
         SM_KCHECK();
       } else {
