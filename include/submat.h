@@ -92,7 +92,10 @@ typedef struct {
                                   0: BF16 tensor cores on six row-scaled 6-bit slices per
                                   operand (exact integer sums, FP64 combination, ~36 bits);
                                   1: FP64 SIMT GEMM */
-  int reserved[4];             /* must be zero */
+  int tile_n_ns;               /* tensor-core output tile width in the Newton-Schulz phase:
+                                  0 = chosen per wave, or 128 / 256 */
+  int tile_n_corr;             /* the same for the correction phase (0 = 128, measured best) */
+  int reserved[2];             /* must be zero */
 } submat_options;
 
 /* Aggregate statistics of the last submat_sign / submat_mu_search call. */

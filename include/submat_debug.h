@@ -31,13 +31,14 @@ extern "C" {
  *   skip_arrive  test hook: nonzero makes the epilogue withhold its release
  *          of the accumulator, so a bounded wait must expire
  *   timeout_s    limit of each device wait (seconds; <= 0 selects 2 s)
+ *   tile_n       output tile width: 128 or 256 (0 selects 128)
  * Returns OK, INVALID_ARG, TIMEOUT (a bounded wait expired; the kernel freed
  * its resources and returned), CUDA.
  */
 submat_status submat_debug_tc_gemm(int count, int ld, int n, const void* A_hi, const void* A_lo,
                                    const void* B_hi, const void* B_lo, int split, int sym,
                                    float* C, double* res2, int skip_arrive, double timeout_s,
-                                   void* stream);
+                                   int tile_n, void* stream);
 
 #ifdef __cplusplus
 }

@@ -54,7 +54,8 @@ struct Scratch {
 extern "C" submat_status submat_debug_tc_gemm(int count, int ld, int n, const void* A_hi,
                                               const void* A_lo, const void* B_hi, const void* B_lo,
                                               int split, int sym, float* C, double* res2,
-                                              int skip_arrive, double timeout_s, void* stream) {
+                                              int skip_arrive, double timeout_s, int tile_n,
+                                              void* stream) {
   using namespace submat;
   clear_error();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -67,17 +68,25 @@ extern "C" submat_status submat_debug_tc_gemm(int count, int ld, int n, const vo
   std::vector<int64_t> off(count);
   std::vector<int32_t> lds(count, ld), ns(count, n);
   for (int s = 0; s < count; ++s) off[s] = int64_t(s) * ld * ld;
+  const int bn = tile_n == 256 ? 256 : 128;
+  if (tile_n != 0 && tile_n != 128 && tile_n != 256) {
+    set_error("tile_n must be 0, 128 or 256");
+    return SUBMAT_ERR_INVALID_ARG;
+  }
   std::vector<int4> items;
   const int T = (ld + 127) / 128;
+  const int TB = (ld + bn - 1) / bn;
+  const int H = bn / 128;
   for (int s = 0; s < count; ++s)
     for (int a = 0; a < T; ++a)
-      for (int b = 0; b < T; ++b)
-        if (!sym || a <= b) items.push_back(make_int4(s, a, b, 0 | (s << 8)));
-  CUtensorMap maps[4];
+      for (int b = 0; b < TB; ++b)
+        if (!sym || H * b + H - 1 >= a) items.push_back(make_int4(s, a, b, 0 | (s << 8)));
+  CUtensorMap maps[8];
   std::memset(maps, 0, sizeof(maps));
   const void* srcs[4] = {A_hi, split ? A_lo : A_hi, B_hi, split ? B_lo : B_hi};
   for (int m = 0; m < 4; ++m)
-    if (make_bucket_map(&maps[m], srcs[m], ld, count) != 0) {
+    if (make_bucket_map(&maps[m], srcs[m], ld, count) != 0 ||
+        make_bucket_map(&maps[4 + m], srcs[m], ld, count, 256) != 0) {
       set_error("cuTensorMapEncodeTiled failed (map %d)", m);
       return SUBMAT_ERR_CUDA;
     }
@@ -96,6 +105,8 @@ extern "C" submat_status submat_debug_tc_gemm(int count, int ld, int n, const vo
   p.items = d_items;
   p.nitems = int(items.size());
   p.maps = d_maps;
+  p.maps_b = d_maps + 4;
+  p.bn = bn;
   p.nbucket = 1;
   p.nmaps = 4;
   p.na = split ? 2 : 1;
@@ -111,8 +122,8 @@ extern "C" submat_status submat_debug_tc_gemm(int count, int ld, int n, const vo
     p.prod_a[0] = 0; p.prod_b[0] = 0; p.prod_acc[0] = 0; p.prod_first[0] = 1;
   }
   p.nacc = 1;
-  p.nstage = tc_pick_stages(p.na, p.nb);
-  p.tmem_cols = 256;
+  p.nstage = tc_pick_stages(p.na, p.nb, bn);
+  p.tmem_cols = 2 * bn;
   p.off = d_off; p.ld = d_ld; p.n = d_n;
   p.state = nullptr;
   p.skip_state = -1;

@@ -481,7 +481,8 @@ dim3 pair_grid(const Wave& wv) {
 }
 
 struct MixedState {
-  std::vector<CUtensorMap*> d_maps;  // per wave: [MS_COUNT][nbucket]
+  std::vector<CUtensorMap*> d_maps;  // per wave: [MS_COUNT][nbucket], 128-row boxes
+  std::vector<CUtensorMap*> d_maps_b;  // per wave: the same with 256-row boxes
   std::vector<int64_t*> d_voff;      // per wave: offset of each submatrix's row-scale vector
   int* rs_x = nullptr;               // row exponents of the first operand's slices
   int* rs_y = nullptr;               // row exponents of the second operand's slices
@@ -520,6 +521,21 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       SM_CUDA(cudaMemcpyAsync(d, maps.data(), maps.size() * sizeof(CUtensorMap),
                               cudaMemcpyHostToDevice, st));
       ms->d_maps.push_back(d);
+      // the same sets with 256-row boxes for B operands of 128 x 256 tiles
+      for (int mset = 0; mset < MS_COUNT; ++mset)
+        for (int k = 0; k < nbk; ++k) {
+          const __nv_bfloat16* base = static_cast<const __nv_bfloat16*>(bases[mset]) + wv.bucket_base[k];
+          if (make_bucket_map(&maps[size_t(mset) * nbk + k], base, int(wv.bucket_ld[k]),
+                              wv.bucket_count[k], 256) != 0) {
+            set_error("cuTensorMapEncodeTiled failed");
+            return SUBMAT_ERR_CUDA;
+          }
+        }
+      CUtensorMap* db = nullptr;
+      SM_TRY(alloc(&db, maps.size(), "tensor maps"));
+      SM_CUDA(cudaMemcpyAsync(db, maps.data(), maps.size() * sizeof(CUtensorMap),
+                              cudaMemcpyHostToDevice, st));
+      ms->d_maps_b.push_back(db);
       std::vector<int64_t> vo(wv.count);
       int64_t acc = 0;
       for (int s = 0; s < wv.count; ++s) { vo[s] = acc; acc += wv.host_ld[s]; }
@@ -548,6 +564,20 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
   for (size_t wi = 0; wi < waves.size(); ++wi) {
     Wave& wv = waves[wi];
     const int nbk = int(wv.bucket_ld.size());
+    int bn = 128;
+    const int4* SYM = nullptr;
+    int NSYM = 0;
+    const int4* FULL = nullptr;
+    int NFULL = 0;
+    // tile width of the tensor-core launches that follow (per phase)
+    auto use_width = [&](int want) {
+      bn = want == 128 || want == 256 ? want : wv.bn;
+      SYM = bn == 256 ? wv.sym256 : wv.sym128;
+      NSYM = bn == 256 ? wv.n_sym256 : wv.n_sym128;
+      FULL = bn == 256 ? wv.full256 : wv.full128;
+      NFULL = bn == 256 ? wv.n_full256 : wv.n_full128;
+    };
+    use_width(opt.tile_n_ns);
     auto tc = [&](const int4* items, int nitems, int sa0, int sa1, int sb0, int sb1, int sym,
                   float alpha, float beta) {
       TcGemmParams p;
@@ -555,6 +585,8 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       p.items = items;
       p.nitems = nitems;
       p.maps = ms->d_maps[wi];
+      p.maps_b = ms->d_maps_b[wi];
+      p.bn = bn;
       p.nbucket = nbk;
       p.nmaps = MS_COUNT * nbk;
       p.na = 2; p.nb = 2;
@@ -564,8 +596,8 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
       for (int i = 0; i < 3; ++i) { p.prod_a[i] = pa[i]; p.prod_b[i] = pb[i]; p.prod_acc[i] = 0; p.prod_first[i] = i == 0; }
       p.nacc = 1;
-      p.nstage = tc_pick_stages(2, 2);
-      p.tmem_cols = 256;
+      p.nstage = tc_pick_stages(2, 2, bn);
+      p.tmem_cols = 2 * bn;
       p.off = wv.dev.off; p.ld = wv.dev.ld; p.n = wv.dev.n;
       p.state = nullptr;
       p.skip_state = -1;
@@ -609,14 +641,14 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     // ---- BF16x3 Newton-Schulz on the tensor cores ----
     int cur = 0;
     for (int k = 0; k < opt.max_iter; ++k) {
-      TcGemmParams g1 = tc(wv.sym128, wv.n_sym128, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
+      TcGemmParams g1 = tc(SYM, NSYM, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
                            cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0, 1, 1.0f, 0.0f);
       g1.out_hi = b.Y[0]; g1.out_lo = b.Y[1];
       g1.res2 = ns.res2;
       g1.state = ns.state; g1.skip_state = ST_DONE;
       SM_CUDA(launch(g1));
       SM_CUDA(launch_ns_update(wv.dev, ns, tol_eff, floor_thr, opt.max_iter, d_flags, st));
-      TcGemmParams g2 = tc(wv.sym128, wv.n_sym128, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
+      TcGemmParams g2 = tc(SYM, NSYM, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
                            MS_YH, MS_YL, 1, -0.5f, 1.5f);
       g2.c0_hi = b.X[cur][0]; g2.c0_lo = b.X[cur][1];
       g2.out_hi = b.X[cur ^ 1][0]; g2.out_lo = b.X[cur ^ 1][1];
@@ -633,6 +665,9 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
 
     // ---- correction rounds ----
     tc_class = KC_TC_REF;
+    // the correction's launches are epilogue-heavy (int64 read-modify-write,
+    // FP32 outputs): measured faster with 128-wide tiles on every workload
+    use_width(opt.tile_n_corr ? opt.tile_n_corr : 128);
     std::vector<int> lp_iters(wv.count);
     SM_CUDA(cudaMemcpyAsync(lp_iters.data(), ns.iters, sizeof(int) * wv.count, cudaMemcpyDeviceToHost, st));
     SM_CUDA(cudaMemsetAsync(ms->cg_count, 0, sizeof(int) * max_wave, st));
@@ -666,9 +701,11 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
           const int k = std::min(per_acc, np - c0);
           TcGemmParams p;
           std::memset(&p, 0, sizeof(p));
-          p.items = sym ? wv.sym128 : wv.full128;
-          p.nitems = sym ? wv.n_sym128 : wv.n_full128;
+          p.items = sym ? SYM : FULL;
+          p.nitems = sym ? NSYM : NFULL;
           p.maps = ms->d_maps[wi];
+          p.maps_b = ms->d_maps_b[wi];
+          p.bn = bn;
           p.nbucket = nbk;
           p.nmaps = MS_COUNT * nbk;
           p.na = k; p.nb = k;
@@ -679,8 +716,8 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
           }
           p.nprod = k;
           p.nacc = 1;
-          p.nstage = tc_pick_stages(k, k);
-          p.tmem_cols = 256;
+          p.nstage = tc_pick_stages(k, k, bn);
+          p.tmem_cols = 2 * bn;
           p.off = wv.dev.off; p.ld = wv.dev.ld; p.n = wv.dev.n;
           p.skip_state = -1;
           p.sym = sym;
@@ -729,7 +766,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       k_split64<<<eg, 256, 0, st>>>(wv.dev, b.T, b.Y[0], b.Y[1]);
       SM_KCHECK();
       // F_c = -1/2 S (I - S^2)
-      TcGemmParams g = tc(wv.sym128, wv.n_sym128, MS_XH0, MS_XL0, MS_YH, MS_YL, 1, -0.5f, 0.0f);
+      TcGemmParams g = tc(SYM, NSYM, MS_XH0, MS_XL0, MS_YH, MS_YL, 1, -0.5f, 0.0f);
       g.out_f32 = b.Fc;
       SM_CUDA(launch(g));
       // T = S a
@@ -753,14 +790,14 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       k_split32<<<eg, 256, 0, st>>>(wv.dev, b.Fc, b.Y[0], b.Y[1]);
       SM_KCHECK();
       // W = F_c a
-      TcGemmParams g3 = tc(wv.full128, wv.n_full128, MS_YH, MS_YL, MS_AH, MS_AL, 0, 1.0f, 0.0f);
+      TcGemmParams g3 = tc(FULL, NFULL, MS_YH, MS_YL, MS_AH, MS_AL, 0, 1.0f, 0.0f);
       g3.out_f32 = b.cw;
       SM_CUDA(launch(g3));
       // M = [S, a] - [F_c, a] (split into Y), H = (S a + a S) / 2 (split)
       k_comm<<<pair_grid(wv), dim3(32, 8), 0, st>>>(wv.dev, b.T, b.cw, b.Y[0], b.Y[1], b.Hh[0], b.Hh[1]);
       SM_KCHECK();
       // C = M S (symmetric to first order) -> CG residual
-      TcGemmParams g4 = tc(wv.sym128, wv.n_sym128, MS_YH, MS_YL, MS_XH0, MS_XL0, 1, 1.0f, 0.0f);
+      TcGemmParams g4 = tc(SYM, NSYM, MS_YH, MS_YL, MS_XH0, MS_XL0, 1, 1.0f, 0.0f);
       g4.out_f32 = b.cr;
       SM_CUDA(launch(g4));
       // CG on L -> H L + L H, per submatrix until the relative residual is below cg_tol
@@ -770,7 +807,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       SM_KCHECK();
       SM_CUDA(cudaMemcpyAsync(rr0, rr, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
       for (int it = 0; it < cg_max; ++it) {
-        TcGemmParams gh = tc(wv.full128, wv.n_full128, MS_HH, MS_HL, MS_YH, MS_YL, 0, 1.0f, 0.0f);
+        TcGemmParams gh = tc(FULL, NFULL, MS_HH, MS_HL, MS_YH, MS_YL, 0, 1.0f, 0.0f);
         gh.out_f32 = b.cw;
         gh.state = ms->cg_done; gh.skip_state = 1;
         SM_CUDA(launch(gh));

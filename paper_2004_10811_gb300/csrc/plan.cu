@@ -189,7 +189,8 @@ submat_status Plan::build_waves(size_t bpe, size_t cap, std::vector<Wave>& waves
     std::vector<int32_t> sub(wv.count), ld(wv.count), nn(wv.count);
     std::vector<int64_t> off(wv.count);
     std::vector<int2> gitems;
-    std::vector<int4> sym64, full64, sym128, full128;
+    std::vector<int4> sym64, full64, sym128, full128, sym256, full256;
+    double area128 = 0.0, area256 = 0.0;
     std::vector<int64_t> lds;
     for (int s = 0; s < wv.count; ++s) lds.push_back(ld_of[wv.first + s]);
     std::sort(lds.begin(), lds.end());
@@ -226,13 +227,24 @@ submat_status Plan::build_waves(size_t bpe, size_t cap, std::vector<Wave>& waves
           if (a <= b) sym64.push_back(make_int4(s, a, b, 0));
         }
       const int T2 = int((ld_of[j] + 127) / 128);
+      const int T4 = int((ld_of[j] + 255) / 256);
       const int tag = bucket_of[s] | (slot_of[s] << 8);
       for (int a = 0; a < T2; ++a)
         for (int b = 0; b < T2; ++b) {
           full128.push_back(make_int4(s, a, b, tag));
           if (a <= b) sym128.push_back(make_int4(s, a, b, tag));
         }
+      // 128 x 256 tiles: sub-tiles (a, 2b) and (a, 2b + 1)
+      for (int a = 0; a < T2; ++a)
+        for (int b = 0; b < T4; ++b) {
+          full256.push_back(make_int4(s, a, b, tag));
+          if (2 * b + 1 >= a) sym256.push_back(make_int4(s, a, b, tag));
+        }
+      area128 += double(T2) * T2;
+      area256 += double(T2) * T4 * 2;
     }
+    // the wider tile when its padding costs at most 8 % more MMA work
+    wv.bn = area256 <= 1.08 * area128 ? 256 : 128;
     int32_t* d_sub; int32_t* d_ld; int32_t* d_n; int64_t* d_off;
     SM_TRY(put(&d_sub, sub, st, "wave submatrices"));
     SM_TRY(put(&d_ld, ld, st, "wave ld"));
@@ -249,6 +261,10 @@ submat_status Plan::build_waves(size_t bpe, size_t cap, std::vector<Wave>& waves
     wv.n_sym128 = int(sym128.size());
     SM_TRY(put(&wv.full128, full128, st, "tile list"));
     wv.n_full128 = int(full128.size());
+    SM_TRY(put(&wv.sym256, sym256, st, "tile list"));
+    wv.n_sym256 = int(sym256.size());
+    SM_TRY(put(&wv.full256, full256, st, "tile list"));
+    wv.n_full256 = int(full256.size());
     wv.host_ld = ld;
     wv.host_n = nn;
     wv.host_off = off;
@@ -696,6 +712,11 @@ submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int
     if (o.prec < 0 || o.prec > 2) { submat::set_error("bad precision %d", o.prec); return SUBMAT_ERR_INVALID_ARG; }
     if (o.max_iter < 0 || o.tol < 0.0 || o.refine_rounds < 0) {
       submat::set_error("negative max_iter, tol or refine_rounds");
+      return SUBMAT_ERR_INVALID_ARG;
+    }
+    if ((o.tile_n_ns != 0 && o.tile_n_ns != 128 && o.tile_n_ns != 256) ||
+        (o.tile_n_corr != 0 && o.tile_n_corr != 128 && o.tile_n_corr != 256)) {
+      submat::set_error("tile widths must be 0, 128 or 256");
       return SUBMAT_ERR_INVALID_ARG;
     }
     for (int r : o.reserved)

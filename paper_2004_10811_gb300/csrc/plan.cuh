@@ -34,6 +34,11 @@ struct Wave {
   int n_sym128 = 0;
   int4* full128 = nullptr;
   int n_full128 = 0;
+  int4* sym256 = nullptr;  // 128x256 tiles (s, ti, tj, tag) covering sub-tiles (ti, 2tj), (ti, 2tj+1)
+  int n_sym256 = 0;
+  int4* full256 = nullptr;
+  int n_full256 = 0;
+  int bn = 128;            // tensor-core tile width used for this wave
   std::vector<int64_t> bucket_ld, bucket_base;  // size buckets: [count][ld][ld] each
   std::vector<int> bucket_count;
   std::vector<int32_t> host_ld, host_n;

@@ -29,13 +29,15 @@ namespace submat {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int TILE_BYTES = BM * BK * 2;  // one 128 x 64 BF16 operand tile
+constexpr int BM = 128, BK = 64;
+constexpr int TILE_BYTES = BM * BK * 2;  // one 128 x 64 BF16 operand tile (A side)
 constexpr int STG_PITCH = 33;            // staged row pitch (32-bit words)
-constexpr uint32_t IDESC = (1u << 4)            // D format: F32
-                           | (1u << 7)          // A format: BF16
-                           | (1u << 10)         // B format: BF16
-                           | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+
+// instruction descriptor: D F32, A and B BF16, both K-major, M = 128, N = BN
+template <int BN>
+__device__ __forceinline__ constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -106,12 +108,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
+                                          uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accum));
+      "l"(a), "l"(b), "r"(id), "r"(accum));
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -248,13 +251,16 @@ __device__ __forceinline__ void load_c0(const TcGemmParams& p, int64_t idx, floa
   }
 }
 
+template <int BN>
 __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGemmParams p) {
+  constexpr int TILE_B = BN * BK * 2;  // one BN x 64 BF16 operand tile (B side)
+  constexpr int HALVES = BN / 128;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
-  const int nslot = p.na + p.nb;
+  const int stage_bytes = p.na * TILE_BYTES + p.nb * TILE_B;
   uint8_t* tiles = smem;
-  uint32_t* stg = reinterpret_cast<uint32_t*>(tiles + size_t(p.nstage) * nslot * TILE_BYTES);
+  uint32_t* stg = reinterpret_cast<uint32_t*>(tiles + size_t(p.nstage) * stage_bytes);
   uint64_t* bars = reinterpret_cast<uint64_t*>(stg + BM * STG_PITCH);
   uint64_t* full = bars;
   uint64_t* empty = bars + p.nstage;
@@ -304,17 +310,18 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       if (p.state && p.state[item.x] == p.skip_state) continue;
       const int bucket = item.w & 0xFF, slot = item.w >> 8;
       const int nk = p.ld[item.x] / BK;
-      const CUtensorMap* mapsb = p.maps + bucket;
+      const CUtensorMap* mapsa = p.maps + bucket;
+      const CUtensorMap* mapsb = (BN == 128 ? p.maps : p.maps_b) + bucket;
       for (int kb = 0; kb < nk; ++kb) {
         if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, limit)) { ok = false; break; }
-        uint8_t* st = tiles + size_t(stage) * nslot * TILE_BYTES;
-        mbar_expect_tx(&full[stage], uint32_t(nslot * TILE_BYTES));
+        uint8_t* st = tiles + size_t(stage) * stage_bytes;
+        mbar_expect_tx(&full[stage], uint32_t(stage_bytes));
         for (int a = 0; a < p.na; ++a)
-          tma_load_3d(st + a * TILE_BYTES, mapsb + p.a_set[a] * p.nbucket, &full[stage], kb * BK,
+          tma_load_3d(st + a * TILE_BYTES, mapsa + p.a_set[a] * p.nbucket, &full[stage], kb * BK,
                       item.y * BM, slot);
         for (int b = 0; b < p.nb; ++b)
-          tma_load_3d(st + (p.na + b) * TILE_BYTES, mapsb + p.b_set[b] * p.nbucket, &full[stage],
-                      kb * BK, item.z * BN, slot);
+          tma_load_3d(st + p.na * TILE_BYTES + b * TILE_B, mapsb + p.b_set[b] * p.nbucket,
+                      &full[stage], kb * BK, item.z * BN, slot);
         issued |= 1u << stage;
         issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
         if (++stage == p.nstage) { stage = 0; phase ^= 1u; }
@@ -349,14 +356,14 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       for (int kb = 0; kb < nk; ++kb) {
         if (!mbar_wait(&full[stage], phase, abort_flag, limit)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t sb = smem_u32(tiles + size_t(stage) * nslot * TILE_BYTES);
+        const uint32_t sb = smem_u32(tiles + size_t(stage) * stage_bytes);
         for (int pr = 0; pr < p.nprod; ++pr) {
           const uint64_t ad = sdesc(sb + uint32_t(p.prod_a[pr] * TILE_BYTES));
-          const uint64_t bd = sdesc(sb + uint32_t((p.na + p.prod_b[pr]) * TILE_BYTES));
+          const uint64_t bd = sdesc(sb + uint32_t(p.na * TILE_BYTES + p.prod_b[pr] * TILE_B));
           const uint32_t d = dbase + uint32_t(p.prod_acc[pr] * BN);
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)
-            umma_bf16(d, ad + uint64_t(2 * k), bd + uint64_t(2 * k),
+            umma_bf16(d, ad + uint64_t(2 * k), bd + uint64_t(2 * k), idesc<BN>(),
                       (kb > 0 || k > 0 || !p.prod_first[pr]) ? 1u : 0u);
         }
         umma_commit(&empty[stage]);
@@ -398,38 +405,46 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       epi_bar();
       if (!*epi_ok) break;
       tc_fence_after();
-      float acc[BN];
-      const uint32_t tb = tmem_base + (uint32_t(quarter * 32) << 16) + uint32_t(ab * p.nacc * BN);
+      ++tcount;
+      const int ld = p.ld[s];
+      const int n = p.n[s];
+      const int64_t base = p.off[s];
+      const int rg = item.y * BM + r;
+      double part = 0.0;
+      const uint32_t tbase = tmem_base + (uint32_t(quarter * 32) << 16) + uint32_t(ab * p.nacc * BN);
+      for (int h = 0; h < HALVES; ++h) {
+      float acc[128];
+      const uint32_t tb = tbase + uint32_t(h * 128);
 #pragma unroll
-      for (int c = 0; c < BN / 32; ++c) tmem_ld32(tb + uint32_t(c * 32), acc + c * 32);
+      for (int c = 0; c < 4; ++c) tmem_ld32(tb + uint32_t(c * 32), acc + c * 32);
       tmem_wait_ld();
       for (int a = 1; a < p.nacc; ++a) {
         float tmp[32];
 #pragma unroll
-        for (int c = 0; c < BN / 32; ++c) {
+        for (int c = 0; c < 4; ++c) {
           tmem_ld32(tb + uint32_t(a * BN + c * 32), tmp);
           tmem_wait_ld();
 #pragma unroll
           for (int q = 0; q < 32; ++q) acc[c * 32 + q] += tmp[q];
         }
       }
-      tc_fence_before();
-      if (!p.test_skip_arrive) mbar_arrive(&tempty[ab]);
-      ++tcount;
-
-      const int ld = p.ld[s];
-      const int n = p.n[s];
-      const int64_t base = p.off[s];
-      const int rg = item.y * BM + r;
-      // symmetric output: off-diagonal tiles are mirrored; diagonal tiles keep
-      // their upper triangle and take the strict lower one from it, so the
-      // result is exactly symmetric whatever the accumulation order
-      const bool diag_sym = p.sym && item.y == item.z;
+      if (h == HALVES - 1) {
+        tc_fence_before();
+        if (!p.test_skip_arrive) mbar_arrive(&tempty[ab]);
+      }
+      // this half is the 128 x 128 sub-tile (item.y, sub_tj) of C
+      const int sub_tj = item.z * HALVES + h;
+      // symmetric output: sub-tiles below the diagonal are not written, those
+      // above it are mirrored, diagonal ones keep their upper triangle and take
+      // the strict lower one from it, so C is exactly symmetric whatever the
+      // accumulation order
+      if (p.sym && sub_tj < item.y) continue;
+      const bool diag_sym = p.sym && item.y == sub_tj;
       const bool mirror = p.sym != 0;
-      double part = 0.0;
+      const double res_weight = (mirror && !diag_sym) ? 2.0 : 1.0;  // the mirror counts too
 #pragma unroll
-      for (int c = 0; c < BN / 32; ++c) {
-        const int cg0 = item.z * BN + c * 32;
+      for (int c = 0; c < 4; ++c) {
+        const int cg0 = sub_tj * 128 + c * 32;
         float o[32];
         const bool inside = (rg < ld) && (cg0 < ld);
         if (p.out_i64) {
@@ -467,7 +482,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
             epi_bar();
             const int t = threadIdx.x - 64;
             const int q = t >> 2, part4 = t & 3;
-            const int mrow = item.z * BN + c * 32 + q;
+            const int mrow = sub_tj * 128 + c * 32 + q;
             const int mcol0 = item.y * BM + part4 * 32;
             if (mrow < ld && mcol0 < ld) {
               const int hi = diag_sym ? c * 32 + q - part4 * 32 : 32;
@@ -499,7 +514,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
             epi_bar();
             const int t = threadIdx.x - 64;
             const int q = t >> 2, part4 = t & 3;
-            const int mrow = item.z * BN + c * 32 + q;
+            const int mrow = sub_tj * 128 + c * 32 + q;
             const int mcol0 = item.y * BM + part4 * 32;
             if (mrow < ld && mcol0 < ld) {
               float w[32];
@@ -543,7 +558,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
               const float e = o[q] - ((rg == cg && rg < n) ? 1.0f : 0.0f);
               pc = fmaf(e, e, pc);
             }
-            part += double(pc);
+            part += res_weight * double(pc);
           }
           if (diag_sym) store_range(p, idx, o, r - c * 32, 32);
           else store_row(p, idx, o);
@@ -558,7 +573,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
           epi_bar();
           const int t = threadIdx.x - 64;
           const int q = t >> 2, part4 = t & 3;
-          const int mrow = item.z * BN + c * 32 + q;       // row of the mirrored tile
+          const int mrow = sub_tj * 128 + c * 32 + q;       // row of the mirrored tile
           const int mcol0 = item.y * BM + part4 * 32;      // its first column
           if (mrow < ld && mcol0 < ld) {
             float w[32];
@@ -570,10 +585,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
           epi_bar();
         }
       }
+      }  // halves
       if (p.res2) {
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o2);
-        if (lane == 0 && part != 0.0) atomicAdd(&p.res2[s], (mirror && !diag_sym) ? 2.0 * part : part);
+        if (lane == 0 && part != 0.0) atomicAdd(&p.res2[s], part);
       }
     }
   }
@@ -587,23 +603,34 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
 
 }  // namespace
 
-int tc_smem_bytes(int na, int nb, int nstage) {
-  return 1024 + nstage * (na + nb) * TILE_BYTES + BM * STG_PITCH * 4 + (2 * nstage + 5) * 8 + 32;
+int tc_smem_bytes(int na, int nb, int nstage, int bn) {
+  return 1024 + nstage * (na * TILE_BYTES + nb * bn * BK * 2) + BM * STG_PITCH * 4 + (2 * nstage + 5) * 8 +
+         32;
 }
 
-int tc_pick_stages(int na, int nb) {
+int tc_pick_stages(int na, int nb, int bn) {
   const int budget = 227 * 1024;
   int st = 6;
-  while (st > 2 && tc_smem_bytes(na, nb, st) > budget) --st;
+  while (st > 2 && tc_smem_bytes(na, nb, st, bn) > budget) --st;
   return st;
 }
 
 cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st) {
   if (p.nitems <= 0) return cudaSuccess;
-  const int smem = tc_smem_bytes(p.na, p.nb, p.nstage);
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  k_tc_gemm<<<grid, 192, smem, st>>>(p);
+  const int bn = p.bn == 256 ? 256 : 128;
+  if (bn == 256 && (p.nacc != 1 || p.tmem_cols != 512 || !p.maps_b)) return cudaErrorInvalidValue;
+  const int smem = tc_smem_bytes(p.na, p.nb, p.nstage, bn);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (bn == 256) {
+    e = cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<256><<<grid, 192, smem, st>>>(p);
+  } else {
+    e = cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<128><<<grid, 192, smem, st>>>(p);
+  }
   count_launch();
   return cudaGetLastError();
 }
@@ -630,12 +657,12 @@ static PFN_encodeTiled get_encoder() {
   return fn;
 }
 
-int make_bucket_map(CUtensorMap* out, const void* base, int ld, int count) {
+int make_bucket_map(CUtensorMap* out, const void* base, int ld, int count, int box_rows) {
   PFN_encodeTiled enc = get_encoder();
   if (!enc) return -1;
   const cuuint64_t dims[3] = {cuuint64_t(ld), cuuint64_t(ld), cuuint64_t(count)};
   const cuuint64_t strides[2] = {cuuint64_t(ld) * 2, cuuint64_t(ld) * ld * 2};
-  const cuuint32_t box[3] = {BK, BM, 1};
+  const cuuint32_t box[3] = {BK, cuuint32_t(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,

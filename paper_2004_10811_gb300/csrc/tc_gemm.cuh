@@ -17,7 +17,9 @@ constexpr int TC_MAX_PROD = 16;
 struct TcGemmParams {
   const int4* items;        // (s, ti, tj, bucket | slot << 8), 128 x 128 tiles
   int nitems;
-  const CUtensorMap* maps;  // device array [set][bucket]
+  const CUtensorMap* maps;  // device array [set][bucket], 128-row boxes (A operands; B when bn = 128)
+  const CUtensorMap* maps_b;  // same sets with 256-row boxes (B operands when bn = 256)
+  int bn;                   // output tile width: 128 or 256 (then nacc = 1, tmem_cols = 512)
   int nbucket, nmaps;
   int na, nb;               // A-side and B-side operand slices per k-block
   int a_set[TC_MAX_SLOTS];  // tensor-map set of each A slice
@@ -62,10 +64,10 @@ struct TcGemmParams {
   int test_skip_arrive;           // test hook: epilogue withholds its TMEM release
 };
 
-int tc_smem_bytes(int na, int nb, int nstage);
-int tc_pick_stages(int na, int nb);
+int tc_smem_bytes(int na, int nb, int nstage, int bn = 128);
+int tc_pick_stages(int na, int nb, int bn = 128);
 cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st);
-// 3D map over a bucket [count][ld][ld] of BF16, box 64 x 128 x 1, 128B swizzle.
-int make_bucket_map(CUtensorMap* out, const void* base, int ld, int count);
+// 3D map over a bucket [count][ld][ld] of BF16, box 64 x box_rows x 1, 128B swizzle.
+int make_bucket_map(CUtensorMap* out, const void* base, int ld, int count, int box_rows = 128);
 
 }  // namespace submat

@@ -48,7 +48,8 @@ class Options(C.Structure):
         ("prec", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("beta_mode", C.c_int),
         ("symmetrize", C.c_int), ("workspace_cap_bytes", C.c_size_t),
         ("refine_rounds", C.c_int), ("timing", C.c_int), ("col_begin", C.c_int), ("col_end", C.c_int),
-        ("hp_mode", C.c_int), ("reserved", C.c_int * 4),
+        ("hp_mode", C.c_int), ("tile_n_ns", C.c_int), ("tile_n_corr", C.c_int),
+        ("reserved", C.c_int * 2),
     ]
 
 
@@ -99,7 +100,7 @@ def load(path: str = LIB_PATH):
     lib.submat_get_stats.argtypes = [vp, C.POINTER(Stats)]
     lib.submat_get_sub_stats.argtypes = [vp, i32p, i32p, dp, dp]
     lib.submat_debug_tc_gemm.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, C.c_int,
-                                         vp, vp, C.c_int, C.c_double, vp]
+                                         vp, vp, C.c_int, C.c_double, C.c_int, vp]
     lib.submat_dense_sign_noalloc.argtypes = [C.c_int, vp, C.c_double, vp, C.POINTER(C.c_int), vp]
     lib.submat_last_error.argtypes = []
     lib.submat_last_error.restype = C.c_char_p
@@ -147,7 +148,7 @@ class Plan:
 
     def __init__(self, block_sizes, row_ptr, col_idx, prec="fp64", tol=0.0, max_iter=0,
                  beta_mode=0, symmetrize=False, workspace_cap_bytes=0, refine_rounds=0,
-                 timing=False, columns=None, hp_mode=0, stream=None):
+                 timing=False, columns=None, hp_mode=0, tile_n_ns=0, tile_n_corr=0, stream=None):
         lib = load()
         self._lib = lib
         self.block_sizes = np.ascontiguousarray(block_sizes, dtype=np.int32)
@@ -164,6 +165,8 @@ class Plan:
         opt.refine_rounds = int(refine_rounds)
         opt.timing = int(bool(timing))
         opt.hp_mode = int(hp_mode)
+        opt.tile_n_ns = int(tile_n_ns)
+        opt.tile_n_corr = int(tile_n_corr)
         if columns is not None:
             opt.col_begin, opt.col_end = int(columns[0]), int(columns[1])
         self.options = opt
@@ -280,7 +283,7 @@ def make_autograd_sign(plan: Plan):
 
 
 def debug_tc_gemm(A_hi, B_hi, A_lo=None, B_lo=None, n=None, sym=False, res2=None, skip_arrive=False,
-                  timeout_s=2.0, stream=None, allow_timeout=False):
+                  timeout_s=2.0, stream=None, allow_timeout=False, tile_n=128):
     """Test hook: the grouped BF16 tensor-core GEMM alone (include/submat_debug.h).
 
     A_*, B_*: CUDA bfloat16 tensors [count, ld, ld]; returns (C float32, status name).
@@ -294,7 +297,7 @@ def debug_tc_gemm(A_hi, B_hi, A_lo=None, B_lo=None, n=None, sym=False, res2=None
     ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
     st = lib.submat_debug_tc_gemm(count, ld, ld if n is None else int(n), ptr(A_hi), ptr(A_lo),
                                   ptr(B_hi), ptr(B_lo), int(split), int(bool(sym)), ptr(C_), ptr(res2),
-                                  int(bool(skip_arrive)), float(timeout_s), _stream(stream))
+                                  int(bool(skip_arrive)), float(timeout_s), int(tile_n), _stream(stream))
     _check(st, allow=(8,) if allow_timeout else ())
     return C_, STATUS[st]
 

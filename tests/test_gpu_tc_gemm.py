@@ -26,29 +26,32 @@ def rand_bf16(count, ld, n, seed, sym=False, scale=1.0):
     return x, hi.cuda(), lo.cuda()
 
 
-def test_single_tile_plain(sm):
-    _x, a, _ = rand_bf16(1, 128, 128, 1)
-    _y, b, _ = rand_bf16(1, 128, 128, 2)
-    c, st = sm.debug_tc_gemm(a, b)
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_single_tile_plain(sm, tile_n):
+    _x, a, _ = rand_bf16(1, 256, 256, 1)
+    _y, b, _ = rand_bf16(1, 256, 256, 2)
+    c, st = sm.debug_tc_gemm(a, b, tile_n=tile_n)
     ref = a.double() @ b.double().transpose(1, 2)
     err = (c.double() - ref).abs().max().item()
     assert st == "OK" and err < 1e-3 * ref.abs().max().item(), err
 
 
+@pytest.mark.parametrize("tile_n", [128, 256])
 @pytest.mark.parametrize("count,ld,n", [(3, 320, 300), (2, 640, 577), (5, 64, 40)])
-def test_ragged_batches_plain(sm, count, ld, n):
+def test_ragged_batches_plain(sm, count, ld, n, tile_n):
     _x, a, _ = rand_bf16(count, ld, n, 3)
     _y, b, _ = rand_bf16(count, ld, n, 4)
-    c, _ = sm.debug_tc_gemm(a, b)
+    c, _ = sm.debug_tc_gemm(a, b, tile_n=tile_n)
     ref = a.double() @ b.double().transpose(1, 2)
     assert (c.double() - ref).abs().max().item() < 2e-3 * ref.abs().max().item()
     assert c[:, n:, :].abs().max().item() == 0.0 and c[:, :, n:].abs().max().item() == 0.0
 
 
-def test_split_product_carries_16_bits(sm):
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_split_product_carries_16_bits(sm, tile_n):
     x, ah, al = rand_bf16(2, 384, 350, 5)
     y, bh, bl = rand_bf16(2, 384, 350, 6)
-    c, _ = sm.debug_tc_gemm(ah, bh, al, bl)
+    c, _ = sm.debug_tc_gemm(ah, bh, al, bl, tile_n=tile_n)
     ref = (x @ y.transpose(1, 2)).cuda()
     rel = (c.double() - ref).abs().max().item() / ref.abs().max().item()
     plain, _ = sm.debug_tc_gemm(ah, bh)
@@ -56,12 +59,13 @@ def test_split_product_carries_16_bits(sm):
     assert rel < 2e-5 and rel < rel_plain / 20, (rel, rel_plain)
 
 
-def test_symmetric_mirror_and_residual(sm):
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_symmetric_mirror_and_residual(sm, tile_n):
     import torch
     x, xh, xl = rand_bf16(3, 448, 430, 7, sym=True, scale=0.05)
     res = torch.zeros(3, dtype=torch.float64, device="cuda")
-    full, _ = sm.debug_tc_gemm(xh, xh, xl, xl)
-    half, _ = sm.debug_tc_gemm(xh, xh, xl, xl, n=430, sym=True, res2=res)
+    full, _ = sm.debug_tc_gemm(xh, xh, xl, xl, tile_n=tile_n)
+    half, _ = sm.debug_tc_gemm(xh, xh, xl, xl, n=430, sym=True, res2=res, tile_n=tile_n)
     assert torch.equal(half, half.transpose(1, 2))
     up = torch.triu(torch.ones(448, 448, dtype=torch.bool, device="cuda"))
     # upper tiles are computed the same way in both launches
@@ -73,10 +77,11 @@ def test_symmetric_mirror_and_residual(sm):
     assert torch.allclose(res, want, rtol=1e-5, atol=1e-9)
 
 
-def test_bounded_wait_reports_timeout_and_context_survives(sm):
-    _x, a, _ = rand_bf16(1, 512, 512, 8)
-    c, st = sm.debug_tc_gemm(a, a, skip_arrive=True, timeout_s=0.2, allow_timeout=True)
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_bounded_wait_reports_timeout_and_context_survives(sm, tile_n):
+    _x, a, _ = rand_bf16(1, 768, 768, 8)
+    c, st = sm.debug_tc_gemm(a, a, skip_arrive=True, timeout_s=0.2, allow_timeout=True, tile_n=tile_n)
     assert st == "TIMEOUT"
-    c2, st2 = sm.debug_tc_gemm(a, a)
+    c2, st2 = sm.debug_tc_gemm(a, a, tile_n=tile_n)
     ref = a.double() @ a.double().transpose(1, 2)
     assert st2 == "OK" and (c2.double() - ref).abs().max().item() < 2e-3 * ref.abs().max().item()
