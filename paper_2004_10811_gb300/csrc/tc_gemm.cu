@@ -542,13 +542,19 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
         if (inside) {
           float c0[32];
           const int64_t idx = base + int64_t(rg) * ld + cg0;
-          const bool has_c0 = (p.c0_f32 || p.c0_hi) && p.beta != 0.0f;
-          if (has_c0) load_c0(p, idx, c0);
+          const bool has_c0 = (p.c0_f32 || p.c0_hi) && p.beta != 0.0f && !p.dot_c0;
+          if (has_c0 || p.dot_c0) load_c0(p, idx, c0);
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
             float v = p.alpha * acc[c * 32 + q];
             if (has_c0) v = fmaf(p.beta, c0[q], v);
             o[q] = v;
+          }
+          if (p.dot_c0) {
+            float pc = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) pc = fmaf(o[q], c0[q], pc);
+            part += 2.0 * double(pc);
           }
           if (p.res2) {
             float pc = 0.0f;
@@ -586,10 +592,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
         }
       }
       }  // halves
-      if (p.res2) {
+      if (p.res2 || p.dot_c0) {
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o2);
-        if (lane == 0 && part != 0.0) atomicAdd(&p.res2[s], part);
+        if (lane == 0 && part != 0.0) atomicAdd(p.res2 ? &p.res2[s] : &p.dot_c0[s], part);
       }
     }
   }

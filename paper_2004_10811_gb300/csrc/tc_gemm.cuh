@@ -43,6 +43,7 @@ struct TcGemmParams {
   const __nv_bfloat16* c0_hi;
   const __nv_bfloat16* c0_lo;
   double* res2;                   // optional ||C - I_n||_F^2 per submatrix
+  double* dot_c0;                 // optional: 2 <C, C0> per submatrix (C0 = c0_f32, beta unused)
   // FP64 output (sliced high-precision products): with out_f64 set, the tile
   // value is  f64_scale * rowscale_a[row] * rowscale_b[col] * acc  (+ f64_diag
   // on the diagonal of the n x n block), written or, with f64_accumulate,
