@@ -116,15 +116,21 @@ typedef struct {
   size_t  workspace_bytes; /* device workspace held by the plan */
   int64_t launches;        /* kernel launches issued by the call */
   /* Per kernel class, with options.timing = 1 (else zero):
-   *   0 tensor-core GEMM, Newton-Schulz;  1 tensor-core GEMM, correction;
-   *   2 FP64/FP32 SIMT GEMM;  3 gather (assembly) kernel.
-   * kernel_ms: summed launch durations; kernel_work: algorithmic work of those
-   * launches -- flops for 0-2 (2 n^3 per general n x n product, n^2 (n + 1)
-   * per product with a symmetric result, a split product counted once), bytes
-   * moved (8 bytes per dense element written plus 8 per K value read) for 3. */
-  double  kernel_ms[4];
-  int32_t kernel_launches[4];
-  double  kernel_work[4];
+   *   0 tensor-core GEMM, Newton-Schulz;  1 tensor-core GEMM, correction
+   *   (split products and the Lyapunov CG);  2 FP64/FP32 SIMT GEMM;
+   *   3 gather (assembly) kernel;  4 tensor-core GEMM, sliced FP64-accurate
+   *   residual products;  5 unused.
+   * kernel_ms: summed launch durations.  kernel_work: algorithmic work of
+   * those launches -- flops for the GEMM classes (2 n^3 per general n x n
+   * product, n^2 (n + 1) per product with a symmetric result; a split or
+   * sliced product counts once, as the product it represents), bytes moved
+   * for the gather (8 per dense element written plus 8 per K value read).
+   * kernel_exec: MMA flops the tensor cores executed (every slice product,
+   * tile padding included); 0 for the other classes. */
+  double  kernel_ms[6];
+  int32_t kernel_launches[6];
+  double  kernel_work[6];
+  double  kernel_exec[6];
 } submat_stats;
 
 /* Fill *opt with defaults (FP64, default tolerances, beta_mode 0). */

@@ -457,6 +457,15 @@ __global__ void k_scale_picked(WaveDev w, const int* __restrict__ pick, const do
   FOR_SUB_ELEMS(w) X[base + e] = A[base + e] * ib;
 }
 
+// 128 x 256 tiles with a sub-tile on or above the diagonal
+int sym256_count(int t128, int t256) {
+  int c = 0;
+  for (int a = 0; a < t128; ++a)
+    for (int b = 0; b < t256; ++b)
+      if (2 * b + 1 >= a) ++c;
+  return c;
+}
+
 dim3 elem_grid(const Wave& wv) {
   int64_t bx = (wv.max_ld2 + 256 * 8 - 1) / (256 * 8);
   bx = std::max<int64_t>(1, std::min<int64_t>(bx, 256));
@@ -467,7 +476,8 @@ dim3 pair_grid(const Wave& wv) {
   int64_t t = 1;
   for (int64_t l : wv.bucket_ld) t = std::max<int64_t>(t, l / 32);
   int64_t np = t * (t + 1) / 2;
-  return dim3(unsigned(std::min<int64_t>(np, 512)), unsigned(wv.count));
+  // one tile pair per block keeps enough loads in flight
+  return dim3(unsigned(std::min<int64_t>(np, 4096)), unsigned(wv.count));
 }
 
 struct MixedState {
@@ -568,6 +578,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       NFULL = bn == 256 ? wv.n_full256 : wv.n_full128;
     };
     use_width(opt.tile_n_ns);
+    const int ns_width = bn;
     auto tc = [&](const int4* items, int nitems, int sa0, int sa1, int sb0, int sb1, int sym,
                   float alpha, float beta) {
       TcGemmParams p;
@@ -677,6 +688,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     const dim3 slice_grid(unsigned(std::max<int64_t>(1, std::min<int64_t>(max_ld / 8, 256))), unsigned(wv.count));
     // C (+)= sign * X Y^T from the slices: level t = p + q weighs 2^(-6 t); each
     // launch sums at most per_acc products of one level in one exact accumulator
+    int hp_launch_products = 0;  // slice products issued (all residual products, this wave)
     auto hp_product = [&](const int* xs, const int* ys, const int* ex, const int* ey,
                           double* out, int sym, double sign, double diag) -> submat_status {
       bool first = true;
@@ -716,7 +728,12 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
           p.out_i64 = reinterpret_cast<long long*>(out);
           p.i64_shift = HP_BITS * (HP_MAX_LEVEL - t);
           p.f64_accumulate = first ? 0 : 1;
-          SM_CUDA(launch(p));
+          const int saved = tc_class;
+          tc_class = KC_TC_HP;
+          const cudaError_t e = launch(p);
+          tc_class = saved;
+          SM_CUDA(e);
+          hp_launch_products += k;
           first = false;
         }
       }
@@ -885,9 +902,21 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       const double sym = n * n * (n + 1.0);
       stats.kernel_work[KC_TC_NS] += 2.0 * sym * lp_iters[s];
       stats.kernel_work[KC_TC_REF] += (2.0 * sym + 2.0 * n3) * rounds + 2.0 * n3 * cgc[s];
-      if (hp_sliced) stats.kernel_work[KC_TC_REF] += (sym + 2.0 * n3) * rounds;
+      // the two residual products: I - S^2 (all tiles: 2 n^3) and S a (2 n^3)
+      if (hp_sliced) stats.kernel_work[KC_TC_HP] += 4.0 * n3 * rounds;
       else stats.kernel_work[KC_SIMT] += (sym + 2.0 * n3) * rounds;
       stats.kernel_work[KC_SIMT] += 2.0 * sym * extra;
+      // executed MMA work: tiles x 2 * 128 * width * K per product
+      const double ldd = double(wv.host_ld[s]);
+      const double t128 = std::ceil(ldd / 128.0);
+      const double tns = std::ceil(ldd / ns_width);
+      const double sym_tiles_ns = ns_width == 256 ? double(sym256_count(int(t128), int(tns))) : t128 * (t128 + 1) / 2;
+      const double tile_ns = 2.0 * 128.0 * ns_width * ldd;
+      const double tile128 = 2.0 * 128.0 * 128.0 * ldd;
+      stats.kernel_exec[KC_TC_NS] += 2.0 * lp_iters[s] * 3.0 * sym_tiles_ns * tile_ns;
+      const double symt = t128 * (t128 + 1) / 2, fullt = t128 * t128;
+      stats.kernel_exec[KC_TC_REF] += rounds * 3.0 * (2.0 * symt + fullt) * tile128 + cgc[s] * 3.0 * fullt * tile128;
+      if (hp_sliced) stats.kernel_exec[KC_TC_HP] += double(hp_launch_products) * fullt * tile128;
     }
     stats.refine_fallback = fallback_total;
   }

@@ -59,7 +59,7 @@ struct KernelTimer {
   submat_status collect(double* ms, int32_t* count);  // after a stream sync
 };
 
-enum KernelClass { KC_TC_NS = 0, KC_TC_REF = 1, KC_SIMT = 2, KC_GATHER = 3 };
+enum KernelClass { KC_TC_NS = 0, KC_TC_REF = 1, KC_SIMT = 2, KC_GATHER = 3, KC_TC_HP = 4 };
 
 int max_ld(const Wave& wv);
 

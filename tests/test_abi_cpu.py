@@ -43,7 +43,7 @@ def test_struct_layouts_match_the_header(lib):
     from paper_2004_10811_gb300.submat import Options, Stats
     src = ('#include "submat.h"\n#include <stdio.h>\n#include <stddef.h>\n'
            'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(submat_options), sizeof(submat_stats),'
-           ' offsetof(submat_options, refine_rounds), offsetof(submat_stats, kernel_work));return 0;}\n')
+           ' offsetof(submat_options, refine_rounds), offsetof(submat_stats, kernel_exec));return 0;}\n')
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "probe.c")
         open(c, "w").write(src)
@@ -53,7 +53,7 @@ def test_struct_layouts_match_the_header(lib):
     assert int(out[0]) == C.sizeof(Options)
     assert int(out[1]) == C.sizeof(Stats)
     assert int(out[2]) == Options.refine_rounds.offset
-    assert int(out[3]) == Stats.kernel_work.offset
+    assert int(out[3]) == Stats.kernel_exec.offset
 
 
 def test_options_default(lib):
