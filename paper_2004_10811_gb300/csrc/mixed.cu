@@ -299,58 +299,76 @@ __device__ __forceinline__ double block_sum(float v, double* red) {
 
 // CG step 2, fused with the symmetrisation: TP = W + W^T read through 32x32
 // tile pairs; alpha = rr / pTp; X += alpha P; R -= alpha TP; rr_new = <R, R>.
-__global__ void k_cg_update_pairs(WaveDev w, const float* __restrict__ W, float* __restrict__ X,
-                                  float* __restrict__ R, const float* __restrict__ Pd,
-                                  const double* rr, const double* ptp, double* rr_new,
-                                  const int* __restrict__ cg_done, int* cg_count) {
+// Block (8, 32): thread (x, y) owns columns 4x..4x+3 of row y of each tile
+// (float4 accesses).
+__global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float* __restrict__ W,
+                                                         float* __restrict__ X, float* __restrict__ R,
+                                                         const float* __restrict__ Pd, const double* rr,
+                                                         const double* ptp, double* rr_new,
+                                                         const int* __restrict__ cg_done, int* cg_count) {
   __shared__ float ta_[32][33], tb_[32][33];
-  __shared__ double red[32];
+  __shared__ double red[8];
   const int s = blockIdx.y;
   if (cg_done[s]) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) ++cg_count[s];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0 && tid == 0) ++cg_count[s];
   const double den = ptp[s];
   const float alpha = (den > 0.0 && rr[s] > 0.0) ? float(rr[s] / den) : 0.0f;
   const int ld = w.ld[s];
   const int64_t base = w.off[s];
   const int T = ld / 32;
   const int npair = T * (T + 1) / 2;
+  const int x4 = threadIdx.x * 4, y = threadIdx.y;
   float part = 0.0f;
   for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
     int a = 0, rem = pi;
     while (rem >= T - a) { rem -= T - a; ++a; }
     const int b = a + rem;
+    const int64_t iab = base + int64_t(a * 32 + y) * ld + b * 32 + x4;
+    const int64_t iba = base + int64_t(b * 32 + y) * ld + a * 32 + x4;
+    const float4 wab = *reinterpret_cast<const float4*>(W + iab);
+    const float4 wba = *reinterpret_cast<const float4*>(W + iba);
     __syncthreads();
-    for (int rr2 = threadIdx.y; rr2 < 32; rr2 += blockDim.y) {
-      ta_[rr2][threadIdx.x] = W[base + int64_t(a * 32 + rr2) * ld + b * 32 + threadIdx.x];
-      tb_[rr2][threadIdx.x] = W[base + int64_t(b * 32 + rr2) * ld + a * 32 + threadIdx.x];
+    ta_[y][x4] = wab.x; ta_[y][x4 + 1] = wab.y; ta_[y][x4 + 2] = wab.z; ta_[y][x4 + 3] = wab.w;
+    tb_[y][x4] = wba.x; tb_[y][x4 + 1] = wba.y; tb_[y][x4 + 2] = wba.z; tb_[y][x4 + 3] = wba.w;
+    __syncthreads();
+    {
+      float4 xv = *reinterpret_cast<const float4*>(X + iab);
+      float4 pv = *reinterpret_cast<const float4*>(Pd + iab);
+      float4 rv = *reinterpret_cast<const float4*>(R + iab);
+      const float tp0 = wab.x + tb_[x4][y], tp1 = wab.y + tb_[x4 + 1][y];
+      const float tp2 = wab.z + tb_[x4 + 2][y], tp3 = wab.w + tb_[x4 + 3][y];
+      xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
+      xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
+      rv.x = fmaf(-alpha, tp0, rv.x); rv.y = fmaf(-alpha, tp1, rv.y);
+      rv.z = fmaf(-alpha, tp2, rv.z); rv.w = fmaf(-alpha, tp3, rv.w);
+      *reinterpret_cast<float4*>(X + iab) = xv;
+      *reinterpret_cast<float4*>(R + iab) = rv;
+      part = fmaf(rv.x, rv.x, part); part = fmaf(rv.y, rv.y, part);
+      part = fmaf(rv.z, rv.z, part); part = fmaf(rv.w, rv.w, part);
     }
-    __syncthreads();
-    for (int rr2 = threadIdx.y; rr2 < 32; rr2 += blockDim.y) {
-      {
-        const int64_t i = base + int64_t(a * 32 + rr2) * ld + b * 32 + threadIdx.x;
-        const float tp = ta_[rr2][threadIdx.x] + tb_[threadIdx.x][rr2];
-        X[i] = fmaf(alpha, Pd[i], X[i]);
-        const float r = fmaf(-alpha, tp, R[i]);
-        R[i] = r;
-        part = fmaf(r, r, part);
-      }
-      if (a != b) {
-        const int64_t i = base + int64_t(b * 32 + rr2) * ld + a * 32 + threadIdx.x;
-        const float tp = tb_[rr2][threadIdx.x] + ta_[threadIdx.x][rr2];
-        X[i] = fmaf(alpha, Pd[i], X[i]);
-        const float r = fmaf(-alpha, tp, R[i]);
-        R[i] = r;
-        part = fmaf(r, r, part);
-      }
+    if (a != b) {
+      float4 xv = *reinterpret_cast<const float4*>(X + iba);
+      float4 pv = *reinterpret_cast<const float4*>(Pd + iba);
+      float4 rv = *reinterpret_cast<const float4*>(R + iba);
+      const float tp0 = wba.x + ta_[x4][y], tp1 = wba.y + ta_[x4 + 1][y];
+      const float tp2 = wba.z + ta_[x4 + 2][y], tp3 = wba.w + ta_[x4 + 3][y];
+      xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
+      xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
+      rv.x = fmaf(-alpha, tp0, rv.x); rv.y = fmaf(-alpha, tp1, rv.y);
+      rv.z = fmaf(-alpha, tp2, rv.z); rv.w = fmaf(-alpha, tp3, rv.w);
+      *reinterpret_cast<float4*>(X + iba) = xv;
+      *reinterpret_cast<float4*>(R + iba) = rv;
+      part = fmaf(rv.x, rv.x, part); part = fmaf(rv.y, rv.y, part);
+      part = fmaf(rv.z, rv.z, part); part = fmaf(rv.w, rv.w, part);
     }
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-  if ((threadIdx.x & 31) == 0) red[warp] = double(part);
+  if ((tid & 31) == 0) red[tid >> 5] = double(part);
   __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
+  if (tid == 0) {
     double t = 0.0;
-    for (int q = 0; q < int(blockDim.x * blockDim.y) / 32; ++q) t += red[q];
+    for (int q = 0; q < 8; ++q) t += red[q];
     atomicAdd(&rr_new[s], t);
   }
 }
@@ -476,8 +494,7 @@ dim3 pair_grid(const Wave& wv) {
   int64_t t = 1;
   for (int64_t l : wv.bucket_ld) t = std::max<int64_t>(t, l / 32);
   int64_t np = t * (t + 1) / 2;
-  // one tile pair per block keeps enough loads in flight
-  return dim3(unsigned(std::min<int64_t>(np, 4096)), unsigned(wv.count));
+  return dim3(unsigned(std::min<int64_t>(np, 512)), unsigned(wv.count));
 }
 
 struct MixedState {
@@ -822,7 +839,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         gh.dot_c0 = ptp;
         gh.state = ms->cg_done; gh.skip_state = 1;
         SM_CUDA(launch(gh));
-        k_cg_update_pairs<<<pair_grid(wv), dim3(32, 8), 0, st>>>(wv.dev, b.cw, b.cx, b.cr, b.cp, rr, ptp,
+        k_cg_update_pairs<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cw, b.cx, b.cr, b.cp, rr, ptp,
                                                                  rrn, ms->cg_done, ms->cg_count);
         SM_KCHECK();
         k_cg_dir<<<eg, 256, 0, st>>>(wv.dev, b.cr, b.cp, rr, rrn, b.Y[0], b.Y[1], ms->cg_done);
