@@ -109,48 +109,6 @@ struct SlicePtrs {
   __nv_bfloat16* p[HP_SLICES];
 };
 
-// Row-scaled integer slices (the splitting of Ozaki et al.): for row r with
-// max_c |X_rc| < 2^e,  X_rc = 2^e sum_{p=1..6} t_p 2^{-6p} + O(2^{e-36}), with
-// integers |t_p| <= 63, exact in BF16.  A product of two slice matrices is a sum
-// of integers below 63^2 * ld, exact in the FP32 accumulator for ld <= 4096
-// (two such products for ld <= 2048).
-__global__ void k_slice(WaveDev w, const double* __restrict__ X, SlicePtrs out,
-                        int* __restrict__ rowexp, const int64_t* __restrict__ voff) {
-  const int s = blockIdx.y;
-  const int ld = w.ld[s];
-  const int64_t base = w.off[s];
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const unsigned long long* Xb = reinterpret_cast<const unsigned long long*>(X);
-  for (int r = warp; r < ld; r += nwarps) {
-    const unsigned long long* row = Xb + base + int64_t(r) * ld;
-    // the largest |x| of the row, compared as bit patterns
-    unsigned long long mb = 0;
-    for (int c = lane; c < ld; c += 32) mb = max(mb, row[c] & 0x7FFFFFFFFFFFFFFFull);
-    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-    const int e = mb ? int(mb >> 52) - 1023 + 1 : 0;  // max |x| < 2^e
-    if (lane == 0) rowexp[voff[s] + r] = e;
-    for (int c = lane; c < ld; c += 32) {
-      const unsigned long long b = row[c];
-      const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
-      const int ex = int(a >> 52) - 1023;
-      // fixed = trunc(|x| 2^(36 - e)) = mantissa * 2^(ex - 16 - e), ex < e
-      unsigned long long fixed = 0;
-      const int sh = e - ex + 16;  // right shift, >= 17
-      if ((a >> 52) != 0 && sh < 64)
-        fixed = ((a & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh;
-      const bool neg = (b >> 63) != 0;
-      const int64_t i = base + int64_t(r) * ld + c;
-#pragma unroll
-      for (int q = 0; q < HP_SLICES; ++q) {
-        const int d = int((fixed >> (HP_BITS * (HP_SLICES - 1 - q))) & ((1u << HP_BITS) - 1));
-        out.p[q][i] = __int2bfloat16_rn(neg ? -d : d);
-      }
-    }
-  }
-}
-
 // (+-) I * 2^k as a double with integer operations only: round-to-nearest of
 // the 64-bit integer to 53 bits, exponent set directly (k within the normal
 // range for the values produced here).
@@ -180,6 +138,73 @@ __device__ __forceinline__ double i64_to_f64_scaled(long long I, int k, bool neg
   const unsigned long long bits = (sign << 63) | (static_cast<unsigned long long>(ex + 1023) << 52) |
                                   (mant & 0xFFFFFFFFFFFFFull);
   return __longlong_as_double(static_cast<long long>(bits));
+}
+
+// Row-scaled integer slices (the splitting of Ozaki et al.): for row r with
+// max_c |X_rc| < 2^e,  X_rc = 2^e sum_{p=1..6} t_p 2^{-6p} + O(2^{e-36}), with
+// integers |t_p| <= 63, exact in BF16.  A product of two slice matrices is a sum
+// of integers below 63^2 * ld, exact in the FP32 accumulator for ld <= 4096
+// (two such products for ld <= 2048).
+//
+// Grid mode (submax != nullptr): one exponent e for the whole submatrix, from
+// the largest |X| of the submatrix (bit pattern in submax), and only the top
+// `keep` slices: X is truncated to the grid 2^(e - 6 keep), the truncated
+// value written back to X (still symmetric for a symmetric X) and represented
+// exactly by its slices.  The sign iterate goes through this mode, so that
+// its square needs keep^2 slice products, all exact.
+__global__ void k_slice(WaveDev w, double* X, SlicePtrs out, int* __restrict__ rowexp,
+                        const int64_t* __restrict__ voff, const unsigned long long* __restrict__ submax,
+                        int keep) {
+  const int s = blockIdx.y;
+  const int ld = w.ld[s];
+  const int64_t base = w.off[s];
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long* Xb = reinterpret_cast<unsigned long long*>(X);
+  const bool grid = submax != nullptr;
+  const int drop = HP_BITS * (HP_SLICES - keep);  // low bits cleared in grid mode
+  int eg = 0;
+  if (grid) {
+    const unsigned long long mb = submax[s] & 0x7FFFFFFFFFFFFFFFull;
+    eg = mb ? int(mb >> 52) - 1023 + 1 : 0;
+  }
+  for (int r = warp; r < ld; r += nwarps) {
+    unsigned long long* row = Xb + base + int64_t(r) * ld;
+    int e = eg;
+    if (!grid) {
+      // the largest |x| of the row, compared as bit patterns
+      unsigned long long mb = 0;
+      for (int c = lane; c < ld; c += 32) mb = max(mb, row[c] & 0x7FFFFFFFFFFFFFFFull);
+      for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+      e = mb ? int(mb >> 52) - 1023 + 1 : 0;  // max |x| < 2^e
+    }
+    if (lane == 0) rowexp[voff[s] + r] = e;
+    for (int c = lane; c < ld; c += 32) {
+      const unsigned long long b = row[c];
+      const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+      const int ex = int(a >> 52) - 1023;
+      // fixed = trunc(|x| 2^(36 - e)) = mantissa * 2^(ex - 16 - e), ex < e
+      unsigned long long fixed = 0;
+      const int sh = e - ex + 16;  // right shift, >= 17
+      if ((a >> 52) != 0 && sh < 64)
+        fixed = ((a & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh;
+      const bool neg = (b >> 63) != 0;
+      const int64_t i = base + int64_t(r) * ld + c;
+      if (grid) {
+        fixed = (fixed >> drop) << drop;
+        const double v = i64_to_f64_scaled(static_cast<long long>(fixed), e - HP_BITS * HP_SLICES, neg);
+        row[c] = static_cast<unsigned long long>(__double_as_longlong(v));
+      }
+#pragma unroll
+      for (int q = 0; q < HP_SLICES; ++q) {
+        if (q < keep) {
+          const int d = int((fixed >> (HP_BITS * (HP_SLICES - 1 - q))) & ((1u << HP_BITS) - 1));
+          out.p[q][i] = __int2bfloat16_rn(neg ? -d : d);
+        }
+      }
+    }
+  }
 }
 
 // T = sign * I * 2^(e_row + f_col - 6 L) + diag * I_n   (I: the exact int64 sum)
@@ -228,17 +253,35 @@ __global__ void k_rescale_split(WaveDev w, __nv_bfloat16* xh, __nv_bfloat16* xl,
 }
 
 // Bring every final iterate to parity 0 and widen it: S = hi + lo (FP64).
+__device__ __forceinline__ void block_max_bits(float mx, unsigned long long* out) {
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int q = 0; q < int(blockDim.x) / 32; ++q) t = fmaxf(t, red[q]);
+    // the FP32 value widened exactly: its bit pattern orders like the value
+    atomicMax(out, (unsigned long long)__double_as_longlong(f2d_exact(t)));
+  }
+}
+
+// ... and submax[s] = max |S| of the submatrix (bit pattern of a bound >= it)
 __global__ void k_widen(WaveDev w, const int* __restrict__ par, __nv_bfloat16* x0h, __nv_bfloat16* x0l,
                         const __nv_bfloat16* __restrict__ x1h, const __nv_bfloat16* __restrict__ x1l,
-                        double* __restrict__ S) {
+                        double* __restrict__ S, unsigned long long* submax) {
   const bool one = par[blockIdx.y] != 0;
+  float mx = 0.0f;
   FOR_SUB_ELEMS(w) {
     const int64_t i = base + e;
     __nv_bfloat16 h = one ? x1h[i] : x0h[i];
     __nv_bfloat16 l = one ? x1l[i] : x0l[i];
     if (one) { x0h[i] = h; x0l[i] = l; }
-    S[i] = f2d_exact(__bfloat162float(h) + __bfloat162float(l));  // exact: exponents 8+ apart
+    const float v = __bfloat162float(h) + __bfloat162float(l);  // exact: exponents 8+ apart
+    S[i] = f2d_exact(v);
+    mx = fmaxf(mx, fabsf(v));
   }
+  block_max_bits(mx, &submax[blockIdx.y]);
 }
 
 __global__ void k_split64(WaveDev w, const double* __restrict__ src, __nv_bfloat16* hi, __nv_bfloat16* lo) {
@@ -422,22 +465,31 @@ __global__ void k_cg_check(int nsub, const double* rr, const double* rr0, int* c
 
 // S <- S - F_c - F_a, and corr_s = max |F_c + F_a| (bits of a non-negative double)
 __global__ void k_apply(WaveDev w, double* __restrict__ S, const float* __restrict__ Fc,
-                        const float* __restrict__ Fa, unsigned long long* corr) {
+                        const float* __restrict__ Fa, unsigned long long* corr, unsigned long long* submax) {
   __shared__ double red[32];
+  __shared__ unsigned long long redb[32];
   float mx = 0.0f;
+  unsigned long long mb = 0;
   FOR_SUB_ELEMS(w) {
     const int64_t i = base + e;
     const float f = Fc[i] + Fa[i];
-    S[i] = S[i] - f2d_exact(f);
+    const double v = S[i] - f2d_exact(f);
+    S[i] = v;
     mx = fmaxf(mx, fabsf(f));
+    mb = max(mb, static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull);
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = double(mx);
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  }
+  if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = double(mx); redb[threadIdx.x >> 5] = mb; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int q = 0; q < int(blockDim.x) / 32; ++q) t = fmax(t, red[q]);
+    unsigned long long tb = 0;
+    for (int q = 0; q < int(blockDim.x) / 32; ++q) { t = fmax(t, red[q]); tb = max(tb, redb[q]); }
     atomicMax(&corr[blockIdx.y], (unsigned long long)__double_as_longlong(t));
+    atomicMax(&submax[blockIdx.y], tb);
   }
 }
 
@@ -506,6 +558,7 @@ struct MixedState {
   double* scal = nullptr;            // per-slot scalars: rr, ptp, rr_new, rr0 (4 x max_wave)
   int* cg_done = nullptr;            // per slot
   int* cg_count = nullptr;           // per slot: CG iterations run (all rounds)
+  unsigned long long* submax = nullptr;  // per slot: bit pattern of max |S|
   int* pick = nullptr;               // per slot: FP64 fallback
   unsigned long long* corr = nullptr;  // per slot: max |correction| of the last round
 };
@@ -568,6 +621,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     SM_TRY(alloc(&ms->cg_count, size_t(max_wave), "CG counts"));
     SM_TRY(alloc(&ms->pick, size_t(max_wave), "fallback flags"));
     SM_TRY(alloc(&ms->corr, size_t(max_wave), "correction sizes"));
+    SM_TRY(alloc(&ms->submax, size_t(max_wave), "iterate maxima"));
   }
   const long long tmo = timeout_cycles_for(2.0);
   const int nsm = num_sms();
@@ -689,7 +743,8 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     std::vector<int> lp_iters(wv.count);
     SM_CUDA(cudaMemcpyAsync(lp_iters.data(), ns.iters, sizeof(int) * wv.count, cudaMemcpyDeviceToHost, st));
     SM_CUDA(cudaMemsetAsync(ms->cg_count, 0, sizeof(int) * max_wave, st));
-    k_widen<<<eg, 256, 0, st>>>(wv.dev, ns.par, b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.S);
+    SM_CUDA(cudaMemsetAsync(ms->submax, 0, sizeof(unsigned long long) * max_wave, st));
+    k_widen<<<eg, 256, 0, st>>>(wv.dev, ns.par, b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.S, ms->submax);
     SM_KCHECK();
     k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
     SM_KCHECK();
@@ -706,15 +761,15 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     // C (+)= sign * X Y^T from the slices: level t = p + q weighs 2^(-6 t); each
     // launch sums at most per_acc products of one level in one exact accumulator
     int hp_launch_products = 0;  // slice products issued (all residual products, this wave)
-    auto hp_product = [&](const int* xs, const int* ys, const int* ex, const int* ey,
+    auto hp_product = [&](const int* xs, int nx, const int* ys, int ny, const int* ex, const int* ey,
                           double* out, int sym, double sign, double diag) -> submat_status {
       bool first = true;
       for (int t = 2; t <= HP_MAX_LEVEL; ++t) {
         int pairs[HP_SLICES][2];
         int np = 0;
-        for (int pp = 1; pp <= HP_SLICES; ++pp) {
+        for (int pp = 1; pp <= nx; ++pp) {
           const int qq = t - pp;
-          if (qq >= 1 && qq <= HP_SLICES) { pairs[np][0] = pp; pairs[np][1] = qq; ++np; }
+          if (qq >= 1 && qq <= ny) { pairs[np][0] = pp; pairs[np][1] = qq; ++np; }
         }
         for (int c0 = 0; c0 < np; c0 += per_acc) {
           const int k = std::min(per_acc, np - c0);
@@ -768,12 +823,16 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     for (int rd = 0; rd < rounds; ++rd) {
       // ---- the two high-precision residual products ----
       // T = I - S^2
+      // the first round puts S on a 24-bit grid (four slices, S^2 exact): the
+      // rounding (<= 2^-24 max|S|) is well below the BF16x3 error that the
+      // round corrects; later rounds, correcting O(1e-9) errors, keep 36 bits
+      const int s_keep = rd == 0 ? 4 : HP_SLICES;
       if (hp_sliced) {
-        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi]);
+        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi], ms->submax, s_keep);
         SM_KCHECK();
         // all tiles: the integer sums are exact, so the result is exactly
         // symmetric without the mirror pass (which costs more than the tiles)
-        SM_TRY(hp_product(S_SETS, S_SETS, ms->rs_x, ms->rs_x, b.T, 0, -1.0, 1.0));
+        SM_TRY(hp_product(S_SETS, s_keep, S_SETS, s_keep, ms->rs_x, ms->rs_x, b.T, 0, -1.0, 1.0));
         k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
         SM_KCHECK();
       } else {
@@ -795,11 +854,11 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       SM_CUDA(launch(g));
       // T = S a
       if (hp_sliced) {
-        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi]);
+        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi], ms->submax, s_keep);
         SM_KCHECK();
-        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.A, sl_a, ms->rs_y, ms->d_voff[wi]);
+        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.A, sl_a, ms->rs_y, ms->d_voff[wi], nullptr, HP_SLICES);
         SM_KCHECK();
-        SM_TRY(hp_product(S_SETS, A_SETS, ms->rs_x, ms->rs_y, b.T, 0, 1.0, 0.0));
+        SM_TRY(hp_product(S_SETS, s_keep, A_SETS, HP_SLICES, ms->rs_x, ms->rs_y, b.T, 0, 1.0, 0.0));
         k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
         SM_KCHECK();
         k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
@@ -858,7 +917,8 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         }
       }
       SM_CUDA(cudaMemsetAsync(ms->corr, 0, sizeof(unsigned long long) * max_wave, st));
-      k_apply<<<eg, 256, 0, st>>>(wv.dev, b.S, b.Fc, b.cx, ms->corr);
+      SM_CUDA(cudaMemsetAsync(ms->submax, 0, sizeof(unsigned long long) * max_wave, st));
+      k_apply<<<eg, 256, 0, st>>>(wv.dev, b.S, b.Fc, b.cx, ms->corr, ms->submax);
       SM_KCHECK();
     }
     // ---- FP64 Newton-Schulz for the submatrices the correction could not settle ----
