@@ -162,6 +162,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--columns", default=None,
                     help="a:b -- evaluate only block columns [a, b) (small cases for profiling)")
+    ap.add_argument("--tile-n-ns", type=int, default=0, choices=[0, 128, 256])
+    ap.add_argument("--tile-n-corr", type=int, default=0, choices=[0, 128, 256])
+    ap.add_argument("--tile-n-hp", type=int, default=0, choices=[0, 128, 256])
     args = ap.parse_args()
 
     cfg_index, desc = WORKLOADS[args.workload]
@@ -198,7 +201,8 @@ def main():
     K = torch.from_numpy(m.vals).to(dev)
     D = torch.empty_like(K)
     columns = tuple(int(x) for x in args.columns.split(":")) if args.columns else None
-    plan = pkg.Plan.from_bsr(m, prec=args.prec, timing=True, columns=columns)
+    plan = pkg.Plan.from_bsr(m, prec=args.prec, timing=True, columns=columns, tile_n_ns=args.tile_n_ns,
+                             tile_n_corr=args.tile_n_corr, tile_n_hp=args.tile_n_hp)
     for _ in range(args.warmup):
         plan.sign(K, m.mu, out=D)
     torch.cuda.synchronize()

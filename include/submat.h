@@ -89,13 +89,15 @@ typedef struct {
                                   contiguous chunk, Section IV-E); 0, 0 = all columns.  The
                                   other block columns of D are left untouched. */
   int hp_mode;                 /* mixed path, the two residual products I - S^2 and S a:
-                                  0: BF16 tensor cores on six row-scaled 6-bit slices per
-                                  operand (exact integer sums, FP64 combination, ~36 bits);
+                                  0: BF16 tensor cores on 6-bit integer slices (S on a 24-bit
+                                  grid: four slices; a row-scaled: six), exact integer sums
+                                  in 64-bit integers, one rounding to FP64;
                                   1: FP64 SIMT GEMM */
   int tile_n_ns;               /* tensor-core output tile width in the Newton-Schulz phase:
                                   0 = chosen per wave, or 128 / 256 */
-  int tile_n_corr;             /* the same for the correction phase (0 = 128, measured best) */
-  int reserved[2];             /* must be zero */
+  int tile_n_corr;             /* the same for the correction phase (0 = 256) */
+  int tile_n_hp;               /* the same for the sliced residual products (0 = 128) */
+  int reserved[1];             /* must be zero */
 } submat_options;
 
 /* Aggregate statistics of the last submat_sign / submat_mu_search call. */

@@ -715,7 +715,8 @@ submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int
       return SUBMAT_ERR_INVALID_ARG;
     }
     if ((o.tile_n_ns != 0 && o.tile_n_ns != 128 && o.tile_n_ns != 256) ||
-        (o.tile_n_corr != 0 && o.tile_n_corr != 128 && o.tile_n_corr != 256)) {
+        (o.tile_n_corr != 0 && o.tile_n_corr != 128 && o.tile_n_corr != 256) ||
+        (o.tile_n_hp != 0 && o.tile_n_hp != 128 && o.tile_n_hp != 256)) {
       submat::set_error("tile widths must be 0, 128 or 256");
       return SUBMAT_ERR_INVALID_ARG;
     }
