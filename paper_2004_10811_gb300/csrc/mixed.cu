@@ -207,24 +207,46 @@ __global__ void k_slice(WaveDev w, double* X, SlicePtrs out, int* __restrict__ r
   }
 }
 
-// T = sign * I * 2^(e_row + f_col - 6 L) + diag * I_n   (I: the exact int64 sum)
-__global__ void k_hp_finalize(WaveDev w, double* __restrict__ T, const int* __restrict__ ex,
-                              const int* __restrict__ ey, const int64_t* __restrict__ voff,
-                              double sign, double diag) {
+// I - S^2 from the symmetric slice sum Z = sum_{p<q} 2 w s_p s_q + sum_p w s_p^2
+// (s_p symmetric, so s_q s_p = (s_p s_q)^T): S^2 = (Z + Z^T) / 2, exact in
+// 64-bit integers (Z + Z^T is even).  Written straight to the BF16 (hi, lo)
+// split that the next product reads.  32x32 tile pairs through shared memory.
+__global__ void k_hp_finalize_sym(WaveDev w, const long long* __restrict__ Z, const int* __restrict__ ex,
+                                  const int64_t* __restrict__ voff, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  __shared__ long long ta_[32][33], tb_[32][33];
   const int s = blockIdx.y;
   const int ld = w.ld[s];
   const int n = w.n[s];
   const int64_t base = w.off[s];
   const int64_t vo = voff[s];
-  long long* I = reinterpret_cast<long long*>(T);
-  const int64_t total = int64_t(ld) * ld;
-  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-       e += int64_t(gridDim.x) * blockDim.x) {
-    const int r = int(e / ld), c = int(e - int64_t(r) * ld);
-    const int k = ex[vo + r] + ey[vo + c] - HP_BITS * HP_MAX_LEVEL;
-    double v = i64_to_f64_scaled(I[base + e], k, sign < 0.0);
-    if (r == c && r < n) v += diag;
-    T[base + e] = v;
+  const int T = ld / 32;
+  const int npair = T * (T + 1) / 2;
+  const int tx = threadIdx.x;
+  for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
+    int a = 0, rem = pi;
+    while (rem >= T - a) { rem -= T - a; ++a; }
+    const int b = a + rem;
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      ta_[r][tx] = Z[base + int64_t(a * 32 + r) * ld + b * 32 + tx];
+      tb_[r][tx] = Z[base + int64_t(b * 32 + r) * ld + a * 32 + tx];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      {
+        const int row = a * 32 + r, col = b * 32 + tx;
+        const long long z = (ta_[r][tx] + tb_[tx][r]) >> 1;
+        double v = i64_to_f64_scaled(z, ex[vo + row] + ex[vo + col] - HP_BITS * HP_MAX_LEVEL, true);
+        if (row == col && row < n) v += 1.0;
+        split2(v, hi, lo, base + int64_t(row) * ld + col);
+      }
+      if (a != b) {
+        const int row = b * 32 + r, col = a * 32 + tx;
+        const long long z = (tb_[r][tx] + ta_[tx][r]) >> 1;
+        const double v = i64_to_f64_scaled(z, ex[vo + row] + ex[vo + col] - HP_BITS * HP_MAX_LEVEL, true);
+        split2(v, hi, lo, base + int64_t(row) * ld + col);
+      }
+    }
   }
 }
 
@@ -295,15 +317,24 @@ __global__ void k_split32(WaveDev w, const float* __restrict__ src, __nv_bfloat1
 // For a 32x32 tile pair (a, b), a <= b, with P = S a (FP64) and W = F_c a (FP32):
 //   M = (P - P^T) - (W - W^T)  -> BF16 split (the commutator [S, a] - [F_c, a])
 //   H = (P + P^T) / 2          -> BF16 split
-__global__ void k_comm(WaveDev w, const double* __restrict__ P, const float* __restrict__ W,
+// P is either FP64 (Pd) or the exact int64 slice sum Z with row exponents ex
+// (rows of S) and ey (columns): P_ij = Z_ij 2^(ex_i + ey_j - 48).
+__global__ void k_comm(WaveDev w, const double* __restrict__ Pd, const long long* __restrict__ Z,
+                       const int* __restrict__ ex, const int* __restrict__ ey,
+                       const int64_t* __restrict__ voff, const float* __restrict__ W,
                        __nv_bfloat16* mh, __nv_bfloat16* ml, __nv_bfloat16* hh, __nv_bfloat16* hl) {
   __shared__ double tp[32][33];
   __shared__ float tw[32][33];
   const int s = blockIdx.y;
   const int ld = w.ld[s];
   const int64_t base = w.off[s];
+  const int64_t vo = Z ? voff[s] : 0;
   const int T = ld / 32;
   const int npair = T * (T + 1) / 2;
+  auto P = [&](int64_t i, int row, int col) -> double {
+    if (!Z) return Pd[i];
+    return i64_to_f64_scaled(Z[i], ex[vo + row] + ey[vo + col] - HP_BITS * HP_MAX_LEVEL, false);
+  };
   for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
     int a = 0, rem = pi;
     while (rem >= T - a) { rem -= T - a; ++a; }
@@ -313,13 +344,13 @@ __global__ void k_comm(WaveDev w, const double* __restrict__ P, const float* __r
       __syncthreads();
       for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
         const int64_t src = base + int64_t(tb * 32 + rr) * ld + ta * 32 + threadIdx.x;
-        tp[rr][threadIdx.x] = P[src];
+        tp[rr][threadIdx.x] = P(src, tb * 32 + rr, ta * 32 + threadIdx.x);
         tw[rr][threadIdx.x] = W[src];
       }
       __syncthreads();
       for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
         const int64_t i = base + int64_t(ta * 32 + rr) * ld + tb * 32 + threadIdx.x;
-        const double p = P[i], pt = tp[threadIdx.x][rr];
+        const double p = P(i, ta * 32 + rr, tb * 32 + threadIdx.x), pt = tp[threadIdx.x][rr];
         const float wv = W[i], wt = tw[threadIdx.x][rr];
         // p - pt cancels to O(delta): the one FP64 operation; the rest in FP32
         split2f(d2f_trunc(p - pt) - (wv - wt), mh, ml, i);
@@ -762,59 +793,72 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     // C (+)= sign * X Y^T from the slices: level t = p + q weighs 2^(-6 t); each
     // launch sums at most per_acc products of one level in one exact accumulator
     int hp_launch_products = 0;  // slice products issued (all residual products, this wave)
-    auto hp_product = [&](const int* xs, int nx, const int* ys, int ny, const int* ex, const int* ey,
-                          double* out, int sym, double sign, double diag) -> submat_status {
+    // out (int64) = sum over kept slice pairs (p, q), p + q <= 8, of
+    // 2^(6 (8 - p - q)) X_p Y_q^T.  sym_pairs (X = Y, symmetric slices): only
+    // p <= q, the p < q ones counted twice; the symmetric part of the sum is
+    // then the full one.  Each launch sums at most per_acc products of one
+    // level and one weight in one exact FP32 accumulator.
+    auto hp_product = [&](const int* xs, int nx, const int* ys, int ny, bool sym_pairs,
+                          double* out) -> submat_status {
       const int saved_bn = bn;
       use_width(opt.tile_n_hp ? opt.tile_n_hp : 128);
       bool first = true;
+      auto issue = [&](const int (*pairs)[2], int k, int shift) -> submat_status {
+        TcGemmParams p;
+        std::memset(&p, 0, sizeof(p));
+        p.items = FULL;
+        p.nitems = NFULL;
+        p.maps = ms->d_maps[wi];
+        p.maps_b = ms->d_maps_b[wi];
+        p.bn = bn;
+        p.nbucket = nbk;
+        p.nmaps = MS_COUNT * nbk;
+        p.na = k; p.nb = k;
+        for (int i = 0; i < k; ++i) {
+          p.a_set[i] = xs[pairs[i][0] - 1];
+          p.b_set[i] = ys[pairs[i][1] - 1];
+          p.prod_a[i] = i; p.prod_b[i] = i; p.prod_acc[i] = 0; p.prod_first[i] = i == 0;
+        }
+        p.nprod = k;
+        p.nacc = 1;
+        p.nstage = tc_pick_stages(k, k, bn);
+        p.tmem_cols = 2 * bn;
+        p.off = wv.dev.off; p.ld = wv.dev.ld; p.n = wv.dev.n;
+        p.skip_state = -1;
+        p.flags = d_flags;
+        p.timeout_cycles = tmo;
+        p.out_i64 = reinterpret_cast<long long*>(out);
+        p.i64_shift = shift;
+        p.f64_accumulate = first ? 0 : 1;
+        const int saved = tc_class;
+        tc_class = KC_TC_HP;
+        const cudaError_t e = launch(p);
+        tc_class = saved;
+        SM_CUDA(e);
+        hp_launch_products += k;
+        first = false;
+        return SUBMAT_OK;
+      };
       for (int t = 2; t <= HP_MAX_LEVEL; ++t) {
         int pairs[HP_SLICES][2];
         int np = 0;
+        int diag_p = 0;
         for (int pp = 1; pp <= nx; ++pp) {
           const int qq = t - pp;
-          if (qq >= 1 && qq <= ny) { pairs[np][0] = pp; pairs[np][1] = qq; ++np; }
+          if (qq < 1 || qq > ny) continue;
+          if (sym_pairs && pp > qq) continue;
+          if (sym_pairs && pp == qq) { diag_p = pp; continue; }
+          pairs[np][0] = pp; pairs[np][1] = qq; ++np;
         }
-        for (int c0 = 0; c0 < np; c0 += per_acc) {
-          const int k = std::min(per_acc, np - c0);
-          TcGemmParams p;
-          std::memset(&p, 0, sizeof(p));
-          p.items = sym ? SYM : FULL;
-          p.nitems = sym ? NSYM : NFULL;
-          p.maps = ms->d_maps[wi];
-          p.maps_b = ms->d_maps_b[wi];
-          p.bn = bn;
-          p.nbucket = nbk;
-          p.nmaps = MS_COUNT * nbk;
-          p.na = k; p.nb = k;
-          for (int i = 0; i < k; ++i) {
-            p.a_set[i] = xs[pairs[c0 + i][0] - 1];
-            p.b_set[i] = ys[pairs[c0 + i][1] - 1];
-            p.prod_a[i] = i; p.prod_b[i] = i; p.prod_acc[i] = 0; p.prod_first[i] = i == 0;
-          }
-          p.nprod = k;
-          p.nacc = 1;
-          p.nstage = tc_pick_stages(k, k, bn);
-          p.tmem_cols = 2 * bn;
-          p.off = wv.dev.off; p.ld = wv.dev.ld; p.n = wv.dev.n;
-          p.skip_state = -1;
-          p.sym = sym;
-          p.flags = d_flags;
-          p.timeout_cycles = tmo;
-          p.out_i64 = reinterpret_cast<long long*>(out);
-          p.i64_shift = HP_BITS * (HP_MAX_LEVEL - t);
-          p.f64_accumulate = first ? 0 : 1;
-          const int saved = tc_class;
-          tc_class = KC_TC_HP;
-          const cudaError_t e = launch(p);
-          tc_class = saved;
-          SM_CUDA(e);
-          hp_launch_products += k;
-          first = false;
+        const int shift = HP_BITS * (HP_MAX_LEVEL - t);
+        for (int c0 = 0; c0 < np; c0 += per_acc)
+          SM_TRY(issue(pairs + c0, std::min(per_acc, np - c0), shift + (sym_pairs ? 1 : 0)));
+        if (diag_p) {
+          const int dp[1][2] = {{diag_p, diag_p}};
+          SM_TRY(issue(dp, 1, shift));
         }
       }
       use_width(saved_bn);
-      k_hp_finalize<<<eg, 256, 0, st>>>(wv.dev, out, ex, ey, ms->d_voff[wi], sign, diag);
-      SM_KCHECK();
       return SUBMAT_OK;
     };
     const int rounds = std::max(1, opt.refine_rounds);
@@ -834,10 +878,13 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       if (hp_sliced) {
         k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi], ms->submax, s_keep);
         SM_KCHECK();
-        // all tiles: the integer sums are exact, so the result is exactly
-        // symmetric without the mirror pass (which costs more than the tiles)
-        SM_TRY(hp_product(S_SETS, s_keep, S_SETS, s_keep, ms->rs_x, ms->rs_x, b.T, 0, -1.0, 1.0));
-        k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
+        SM_TRY(hp_product(S_SETS, s_keep, S_SETS, s_keep, true, b.T));
+        // (I - S^2) straight to its split in Y; S's split goes to Z, leaving
+        // S's slices in X for the product S a
+        k_hp_finalize_sym<<<pair_grid(wv), dim3(32, 8), 0, st>>>(
+            wv.dev, reinterpret_cast<const long long*>(b.T), ms->rs_x, ms->d_voff[wi], b.Y[0], b.Y[1]);
+        SM_KCHECK();
+        k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.Z[0], b.Z[1]);
         SM_KCHECK();
       } else {
         if (rd > 0) {
@@ -849,20 +896,23 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         f.A = b.S; f.B = b.S; f.C0 = nullptr; f.C = b.T;
         f.alpha = -1.0; f.beta = 0.0; f.diag = 1.0; f.sym = 1;
         SM_CUDA(f64(f));
+        k_split64<<<eg, 256, 0, st>>>(wv.dev, b.T, b.Y[0], b.Y[1]);
+        SM_KCHECK();
       }
-      k_split64<<<eg, 256, 0, st>>>(wv.dev, b.T, b.Y[0], b.Y[1]);
-      SM_KCHECK();
       // F_c = -1/2 S (I - S^2)
-      TcGemmParams g = tc(SYM, NSYM, MS_XH0, MS_XL0, MS_YH, MS_YL, 1, -0.5f, 0.0f);
+      TcGemmParams g = tc(SYM, NSYM, hp_sliced ? MS_Z0 : MS_XH0, hp_sliced ? MS_Z1 : MS_XL0, MS_YH, MS_YL, 1,
+                          -0.5f, 0.0f);
       g.out_f32 = b.Fc;
       SM_CUDA(launch(g));
       // T = S a
       if (hp_sliced) {
-        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi], ms->submax, s_keep);
-        SM_KCHECK();
+        if (s_keep > 4) {  // slices 5 and 6 of S lived in Y, now (I - S^2)
+          k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi], ms->submax, s_keep);
+          SM_KCHECK();
+        }
         k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.A, sl_a, ms->rs_y, ms->d_voff[wi], nullptr, HP_SLICES);
         SM_KCHECK();
-        SM_TRY(hp_product(S_SETS, s_keep, A_SETS, HP_SLICES, ms->rs_x, ms->rs_y, b.T, 0, 1.0, 0.0));
+        SM_TRY(hp_product(S_SETS, s_keep, A_SETS, HP_SLICES, false, b.T));
         k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
         SM_KCHECK();
         k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
@@ -881,7 +931,10 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       g3.out_f32 = b.cw;
       SM_CUDA(launch(g3));
       // M = [S, a] - [F_c, a] (split into Y), H = (S a + a S) / 2 (split)
-      k_comm<<<pair_grid(wv), dim3(32, 8), 0, st>>>(wv.dev, b.T, b.cw, b.Y[0], b.Y[1], b.Hh[0], b.Hh[1]);
+      // (the sliced S a is read as its exact int64 sum, scaled on the fly)
+      k_comm<<<pair_grid(wv), dim3(32, 8), 0, st>>>(
+          wv.dev, hp_sliced ? nullptr : b.T, hp_sliced ? reinterpret_cast<const long long*>(b.T) : nullptr,
+          ms->rs_x, ms->rs_y, ms->d_voff[wi], b.cw, b.Y[0], b.Y[1], b.Hh[0], b.Hh[1]);
       SM_KCHECK();
       // C = M S (symmetric to first order) -> CG residual
       TcGemmParams g4 = tc(SYM, NSYM, MS_YH, MS_YL, MS_XH0, MS_XL0, 1, 1.0f, 0.0f);

@@ -78,3 +78,15 @@ def test_sliced_and_fp64_residual_products_agree(pkg):
     d1, _t1, s1 = run(pkg, m, 0.0, hp_mode=1, refine_rounds=1)
     assert s0["refine_fallback"] == 0 and s1["refine_fallback"] == 0
     assert np.max(np.abs(d0 - d1)) < 2e-8
+
+
+@pytest.mark.parametrize("hp_mode", [0, 1])
+def test_two_rounds(pkg, hp_mode):
+    """A second correction round (36-bit grid for the sign iterate, level-cut
+    slice products) lands well inside the FP64 path's 1e-10 bound."""
+    m = make_water(40, 23, 6.0, (4, -1.0, -0.3), (19, 0.3, 1.5), seed=79)
+    want = oracle.density_matrix(m, 0.0, workers=4)
+    got, tr, st = run(pkg, m, 0.0, hp_mode=hp_mode, refine_rounds=2)
+    assert st["refine_rounds"] == 2 and st["refine_fallback"] == 0, st
+    assert np.max(np.abs(got - want)) <= 1e-10
+    assert abs(tr - oracle.trace_bsr(m, want)) / m.n_el <= 1e-10
