@@ -829,7 +829,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         p.timeout_cycles = tmo;
         p.out_i64 = reinterpret_cast<long long*>(out);
         p.i64_shift = shift;
-        p.f64_accumulate = first ? 0 : 1;
+        p.i64_accumulate = first ? 0 : 1;
         const int saved = tc_class;
         tc_class = KC_TC_HP;
         const cudaError_t e = launch(p);

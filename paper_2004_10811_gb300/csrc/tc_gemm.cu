@@ -32,6 +32,11 @@ namespace {
 constexpr int BM = 128, BK = 64;
 constexpr int TILE_BYTES = BM * BK * 2;  // one 128 x 64 BF16 operand tile (A side)
 constexpr int STG_PITCH = 33;            // staged row pitch (32-bit words)
+// integer outputs: one 16-column int64 row segment per thread, rows 144 bytes
+// apart (16-byte aligned for the bulk copy, padded against bank conflicts);
+// the buffer doubles as the 32-bit transpose stage of the mirror
+constexpr int I64_SEG = 16, I64_PITCH = 144;
+constexpr int STG_BYTES = (BM * I64_PITCH > BM * STG_PITCH * 4) ? BM * I64_PITCH : BM * STG_PITCH * 4;
 
 // instruction descriptor: D F32, A and B BF16, both K-major, M = 128, N = BN
 template <int BN>
@@ -194,37 +199,6 @@ __device__ __forceinline__ void store_range(const TcGemmParams& p, int64_t idx, 
   }
 }
 
-// FP64 row segment of a sliced product: v_q = scale * ra * rb[q] * acc_q
-// (+ diag where the element sits on the diagonal), for q in [q_lo, q_hi).
-__device__ __forceinline__ void store_f64(const TcGemmParams& p, int64_t idx, const float* acc, double ra,
-                                          const double* rb, int diag_q, int q_lo, int q_hi) {
-  double* d = p.out_f64 + idx;
-  if (q_lo <= 0 && q_hi >= 32) {
-#pragma unroll
-    for (int q = 0; q < 32; q += 2) {
-      double v0 = p.f64_scale * ra * rb[q] * double(acc[q]);
-      double v1 = p.f64_scale * ra * rb[q + 1] * double(acc[q + 1]);
-      if (q == diag_q) v0 += p.f64_diag;
-      if (q + 1 == diag_q) v1 += p.f64_diag;
-      if (p.f64_accumulate) {
-        const double2 o = *reinterpret_cast<const double2*>(d + q);
-        v0 += o.x;
-        v1 += o.y;
-      }
-      *reinterpret_cast<double2*>(d + q) = make_double2(v0, v1);
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      if (q < q_lo || q >= q_hi) continue;
-      double v = p.f64_scale * ra * rb[q] * double(acc[q]);
-      if (q == diag_q) v += p.f64_diag;
-      if (p.f64_accumulate) v += d[q];
-      d[q] = v;
-    }
-  }
-}
-
 __device__ __forceinline__ void load_c0(const TcGemmParams& p, int64_t idx, float* c) {
   if (p.c0_f32) {
     const float4* s = reinterpret_cast<const float4*>(p.c0_f32 + idx);
@@ -261,7 +235,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
   const int stage_bytes = p.na * TILE_BYTES + p.nb * TILE_B;
   uint8_t* tiles = smem;
   uint32_t* stg = reinterpret_cast<uint32_t*>(tiles + size_t(p.nstage) * stage_bytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + BM * STG_PITCH);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(stg) + STG_BYTES);
   uint64_t* full = bars;
   uint64_t* empty = bars + p.nstage;
   uint64_t* tfull = empty + p.nstage;
@@ -449,93 +423,33 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
         const bool inside = (rg < ld) && (cg0 < ld);
         if (p.out_i64) {
           // exact integer sums of slice products, accumulated in 64-bit integers
-          const long long mul = 1LL << p.i64_shift;
+          // (full tiles only: no mirror, no diagonal mask).  Each 16-column row
+          // segment is staged in shared memory and handed to a bulk copy (first
+          // product) or a bulk add in L2 (later ones): no loads on the SM.
           if (inside) {
-            long long* d = p.out_i64 + base + int64_t(rg) * ld + cg0;
-            const int q_lo = diag_sym ? r - c * 32 : 0;
-            if (q_lo <= 0) {
+            const long long mul = 1LL << p.i64_shift;
+            uint8_t* srow = reinterpret_cast<uint8_t*>(stg) + r * I64_PITCH;
 #pragma unroll
-              for (int q = 0; q < 32; q += 2) {
-                long long v0 = (long long)__float2int_rn(acc[c * 32 + q]) * mul;
-                long long v1 = (long long)__float2int_rn(acc[c * 32 + q + 1]) * mul;
-                if (p.f64_accumulate) {
-                  const longlong2 o = *reinterpret_cast<const longlong2*>(d + q);
-                  v0 += o.x;
-                  v1 += o.y;
-                }
-                *reinterpret_cast<longlong2*>(d + q) = make_longlong2(v0, v1);
-              }
-            } else {
+            for (int seg = 0; seg < 32 / I64_SEG; ++seg) {
+              // the previous bulk operation of this thread has read its source
+              asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 #pragma unroll
-              for (int q = 0; q < 32; ++q) {
-                if (q >= q_lo) {
-                  long long v = (long long)__float2int_rn(acc[c * 32 + q]) * mul;
-                  if (p.f64_accumulate) v += d[q];
-                  d[q] = v;
-                }
+              for (int q = 0; q < I64_SEG; ++q) {
+                const long long v = (long long)__float2int_rn(acc[c * 32 + seg * I64_SEG + q]) * mul;
+                *reinterpret_cast<long long*>(srow + 8 * q) = v;
               }
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+              long long* d = p.out_i64 + base + int64_t(rg) * ld + cg0 + seg * I64_SEG;
+              if (p.i64_accumulate)
+                asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], %2;" ::"l"(d),
+                             "r"(smem_u32(srow)), "n"(I64_SEG * 8)
+                             : "memory");
+              else
+                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(d),
+                             "r"(smem_u32(srow)), "n"(I64_SEG * 8)
+                             : "memory");
+              asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             }
-          }
-          if (mirror) {
-#pragma unroll
-            for (int q = 0; q < 32; ++q) stg[r * STG_PITCH + q] = __float_as_uint(acc[c * 32 + q]);
-            epi_bar();
-            const int t = threadIdx.x - 64;
-            const int q = t >> 2, part4 = t & 3;
-            const int mrow = sub_tj * 128 + c * 32 + q;
-            const int mcol0 = item.y * BM + part4 * 32;
-            if (mrow < ld && mcol0 < ld) {
-              const int hi = diag_sym ? c * 32 + q - part4 * 32 : 32;
-              long long* d = p.out_i64 + base + int64_t(mrow) * ld + mcol0;
-#pragma unroll
-              for (int i = 0; i < 32; ++i) {
-                if (i >= hi) continue;
-                long long v = (long long)__float2int_rn(__uint_as_float(stg[(part4 * 32 + i) * STG_PITCH + q])) * mul;
-                if (p.f64_accumulate) v += d[i];
-                d[i] = v;
-              }
-            }
-            epi_bar();
-          }
-          continue;
-        }
-        if (p.out_f64) {
-          // sliced high-precision product: scale the exact integer sums in FP64
-          if (inside) {
-            const int64_t vo = p.voff[s];
-            const double ra = p.rowscale_a[vo + rg];
-            const int dq = (rg < n) ? rg - cg0 : -1;
-            store_f64(p, base + int64_t(rg) * ld + cg0, acc + c * 32, ra, p.rowscale_b + vo + cg0,
-                      (dq >= 0 && dq < 32) ? dq : -1, diag_sym ? r - c * 32 : 0, 32);
-          }
-          if (mirror) {
-#pragma unroll
-            for (int q = 0; q < 32; ++q) stg[r * STG_PITCH + q] = __float_as_uint(acc[c * 32 + q]);
-            epi_bar();
-            const int t = threadIdx.x - 64;
-            const int q = t >> 2, part4 = t & 3;
-            const int mrow = sub_tj * 128 + c * 32 + q;
-            const int mcol0 = item.y * BM + part4 * 32;
-            if (mrow < ld && mcol0 < ld) {
-              float w[32];
-#pragma unroll
-              for (int i = 0; i < 32; ++i) w[i] = __uint_as_float(stg[(part4 * 32 + i) * STG_PITCH + q]);
-              // element (mrow, mcol0 + i) equals element (mcol0 + i, mrow) of the tile:
-              // scales rowscale_a[mcol0 + i] * rowscale_b[mrow]
-              const int64_t vo = p.voff[s];
-              const double* ra_row = p.rowscale_a + vo + mcol0;
-              const double rbm = p.rowscale_b[vo + mrow];
-              const int hi = diag_sym ? c * 32 + q - part4 * 32 : 32;
-              double* d = p.out_f64 + base + int64_t(mrow) * ld + mcol0;
-#pragma unroll
-              for (int i = 0; i < 32; ++i) {
-                if (i >= hi) continue;
-                double v = p.f64_scale * ra_row[i] * rbm * double(w[i]);
-                if (p.f64_accumulate) v += d[i];
-                d[i] = v;
-              }
-            }
-            epi_bar();
           }
           continue;
         }
@@ -598,6 +512,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
         if (lane == 0 && part != 0.0) atomicAdd(p.res2 ? &p.res2[s] : &p.dot_c0[s], part);
       }
     }
+    // bulk copies and adds issued by this thread are complete and visible
+    if (p.out_i64) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
   __syncthreads();
   if (warp == 1) {
@@ -610,7 +526,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
 }  // namespace
 
 int tc_smem_bytes(int na, int nb, int nstage, int bn) {
-  return 1024 + nstage * (na * TILE_BYTES + nb * bn * BK * 2) + BM * STG_PITCH * 4 + (2 * nstage + 5) * 8 +
+  return 1024 + nstage * (na * TILE_BYTES + nb * bn * BK * 2) + STG_BYTES + (2 * nstage + 5) * 8 +
          32;
 }
 
@@ -625,6 +541,7 @@ cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st) {
   if (p.nitems <= 0) return cudaSuccess;
   const int bn = p.bn == 256 ? 256 : 128;
   if (bn == 256 && (p.nacc != 1 || p.tmem_cols != 512 || !p.maps_b)) return cudaErrorInvalidValue;
+  if (p.out_i64 && p.sym) return cudaErrorInvalidValue;  // integer outputs: full tiles only
   const int smem = tc_smem_bytes(p.na, p.nb, p.nstage, bn);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e;

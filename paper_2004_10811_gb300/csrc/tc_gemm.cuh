@@ -44,22 +44,12 @@ struct TcGemmParams {
   const __nv_bfloat16* c0_lo;
   double* res2;                   // optional ||C - I_n||_F^2 per submatrix
   double* dot_c0;                 // optional: 2 <C, C0> per submatrix (C0 = c0_f32, beta unused)
-  // FP64 output (sliced high-precision products): with out_f64 set, the tile
-  // value is  f64_scale * rowscale_a[row] * rowscale_b[col] * acc  (+ f64_diag
-  // on the diagonal of the n x n block), written or, with f64_accumulate,
-  // added to out_f64.  alpha/beta and the other outputs are then unused.
-  double* out_f64;
-  int f64_accumulate;
-  double f64_scale;
-  double f64_diag;
-  const double* rowscale_a;       // per row of the A operand, at voff[s]
-  const double* rowscale_b;       // per row of the B operand (= per column of C)
-  const int64_t* voff;
-  // Exact integer output (sliced products): with out_i64 set, the tile value is
-  // the integer accumulator times 2^i64_shift, written or (f64_accumulate)
-  // added to out_i64; row/column scales are applied later in FP64.
+  // Exact integer output (sliced products, full tiles only): with out_i64 set,
+  // the tile value is the integer accumulator times 2^i64_shift, written or
+  // (i64_accumulate) added to out_i64; row/column scales are applied later.
   long long* out_i64;
   int i64_shift;
+  int i64_accumulate;
   int* flags;
   long long timeout_cycles;
   int test_skip_arrive;           // test hook: epilogue withholds its TMEM release
