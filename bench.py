@@ -165,6 +165,8 @@ def main():
     ap.add_argument("--tile-n-ns", type=int, default=0, choices=[0, 128, 256])
     ap.add_argument("--tile-n-corr", type=int, default=0, choices=[0, 128, 256])
     ap.add_argument("--tile-n-hp", type=int, default=0, choices=[0, 128, 256])
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the plan's default tile widths (autotuning runs unless widths are given)")
     args = ap.parse_args()
 
     cfg_index, desc = WORKLOADS[args.workload]
@@ -203,6 +205,12 @@ def main():
     columns = tuple(int(x) for x in args.columns.split(":")) if args.columns else None
     plan = pkg.Plan.from_bsr(m, prec=args.prec, timing=True, columns=columns, tile_n_ns=args.tile_n_ns,
                              tile_n_corr=args.tile_n_corr, tile_n_hp=args.tile_n_hp)
+    tiles = {"ns": args.tile_n_ns, "correction": args.tile_n_corr, "sliced": args.tile_n_hp, "source": "options"}
+    if args.prec == "mixed" and not args.no_autotune and not (args.tile_n_ns or args.tile_n_corr or args.tile_n_hp):
+        t0 = time.perf_counter()
+        tiles = dict(plan.autotune(K, m.mu, out=D), source="submat_autotune")
+        torch.cuda.synchronize()
+        tiles["autotune_s"] = round(time.perf_counter() - t0, 3)
     for _ in range(args.warmup):
         plan.sign(K, m.mu, out=D)
     torch.cuda.synchronize()
@@ -272,6 +280,7 @@ def main():
         "config": {"workload": args.workload, "description": desc, "prec": args.prec,
                    "n": int(m.n), "nsub": int(m.nblk), "nnzb": int(m.nnzb),
                    "sub_dim_min": int(stats["n_min"]), "sub_dim_max": int(stats["n_max"]), **line_cols,
+                   "tiles": tiles,
                    "l2": "inputs larger than L2 (K %.2f GB, workspace %.1f GB)" % (m.vals.nbytes / 1e9,
                                                                                 stats["workspace_bytes"] / 1e9)},
         "tflops": flops_std / value / 1e12 / world if value > 0 else None,

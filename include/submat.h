@@ -219,6 +219,24 @@ submat_status submat_sign_backward(submat_plan* plan, const double* K_vals, doub
                                    const double* Dbar_vals, double* Kbar_vals,
                                    double* dN_dmu, void* stream);
 
+/*
+ * Tile-shape autotuner (the paper has no counterpart: its GPU runs use cuBLAS).
+ * For a mixed-precision plan, times full evaluations of D(mu) for this K with
+ * CUDA events per kernel class. The candidates are 128- and 256-wide output
+ * tiles for each tensor-core phase: Newton-Schulz, correction split products
+ * and sliced residual products. One untimed warm-up evaluation runs first.
+ * The widths are independent per phase, so the plan keeps the faster width
+ * of each, and later calls of submat_sign use them.
+ *   K_vals      device double[value count]
+ *   D_vals      device double[value count] (caller-owned): receives D(mu)
+ *   tile_n_out  host int[3] or NULL: the chosen widths (NS, correction, sliced)
+ * FP64 and FP32 plans have no tile choice: the call evaluates D once and
+ * reports zeros.  Costs three evaluations; the timing hooks of the `timing`
+ * option are used, whatever its value.
+ */
+submat_status submat_autotune(submat_plan* plan, const double* K_vals, double mu, double* D_vals,
+                              int32_t* tile_n_out, void* stream);
+
 /* Number of doubles in K's (and D's) value array for this plan. */
 int64_t submat_plan_value_count(const submat_plan* plan);
 

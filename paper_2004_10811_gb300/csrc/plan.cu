@@ -626,6 +626,41 @@ void Plan::finish_stats() {
   }
 }
 
+// Tile-width autotuner: a warm-up evaluation, then one evaluation with every
+// tensor-core phase at width 128 and one at 256, timed per kernel class; each
+// phase keeps its faster width.
+submat_status Plan::autotune(const double* K, double mu, double* D, int32_t* chosen, cudaStream_t st) {
+  if (!K || !D) { set_error("K_vals and D_vals must be device pointers"); return SUBMAT_ERR_INVALID_ARG; }
+  if (opt.prec != SUBMAT_MIXED_BF16_REFINE) {
+    SM_TRY(sign(K, mu, D, st));
+    if (chosen) chosen[0] = chosen[1] = chosen[2] = 0;
+    return SUBMAT_OK;
+  }
+  const bool timer_was_on = timer.on;
+  if (gather_bytes.size() != size_t(nblk)) gather_bytes.assign(nblk, 0.0);
+  SM_TRY(sign(K, mu, D, st));  // warm-up: maps, state, caches
+  timer.on = true;
+  const int widths[2] = {128, 256};
+  const int classes[3] = {KC_TC_NS, KC_TC_REF, KC_TC_HP};
+  double ms[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  submat_status status = SUBMAT_OK;
+  for (int w = 0; w < 2 && status == SUBMAT_OK; ++w) {
+    opt.tile_n_ns = opt.tile_n_corr = opt.tile_n_hp = widths[w];
+    status = sign(K, mu, D, st);
+    for (int c = 0; c < 3; ++c) ms[w][c] = stats.kernel_ms[classes[c]];
+  }
+  timer.on = timer_was_on;
+  SM_TRY(status);
+  const int best[3] = {ms[1][0] < ms[0][0] ? 256 : 128, ms[1][1] < ms[0][1] ? 256 : 128,
+                       ms[1][2] < ms[0][2] ? 256 : 128};
+  opt.tile_n_ns = best[0];
+  opt.tile_n_corr = best[1];
+  opt.tile_n_hp = best[2];
+  if (chosen)
+    for (int c = 0; c < 3; ++c) chosen[c] = best[c];
+  return SUBMAT_OK;
+}
+
 submat_status Plan::sign(const double* K, double mu, double* D, cudaStream_t st) {
   if (!K || !D) { set_error("K_vals and D_vals must be device pointers"); return SUBMAT_ERR_INVALID_ARG; }
   reset_stats();
@@ -753,6 +788,16 @@ submat_status submat_sign(submat_plan* plan, const double* K_vals, double mu, do
     if (!plan) { submat::set_error("plan is NULL"); return SUBMAT_ERR_INVALID_ARG; }
     if (!std::isfinite(mu)) { submat::set_error("mu is not finite"); return SUBMAT_ERR_INVALID_ARG; }
     return plan->impl.sign(K_vals, mu, D_vals, static_cast<cudaStream_t>(stream));
+  })
+}
+
+submat_status submat_autotune(submat_plan* plan, const double* K_vals, double mu, double* D_vals,
+                              int32_t* tile_n_out, void* stream) {
+  ABI_GUARD({
+    submat::clear_error();
+    if (!plan) { submat::set_error("plan is NULL"); return SUBMAT_ERR_INVALID_ARG; }
+    if (!std::isfinite(mu)) { submat::set_error("mu is not finite"); return SUBMAT_ERR_INVALID_ARG; }
+    return plan->impl.autotune(K_vals, mu, D_vals, tile_n_out, static_cast<cudaStream_t>(stream));
   })
 }
 

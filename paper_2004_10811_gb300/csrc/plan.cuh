@@ -127,6 +127,7 @@ struct Plan {
                           double* mu_out, double* D, cudaStream_t st);
   submat_status backward(const double* K, double mu, const double* Dbar, double* Kbar,
                          double* dN_dmu, cudaStream_t st);
+  submat_status autotune(const double* K, double mu, double* D, int32_t* chosen, cudaStream_t st);
 
   // internals
   submat_status read_flags(cudaStream_t st, int* out);

@@ -28,7 +28,7 @@ EXPORTS = (
     "submat_options_default", "submat_plan_create", "submat_plan_destroy", "submat_sign",
     "submat_sign_host", "submat_trace", "submat_mu_search", "submat_sign_backward",
     "submat_plan_value_count", "submat_get_stats", "submat_get_sub_stats", "submat_last_error",
-    "submat_debug_tc_gemm", "submat_dense_sign_noalloc",
+    "submat_debug_tc_gemm", "submat_dense_sign_noalloc", "submat_autotune",
 )
 
 
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
     lib.submat_trace.argtypes = [vp, vp, dp, vp]
     lib.submat_mu_search.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, C.c_int, dp, vp, vp]
     lib.submat_sign_backward.argtypes = [vp, vp, C.c_double, vp, vp, dp, vp]
+    lib.submat_autotune.argtypes = [vp, vp, C.c_double, vp, i32p, vp]
     lib.submat_plan_value_count.argtypes = [vp]
     lib.submat_plan_value_count.restype = C.c_int64
     lib.submat_get_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -211,6 +212,20 @@ class Plan:
         st = self._lib.submat_sign(self._h, _devptr(K, "K"), float(mu), _devptr(out, "D"), _stream(stream))
         _check(st, allow=(6,) if allow_not_converged else ())
         return out
+
+    def autotune(self, K, mu, out=None, stream=None):
+        """Time the tensor-core tile widths on this K (submat_autotune) and keep
+        the faster one per phase.  Returns {"ns": w, "correction": w, "sliced": w}
+        (zeros for FP64 / FP32 plans); `out` receives D(mu)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(K)
+        w = np.zeros(3, dtype=np.int32)
+        _check(self._lib.submat_autotune(self._h, _devptr(K, "K"), float(mu), _devptr(out, "D"),
+                                         _ptr(w, C.c_int32), _stream(stream)))
+        if w[0]:  # mirror the plan's new widths in the Python-side options
+            self.options.tile_n_ns, self.options.tile_n_corr, self.options.tile_n_hp = (int(x) for x in w)
+        return {"ns": int(w[0]), "correction": int(w[1]), "sliced": int(w[2])}
 
     def sign_host(self, K, mu, out=None, stream=None):
         """Same with host float64 arrays; host<->device copies happen inside."""

@@ -90,3 +90,20 @@ def test_two_rounds(pkg, hp_mode):
     assert st["refine_rounds"] == 2 and st["refine_fallback"] == 0, st
     assert np.max(np.abs(got - want)) <= 1e-10
     assert abs(tr - oracle.trace_bsr(m, want)) / m.n_el <= 1e-10
+
+
+def test_autotune_picks_widths_and_keeps_parity(pkg):
+    """submat_autotune times 128- and 256-wide tiles per tensor-core phase and
+    keeps a valid choice; D from the tuning run and after it meet the bound."""
+    import torch
+    m = make_water(40, 23, 6.0, (4, -1.0, -0.3), (19, 0.3, 1.5), seed=80)
+    want = oracle.density_matrix(m, 0.0, workers=4)
+    K = torch.from_numpy(m.vals).cuda()
+    with pkg.Plan.from_bsr(m, prec="mixed") as plan:
+        D0 = torch.empty_like(K)
+        w = plan.autotune(K, 0.0, out=D0)
+        assert set(w) == {"ns", "correction", "sliced"} and all(v in (128, 256) for v in w.values()), w
+        assert plan.options.tile_n_ns == w["ns"] and plan.options.tile_n_hp == w["sliced"]
+        D1 = plan.sign(K, 0.0)
+    for D in (D0, D1):
+        assert np.max(np.abs(D.cpu().numpy() - want)) <= TOL_MIXED
