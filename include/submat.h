@@ -189,8 +189,11 @@ submat_status submat_trace(submat_plan* plan, const double* D_vals, double* tr,
 /*
  * Find mu with Tr D(mu) = n_el (canonical adaptation, Section IV-G /
  * Algorithm 1), re-evaluating the submatrix signs at each trial mu.
- * Safeguarded Newton-bisection: Newton steps use dN/dmu from the adjoint when
- * it is above a floor and the step stays inside the bracket, else bisection.
+ * Bisection on a bracket [mu0 - 1.01 b, mu0 + 1.01 b] (b: the largest
+ * spectral bound of the submatrices at mu0), oriented by Tr D(mu0) - n_el.
+ * (At zero temperature dN/dmu = 1/2 sum_j sum_{c in j} L_sign(a_j, I)_cc is
+ * exactly zero for nonsingular a_j -- submat_sign_backward reports it -- so
+ * Newton steps never apply.)
  *   n_el       target electron count;  mu0  starting guess
  *   tol        stop when |Tr D - n_el| <= tol * n_el
  *   max_steps  cap on sign evaluations (>= 1)
