@@ -742,18 +742,21 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     SM_CUDA(cudaEventRecord(ev[1], st));
 
     // ---- BF16x3 Newton-Schulz on the tensor cores ----
+    // X_{k+1} = X_k Z_k with Z_k = 1.5 I - 0.5 X_k^2: the squaring writes Z
+    // (and the residual ||X^2 - I||_F from its raw accumulator), so the
+    // update is a plain product whose epilogue loads nothing
     int cur = 0;
     for (int k = 0; k < opt.max_iter; ++k) {
       TcGemmParams g1 = tc(SYM, NSYM, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
-                           cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0, 1, 1.0f, 0.0f);
+                           cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0, 1, -0.5f, 0.0f);
+      g1.diag = 1.5f;
       g1.out_hi = b.Y[0]; g1.out_lo = b.Y[1];
       g1.res2 = ns.res2;
       g1.state = ns.state; g1.skip_state = ST_DONE;
       SM_CUDA(launch(g1));
       SM_CUDA(launch_ns_update(wv.dev, ns, tol_eff, floor_thr, opt.max_iter, d_flags, st));
       TcGemmParams g2 = tc(SYM, NSYM, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
-                           MS_YH, MS_YL, 1, -0.5f, 1.5f);
-      g2.c0_hi = b.X[cur][0]; g2.c0_lo = b.X[cur][1];
+                           MS_YH, MS_YL, 1, 1.0f, 0.0f);
       g2.out_hi = b.X[cur ^ 1][0]; g2.out_lo = b.X[cur ^ 1][1];
       g2.state = ns.state; g2.skip_state = ST_DONE;
       SM_CUDA(launch(g2));

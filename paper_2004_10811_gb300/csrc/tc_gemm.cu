@@ -458,10 +458,12 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
           const int64_t idx = base + int64_t(rg) * ld + cg0;
           const bool has_c0 = (p.c0_f32 || p.c0_hi) && p.beta != 0.0f && !p.dot_c0;
           if (has_c0 || p.dot_c0) load_c0(p, idx, c0);
+          const int dq = (rg < n) ? rg - cg0 : -1;  // diagonal position in this segment
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
             float v = p.alpha * acc[c * 32 + q];
             if (has_c0) v = fmaf(p.beta, c0[q], v);
+            if (q == dq) v += p.diag;
             o[q] = v;
           }
           if (p.dot_c0) {
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
               const int cg = cg0 + q;
-              const float e = o[q] - ((rg == cg && rg < n) ? 1.0f : 0.0f);
+              const float e = acc[c * 32 + q] - ((rg == cg && rg < n) ? 1.0f : 0.0f);
               pc = fmaf(e, e, pc);
             }
             part += res_weight * double(pc);

@@ -33,8 +33,9 @@ struct TcGemmParams {
   const int32_t* n;
   const int* state;
   int skip_state;
-  // epilogue: C = alpha * acc + beta * C0, written as FP32 or as a BF16 (hi, lo) split
-  float alpha, beta;
+  // epilogue: C = alpha * acc + beta * C0 + diag * I_n, written as FP32 or as
+  // a BF16 (hi, lo) split
+  float alpha, beta, diag;
   int sym;                        // also write the mirrored tile (items have ti <= tj)
   float* out_f32;
   __nv_bfloat16* out_hi;
@@ -42,7 +43,7 @@ struct TcGemmParams {
   const float* c0_f32;
   const __nv_bfloat16* c0_hi;
   const __nv_bfloat16* c0_lo;
-  double* res2;                   // optional ||C - I_n||_F^2 per submatrix
+  double* res2;                   // optional ||acc - I_n||_F^2 per submatrix (before alpha, beta, diag)
   double* dot_c0;                 // optional: 2 <C, C0> per submatrix (C0 = c0_f32, beta unused)
   // Exact integer output (sliced products, full tiles only): with out_i64 set,
   // the tile value is the integer accumulator times 2^i64_shift, written or
