@@ -15,7 +15,7 @@ submat_status validate_pattern_public(int nblk, const int32_t* bs, const int64_t
                                       const int32_t* ci);
 const char* last_error();
 size_t mixed_bytes_per_elem();
-constexpr int kPowerIters = 20;  // power steps of the spectral estimate
+constexpr int kPowerIters = 10;  // power steps of the spectral estimate
 void free_mixed(void* state);
 
 struct Wave {
