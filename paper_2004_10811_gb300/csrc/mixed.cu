@@ -807,49 +807,16 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     // out (int64) = sum over kept slice pairs (p, q), p + q <= 8, of
     // 2^(6 (8 - p - q)) X_p Y_q^T.  sym_pairs (X = Y, symmetric slices): only
     // p <= q, the p < q ones counted twice; the symmetric part of the sum is
-    // then the full one.  Each launch sums at most per_acc products of one
-    // level and one weight in one exact FP32 accumulator.
+    // then the full one.
+    // Products are grouped into exact FP32 accumulators: one level and one
+    // weight each, at most per_acc products.  A launch carries one group, or
+    // two groups whose weights differ by at most 2^6 (two TMEM accumulators,
+    // combined exactly in the epilogue) when their slices fit in <= 6 operand
+    // tiles per stage: fewer launches, so fewer int64 passes.
     auto hp_product = [&](const int* xs, int nx, const int* ys, int ny, bool sym_pairs,
                           double* out) -> submat_status {
-      const int saved_bn = bn;
-      use_width(opt.tile_n_hp ? opt.tile_n_hp : 128);
-      bool first = true;
-      auto issue = [&](const int (*pairs)[2], int k, int shift) -> submat_status {
-        TcGemmParams p;
-        std::memset(&p, 0, sizeof(p));
-        p.items = FULL;
-        p.nitems = NFULL;
-        p.maps = ms->d_maps[wi];
-        p.maps_b = ms->d_maps_b[wi];
-        p.bn = bn;
-        p.nbucket = nbk;
-        p.nmaps = MS_COUNT * nbk;
-        p.na = k; p.nb = k;
-        for (int i = 0; i < k; ++i) {
-          p.a_set[i] = xs[pairs[i][0] - 1];
-          p.b_set[i] = ys[pairs[i][1] - 1];
-          p.prod_a[i] = i; p.prod_b[i] = i; p.prod_acc[i] = 0; p.prod_first[i] = i == 0;
-        }
-        p.nprod = k;
-        p.nacc = 1;
-        p.nstage = tc_pick_stages(k, k, bn);
-        p.tmem_cols = 2 * bn;
-        p.off = wv.dev.off; p.ld = wv.dev.ld; p.n = wv.dev.n;
-        p.skip_state = -1;
-        p.flags = d_flags;
-        p.timeout_cycles = tmo;
-        p.out_i64 = reinterpret_cast<long long*>(out);
-        p.i64_shift = shift;
-        p.i64_accumulate = first ? 0 : 1;
-        const int saved = tc_class;
-        tc_class = KC_TC_HP;
-        const cudaError_t e = launch(p);
-        tc_class = saved;
-        SM_CUDA(e);
-        hp_launch_products += k;
-        first = false;
-        return SUBMAT_OK;
-      };
+      struct Group { int np; int pr[2][2]; int shift; };
+      std::vector<Group> groups;  // decreasing shift
       for (int t = 2; t <= HP_MAX_LEVEL; ++t) {
         int pairs[HP_SLICES][2];
         int np = 0;
@@ -862,12 +829,102 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
           pairs[np][0] = pp; pairs[np][1] = qq; ++np;
         }
         const int shift = HP_BITS * (HP_MAX_LEVEL - t);
-        for (int c0 = 0; c0 < np; c0 += per_acc)
-          SM_TRY(issue(pairs + c0, std::min(per_acc, np - c0), shift + (sym_pairs ? 1 : 0)));
-        if (diag_p) {
-          const int dp[1][2] = {{diag_p, diag_p}};
-          SM_TRY(issue(dp, 1, shift));
+        for (int c0 = 0; c0 < np; c0 += per_acc) {
+          Group gr{};
+          gr.np = std::min(per_acc, np - c0);
+          for (int i = 0; i < gr.np; ++i) { gr.pr[i][0] = pairs[c0 + i][0]; gr.pr[i][1] = pairs[c0 + i][1]; }
+          gr.shift = shift + (sym_pairs ? 1 : 0);
+          groups.push_back(gr);
         }
+        if (diag_p) {
+          Group gr{};
+          gr.np = 1; gr.pr[0][0] = gr.pr[0][1] = diag_p; gr.shift = shift;
+          groups.push_back(gr);
+        }
+      }
+      std::stable_sort(groups.begin(), groups.end(),
+                       [](const Group& x, const Group& y) { return x.shift > y.shift; });
+      // distinct A and B slices of a set of groups
+      auto count_sets = [&](const Group* g0, const Group* g1, int* as, int* na_out, int* bs_, int* nb_out) {
+        int na = 0, nb = 0;
+        for (const Group* g : {g0, g1}) {
+          if (!g) continue;
+          for (int i = 0; i < g->np; ++i) {
+            bool fa = false, fb = false;
+            for (int k = 0; k < na; ++k) fa |= as[k] == g->pr[i][0];
+            for (int k = 0; k < nb; ++k) fb |= bs_[k] == g->pr[i][1];
+            if (!fa) as[na++] = g->pr[i][0];
+            if (!fb) bs_[nb++] = g->pr[i][1];
+          }
+        }
+        *na_out = na;
+        *nb_out = nb;
+      };
+      bool first = true;
+      const int saved_bn = bn;
+      auto issue = [&](const Group* g0, const Group* g1) -> submat_status {
+        use_width(g1 ? 128 : (opt.tile_n_hp ? opt.tile_n_hp : 128));  // two accumulators: 2 x 2 x 128 TMEM columns
+        int as[8], bs_[8], na = 0, nb = 0;
+        count_sets(g0, g1, as, &na, bs_, &nb);
+        TcGemmParams p;
+        std::memset(&p, 0, sizeof(p));
+        p.items = FULL;
+        p.nitems = NFULL;
+        p.maps = ms->d_maps[wi];
+        p.maps_b = ms->d_maps_b[wi];
+        p.bn = bn;
+        p.nbucket = nbk;
+        p.nmaps = MS_COUNT * nbk;
+        p.na = na; p.nb = nb;
+        for (int k = 0; k < na; ++k) p.a_set[k] = xs[as[k] - 1];
+        for (int k = 0; k < nb; ++k) p.b_set[k] = ys[bs_[k] - 1];
+        int np = 0;
+        const Group* gs[2] = {g0, g1};
+        for (int acc = 0; acc < 2; ++acc) {
+          const Group* g = gs[acc];
+          if (!g) continue;
+          for (int i = 0; i < g->np; ++i, ++np) {
+            int ia = 0, ib = 0;
+            while (as[ia] != g->pr[i][0]) ++ia;
+            while (bs_[ib] != g->pr[i][1]) ++ib;
+            p.prod_a[np] = ia; p.prod_b[np] = ib; p.prod_acc[np] = acc; p.prod_first[np] = i == 0;
+          }
+        }
+        p.nprod = np;
+        p.nacc = g1 ? 2 : 1;
+        p.nstage = tc_pick_stages(na, nb, bn);
+        p.tmem_cols = 2 * p.nacc * bn;
+        p.off = wv.dev.off; p.ld = wv.dev.ld; p.n = wv.dev.n;
+        p.skip_state = -1;
+        p.flags = d_flags;
+        p.timeout_cycles = tmo;
+        p.out_i64 = reinterpret_cast<long long*>(out);
+        p.i64_shift = g1 ? g1->shift : g0->shift;
+        p.i64_dshift = g1 ? g0->shift - g1->shift : 0;
+        p.i64_accumulate = first ? 0 : 1;
+        const int saved = tc_class;
+        tc_class = KC_TC_HP;
+        const cudaError_t e = launch(p);
+        tc_class = saved;
+        SM_CUDA(e);
+        hp_launch_products += np;
+        first = false;
+        return SUBMAT_OK;
+      };
+      std::vector<char> used(groups.size(), 0);
+      for (size_t i = 0; i < groups.size(); ++i) {
+        if (used[i]) continue;
+        used[i] = 1;
+        int best = -1, best_tiles = 1 << 30;
+        for (size_t j = i + 1; j < groups.size(); ++j) {
+          if (used[j] || groups[i].shift - groups[j].shift > 6) continue;
+          if (groups[i].np + groups[j].np > 4) continue;
+          int as[8], bs_[8], na = 0, nb = 0;
+          count_sets(&groups[i], &groups[j], as, &na, bs_, &nb);
+          if (na + nb <= 6 && na + nb < best_tiles) { best = int(j); best_tiles = na + nb; }
+        }
+        if (best >= 0) used[best] = 1;
+        SM_TRY(issue(&groups[i], best >= 0 ? &groups[best] : nullptr));
       }
       use_width(saved_bn);
       return SUBMAT_OK;

@@ -392,14 +392,29 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
 #pragma unroll
       for (int c = 0; c < 4; ++c) tmem_ld32(tb + uint32_t(c * 32), acc + c * 32);
       tmem_wait_ld();
-      for (int a = 1; a < p.nacc; ++a) {
+      if (p.out_i64 && p.nacc == 2) {
+        // two exact integer accumulators of adjacent levels: acc0 * 2^d + acc1
+        // (|acc| < 2^24, d <= 6: the sum fits in 31 bits), kept as int bits
         float tmp[32];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          tmem_ld32(tb + uint32_t(a * BN + c * 32), tmp);
+          tmem_ld32(tb + uint32_t(BN + c * 32), tmp);
           tmem_wait_ld();
 #pragma unroll
-          for (int q = 0; q < 32; ++q) acc[c * 32 + q] += tmp[q];
+          for (int q = 0; q < 32; ++q)
+            acc[c * 32 + q] = __int_as_float(__float2int_rn(acc[c * 32 + q]) * (1 << p.i64_dshift) +
+                                             __float2int_rn(tmp[q]));
+        }
+      } else {
+        for (int a = 1; a < p.nacc; ++a) {
+          float tmp[32];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            tmem_ld32(tb + uint32_t(a * BN + c * 32), tmp);
+            tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc[c * 32 + q] += tmp[q];
+          }
         }
       }
       if (h == HALVES - 1) {
@@ -435,7 +450,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
               asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 #pragma unroll
               for (int q = 0; q < I64_SEG; ++q) {
-                const long long v = (long long)__float2int_rn(acc[c * 32 + seg * I64_SEG + q]) * mul;
+                const float x = acc[c * 32 + seg * I64_SEG + q];
+                const long long v = (long long)(p.nacc == 2 ? __float_as_int(x) : __float2int_rn(x)) * mul;
                 *reinterpret_cast<long long*>(srow + 8 * q) = v;
               }
               asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -544,6 +560,8 @@ cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st) {
   const int bn = p.bn == 256 ? 256 : 128;
   if (bn == 256 && (p.nacc != 1 || p.tmem_cols != 512 || !p.maps_b)) return cudaErrorInvalidValue;
   if (p.out_i64 && p.sym) return cudaErrorInvalidValue;  // integer outputs: full tiles only
+  if (p.out_i64 && (p.nacc > 2 || (p.nacc == 2 && (p.i64_dshift < 0 || p.i64_dshift > 6))))
+    return cudaErrorInvalidValue;
   const int smem = tc_smem_bytes(p.na, p.nb, p.nstage, bn);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e;

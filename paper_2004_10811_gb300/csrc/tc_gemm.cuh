@@ -48,8 +48,11 @@ struct TcGemmParams {
   // Exact integer output (sliced products, full tiles only): with out_i64 set,
   // the tile value is the integer accumulator times 2^i64_shift, written or
   // (i64_accumulate) added to out_i64; row/column scales are applied later.
+  // With nacc = 2 the two accumulators hold adjacent levels: the tile value
+  // is (acc0 * 2^i64_dshift + acc1) * 2^i64_shift, 0 <= i64_dshift <= 6.
   long long* out_i64;
   int i64_shift;
+  int i64_dshift;
   int i64_accumulate;
   int* flags;
   long long timeout_cycles;
