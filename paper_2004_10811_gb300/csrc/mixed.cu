@@ -863,9 +863,12 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       bool first = true;
       const int saved_bn = bn;
       auto issue = [&](const Group* g0, const Group* g1) -> submat_status {
-        use_width(g1 ? 128 : (opt.tile_n_hp ? opt.tile_n_hp : 128));  // two accumulators: 2 x 2 x 128 TMEM columns
         int as[8], bs_[8], na = 0, nb = 0;
         count_sets(g0, g1, as, &na, bs_, &nb);
+        // 256-wide tiles when two pipeline stages of the launch's slices fit
+        int w = opt.tile_n_hp ? opt.tile_n_hp : 128;
+        if (w == 256 && tc_smem_bytes(na, nb, 2, 256) > 227 * 1024) w = 128;
+        use_width(w);
         TcGemmParams p;
         std::memset(&p, 0, sizeof(p));
         p.items = FULL;
@@ -893,7 +896,9 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         p.nprod = np;
         p.nacc = g1 ? 2 : 1;
         p.nstage = tc_pick_stages(na, nb, bn);
-        p.tmem_cols = 2 * p.nacc * bn;
+        // TMEM holds 512 columns: two accumulators of 256 columns leave room
+        // for one set only (single-buffered)
+        p.tmem_cols = std::min(512, 2 * p.nacc * bn);
         p.off = wv.dev.off; p.ld = wv.dev.ld; p.n = wv.dev.n;
         p.skip_state = -1;
         p.flags = d_flags;

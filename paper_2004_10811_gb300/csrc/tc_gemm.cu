@@ -270,6 +270,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const long long limit = p.timeout_cycles;
+  // accumulator sets in TMEM: two (MMA of the next tile overlaps the drain of
+  // this one) when they fit, else one (freed as soon as the epilogue has read it)
+  const int nbuf = p.tmem_cols >= 2 * p.nacc * BN ? 2 : 1;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
@@ -322,8 +325,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       const int4 item = p.items[it];
       if (p.state && p.state[item.x] == p.skip_state) continue;
       const int nk = p.ld[item.x] / BK;
-      const int ab = tcount & 1;
-      const uint32_t tph = uint32_t(tcount >> 1) & 1u;
+      const int ab = nbuf == 2 ? (tcount & 1) : 0;
+      const uint32_t tph = nbuf == 2 ? (uint32_t(tcount >> 1) & 1u) : (uint32_t(tcount) & 1u);
       if (!mbar_wait(&tempty[ab], tph ^ 1u, abort_flag, limit)) { ok = false; break; }
       tc_fence_after();
       const uint32_t dbase = tmem_base + uint32_t(ab * p.nacc * BN);
@@ -365,8 +368,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       const int4 item = p.items[it];
       const int s = item.x;
       if (p.state && p.state[s] == p.skip_state) continue;
-      const int ab = tcount & 1;
-      const uint32_t tph = uint32_t(tcount >> 1) & 1u;
+      const int ab = nbuf == 2 ? (tcount & 1) : 0;
+      const uint32_t tph = nbuf == 2 ? (uint32_t(tcount >> 1) & 1u) : (uint32_t(tcount) & 1u);
       // one bounded wait, result shared, so the four warps leave together
       if (threadIdx.x == 64) {
         const bool got = mbar_wait(&tfull[ab], tph, abort_flag, limit);
@@ -558,7 +561,9 @@ int tc_pick_stages(int na, int nb, int bn) {
 cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st) {
   if (p.nitems <= 0) return cudaSuccess;
   const int bn = p.bn == 256 ? 256 : 128;
-  if (bn == 256 && (p.nacc != 1 || p.tmem_cols != 512 || !p.maps_b)) return cudaErrorInvalidValue;
+  if (bn == 256 && (p.tmem_cols != 512 || !p.maps_b || !(p.nacc == 1 || (p.nacc == 2 && p.out_i64))))
+    return cudaErrorInvalidValue;
+  if (p.nacc * bn > p.tmem_cols) return cudaErrorInvalidValue;
   if (p.out_i64 && p.sym) return cudaErrorInvalidValue;  // integer outputs: full tiles only
   if (p.out_i64 && (p.nacc > 2 || (p.nacc == 2 && (p.i64_dshift < 0 || p.i64_dshift > 6))))
     return cudaErrorInvalidValue;

@@ -19,7 +19,8 @@ struct TcGemmParams {
   int nitems;
   const CUtensorMap* maps;  // device array [set][bucket], 128-row boxes (A operands; B when bn = 128)
   const CUtensorMap* maps_b;  // same sets with 256-row boxes (B operands when bn = 256)
-  int bn;                   // output tile width: 128 or 256 (then nacc = 1, tmem_cols = 512)
+  int bn;                   // output tile width: 128 or 256 (then tmem_cols = 512: nacc = 1 double-
+                            // buffered, or nacc = 2 integer accumulators single-buffered)
   int nbucket, nmaps;
   int na, nb;               // A-side and B-side operand slices per k-block
   int a_set[TC_MAX_SLOTS];  // tensor-map set of each A slice
