@@ -330,17 +330,24 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       if (!mbar_wait(&tempty[ab], tph ^ 1u, abort_flag, limit)) { ok = false; break; }
       tc_fence_after();
       const uint32_t dbase = tmem_base + uint32_t(ab * p.nacc * BN);
+      // symmetric output, 256-wide tile whose left 128 columns lie below the
+      // diagonal (odd row block): only the right half is wanted, so the MMAs
+      // run at N = 128 on B rows 128..255 into accumulator columns 128..255
+      const bool half = BN == 256 && p.sym && item.z * 2 < item.y;
+      const uint32_t id = half ? idesc<128>() : idesc<BN>();
+      const uint32_t boff = half ? uint32_t(128 * BK * 2) : 0u;
+      const uint32_t doff = half ? 128u : 0u;
       for (int kb = 0; kb < nk; ++kb) {
         if (!mbar_wait(&full[stage], phase, abort_flag, limit)) { ok = false; break; }
         tc_fence_after();
         const uint32_t sb = smem_u32(tiles + size_t(stage) * stage_bytes);
         for (int pr = 0; pr < p.nprod; ++pr) {
           const uint64_t ad = sdesc(sb + uint32_t(p.prod_a[pr] * TILE_BYTES));
-          const uint64_t bd = sdesc(sb + uint32_t(p.na * TILE_BYTES + p.prod_b[pr] * TILE_B));
-          const uint32_t d = dbase + uint32_t(p.prod_acc[pr] * BN);
+          const uint64_t bd = sdesc(sb + uint32_t(p.na * TILE_BYTES + p.prod_b[pr] * TILE_B) + boff);
+          const uint32_t d = dbase + uint32_t(p.prod_acc[pr] * BN) + doff;
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)
-            umma_bf16(d, ad + uint64_t(2 * k), bd + uint64_t(2 * k), idesc<BN>(),
+            umma_bf16(d, ad + uint64_t(2 * k), bd + uint64_t(2 * k), id,
                       (kb > 0 || k > 0 || !p.prod_first[pr]) ? 1u : 0u);
         }
         umma_commit(&empty[stage]);
