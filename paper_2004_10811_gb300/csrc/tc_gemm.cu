@@ -183,9 +183,15 @@ __device__ __forceinline__ void store_row(const TcGemmParams& p, int64_t idx, co
   }
 }
 
-// store o[q] for q in [q_lo, q_hi) only (diagonal tiles of symmetric outputs)
+// store o[q] for q in [q_lo, q_hi) only (diagonal tiles of symmetric outputs):
+// whole segments as vectors, element stores only where the diagonal crosses
 __device__ __forceinline__ void store_range(const TcGemmParams& p, int64_t idx, const float* o,
                                             int q_lo, int q_hi) {
+  if (q_lo >= 32 || q_hi <= 0 || q_lo >= q_hi) return;
+  if (q_lo <= 0 && q_hi >= 32) {
+    store_row(p, idx, o);
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < 32; ++q) {
     if (q < q_lo || q >= q_hi) continue;
@@ -515,9 +521,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
           for (int q = 0; q < 32; ++q) o[q] = 0.0f;
         }
         if (mirror) {
-          // transpose the 128 x 32 chunk through shared memory
+          // transpose the 128 x 32 chunk through shared memory; column q of
+          // row r sits at q ^ 8 (r / 32), so that the row writes and the column
+          // reads below both hit 32 distinct banks
 #pragma unroll
-          for (int q = 0; q < 32; ++q) stg[r * STG_PITCH + q] = __float_as_uint(o[q]);
+          for (int q = 0; q < 32; ++q) stg[r * STG_PITCH + (q ^ (8 * quarter))] = __float_as_uint(o[q]);
           epi_bar();
           const int t = threadIdx.x - 64;
           const int q = t >> 2, part4 = t & 3;
@@ -526,7 +534,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
           if (mrow < ld && mcol0 < ld) {
             float w[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) w[i] = __uint_as_float(stg[(part4 * 32 + i) * STG_PITCH + q]);
+            for (int i = 0; i < 32; ++i) w[i] = __uint_as_float(stg[(part4 * 32 + i) * STG_PITCH + (q ^ (8 * part4))]);
             if (diag_sym) store_range(p, base + int64_t(mrow) * ld + mcol0, w, 0, c * 32 + q - part4 * 32);
             else store_row(p, base + int64_t(mrow) * ld + mcol0, w);
           }
