@@ -158,12 +158,19 @@ __device__ __forceinline__ uint32_t pack_split(float o) {
   return uint32_t(__bfloat16_as_ushort(h)) | (uint32_t(__bfloat16_as_ushort(l)) << 16);
 }
 
-// write 32 values (one row segment) in the output format
+// one 32-byte store (a full L2 sector); the address is 32-byte aligned
+__device__ __forceinline__ void st_v8(void* d, const uint32_t* w) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(d), "r"(w[0]), "r"(w[1]),
+               "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+               : "memory");
+}
+
+// write 32 values (one row segment, 64-byte aligned) in the output format,
+// in whole 32-byte sectors
 __device__ __forceinline__ void store_row(const TcGemmParams& p, int64_t idx, const float* o) {
   if (p.out_f32) {
-    float4* d = reinterpret_cast<float4*>(p.out_f32 + idx);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) d[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    for (int q = 0; q < 4; ++q) st_v8(p.out_f32 + idx + 8 * q, reinterpret_cast<const uint32_t*>(o + 8 * q));
   } else {
     uint32_t hw[16], lw[16];
 #pragma unroll
@@ -172,13 +179,11 @@ __device__ __forceinline__ void store_row(const TcGemmParams& p, int64_t idx, co
       hw[q] = (a & 0xFFFFu) | (b << 16);
       lw[q] = (a >> 16) | (b & 0xFFFF0000u);
     }
-    uint4* dh = reinterpret_cast<uint4*>(p.out_hi + idx);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dh[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+    st_v8(p.out_hi + idx, hw);
+    st_v8(p.out_hi + idx + 16, hw + 8);
     if (p.out_lo) {
-      uint4* dl = reinterpret_cast<uint4*>(p.out_lo + idx);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) dl[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+      st_v8(p.out_lo + idx, lw);
+      st_v8(p.out_lo + idx + 16, lw + 8);
     }
   }
 }
