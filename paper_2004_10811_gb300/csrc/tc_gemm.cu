@@ -212,11 +212,16 @@ __device__ __forceinline__ void store_range(const TcGemmParams& p, int64_t idx, 
 
 __device__ __forceinline__ void load_c0(const TcGemmParams& p, int64_t idx, float* c) {
   if (p.c0_f32) {
-    const float4* s = reinterpret_cast<const float4*>(p.c0_f32 + idx);
+    // whole 32-byte sectors per load
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 v = s[q];
-      c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+    for (int q = 0; q < 4; ++q) {
+      uint32_t w[8];
+      asm volatile("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                   : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+                     "=r"(w[7])
+                   : "l"(p.c0_f32 + idx + 8 * q));
+#pragma unroll
+      for (int e = 0; e < 8; ++e) c[8 * q + e] = __uint_as_float(w[e]);
     }
   } else {
     const uint4* sh = reinterpret_cast<const uint4*>(p.c0_hi + idx);
