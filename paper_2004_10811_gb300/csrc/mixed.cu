@@ -154,7 +154,7 @@ __device__ __forceinline__ double i64_to_f64_scaled(long long I, int k, bool neg
 // its square needs keep^2 slice products, all exact.
 __global__ void k_slice(WaveDev w, double* X, SlicePtrs out, int* __restrict__ rowexp,
                         const int64_t* __restrict__ voff, const unsigned long long* __restrict__ submax,
-                        int keep) {
+                        int keep, __nv_bfloat16* split_hi, __nv_bfloat16* split_lo) {
   const int s = blockIdx.y;
   const int ld = w.ld[s];
   const int64_t base = w.off[s];
@@ -195,6 +195,7 @@ __global__ void k_slice(WaveDev w, double* X, SlicePtrs out, int* __restrict__ r
         fixed = (fixed >> drop) << drop;
         const double v = i64_to_f64_scaled(static_cast<long long>(fixed), e - HP_BITS * HP_SLICES, neg);
         row[c] = static_cast<unsigned long long>(__double_as_longlong(v));
+        if (split_hi) split2(v, split_hi, split_lo, i);  // the BF16 pair of the rounded value
       }
 #pragma unroll
       for (int q = 0; q < HP_SLICES; ++q) {
@@ -948,16 +949,19 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       // rounding (<= 2^-24 max|S|) is well below the BF16x3 error that the
       // round corrects; later rounds, correcting O(1e-9) errors, keep 36 bits
       const int s_keep = rd == 0 ? 4 : HP_SLICES;
+      if (rd > 0) {  // a's split, overwritten by its slices in the previous round
+        k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
+        SM_KCHECK();
+      }
       if (hp_sliced) {
-        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi], ms->submax, s_keep);
+        // slices of S in X (and Y for six), S's BF16 split in Z
+        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi], ms->submax, s_keep,
+                                            b.Z[0], b.Z[1]);
         SM_KCHECK();
         SM_TRY(hp_product(S_SETS, s_keep, S_SETS, s_keep, true, b.T));
-        // (I - S^2) straight to its split in Y; S's split goes to Z, leaving
-        // S's slices in X for the product S a
+        // (I - S^2) straight to its split in Y
         k_hp_finalize_sym<<<pair_grid(wv), dim3(32, 8), 0, st>>>(
             wv.dev, reinterpret_cast<const long long*>(b.T), ms->rs_x, ms->d_voff[wi], b.Y[0], b.Y[1]);
-        SM_KCHECK();
-        k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.Z[0], b.Z[1]);
         SM_KCHECK();
       } else {
         if (rd > 0) {
@@ -972,24 +976,45 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         k_split64<<<eg, 256, 0, st>>>(wv.dev, b.T, b.Y[0], b.Y[1]);
         SM_KCHECK();
       }
+      // S's split: Z (sliced path) or X0 (FP64 path)
+      const int s_hi = hp_sliced ? MS_Z0 : MS_XH0, s_lo = hp_sliced ? MS_Z1 : MS_XL0;
       // F_c = -1/2 S (I - S^2)
-      TcGemmParams g = tc(SYM, NSYM, hp_sliced ? MS_Z0 : MS_XH0, hp_sliced ? MS_Z1 : MS_XL0, MS_YH, MS_YL, 1,
-                          -0.5f, 0.0f);
+      TcGemmParams g = tc(SYM, NSYM, s_hi, s_lo, MS_YH, MS_YL, 1, -0.5f, 0.0f);
       g.out_f32 = b.Fc;
       SM_CUDA(launch(g));
+      // W = F_c a, before S a so that a's split and Y are free for a's slices
+      k_split32<<<eg, 256, 0, st>>>(wv.dev, b.Fc, b.Y[0], b.Y[1]);
+      SM_KCHECK();
+      TcGemmParams g3 = tc(FULL, NFULL, MS_YH, MS_YL, MS_AH, MS_AL, 0, 1.0f, 0.0f);
+      g3.out_f32 = b.cw;
+      SM_CUDA(launch(g3));
       // T = S a
+      int c_hi = s_hi, c_lo = s_lo;  // S's split for C = M S below
       if (hp_sliced) {
-        if (s_keep > 4) {  // slices 5 and 6 of S lived in Y, now (I - S^2)
-          k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi], ms->submax, s_keep);
+        if (s_keep <= 4) {
+          // a's six slices in a's split, H's split and Y (all free now); S's
+          // split stays in Z
+          static const int A_SETS4[HP_SLICES] = {MS_AH, MS_AL, MS_HH, MS_HL, MS_YH, MS_YL};
+          SlicePtrs sl_a4{{b.Ah[0], b.Ah[1], b.Hh[0], b.Hh[1], b.Y[0], b.Y[1]}};
+          k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.A, sl_a4, ms->rs_y, ms->d_voff[wi], nullptr, HP_SLICES,
+                                              nullptr, nullptr);
           SM_KCHECK();
+          SM_TRY(hp_product(S_SETS, s_keep, A_SETS4, HP_SLICES, false, b.T));
+        } else {
+          // six slices of S again (5 and 6 lived in Y), a's slices over Z,
+          // then S's split back in X0
+          k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi], ms->submax, s_keep,
+                                              nullptr, nullptr);
+          SM_KCHECK();
+          k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.A, sl_a, ms->rs_y, ms->d_voff[wi], nullptr, HP_SLICES,
+                                              nullptr, nullptr);
+          SM_KCHECK();
+          SM_TRY(hp_product(S_SETS, s_keep, A_SETS, HP_SLICES, false, b.T));
+          k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
+          SM_KCHECK();
+          c_hi = MS_XH0;
+          c_lo = MS_XL0;
         }
-        k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.A, sl_a, ms->rs_y, ms->d_voff[wi], nullptr, HP_SLICES);
-        SM_KCHECK();
-        SM_TRY(hp_product(S_SETS, s_keep, A_SETS, HP_SLICES, false, b.T));
-        k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
-        SM_KCHECK();
-        k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
-        SM_KCHECK();
       } else {
         GemmF64Args f2{};
         f2.w = wv.dev; f2.items = wv.full64; f2.nitems = wv.n_full64;
@@ -997,12 +1022,6 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         f2.alpha = 1.0; f2.beta = 0.0; f2.diag = 0.0; f2.sym = 0;
         SM_CUDA(f64(f2));
       }
-      k_split32<<<eg, 256, 0, st>>>(wv.dev, b.Fc, b.Y[0], b.Y[1]);
-      SM_KCHECK();
-      // W = F_c a
-      TcGemmParams g3 = tc(FULL, NFULL, MS_YH, MS_YL, MS_AH, MS_AL, 0, 1.0f, 0.0f);
-      g3.out_f32 = b.cw;
-      SM_CUDA(launch(g3));
       // M = [S, a] - [F_c, a] (split into Y), H = (S a + a S) / 2 (split)
       // (the sliced S a is read as its exact int64 sum, scaled on the fly)
       k_comm<<<pair_grid(wv), dim3(32, 8), 0, st>>>(
@@ -1010,7 +1029,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
           ms->rs_x, ms->rs_y, ms->d_voff[wi], b.cw, b.Y[0], b.Y[1], b.Hh[0], b.Hh[1]);
       SM_KCHECK();
       // C = M S (symmetric to first order) -> CG residual
-      TcGemmParams g4 = tc(SYM, NSYM, MS_YH, MS_YL, MS_XH0, MS_XL0, 1, 1.0f, 0.0f);
+      TcGemmParams g4 = tc(SYM, NSYM, MS_YH, MS_YL, c_hi, c_lo, 1, 1.0f, 0.0f);
       g4.out_f32 = b.cr;
       SM_CUDA(launch(g4));
       // CG on L -> H L + L H, per submatrix until the relative residual is below cg_tol
