@@ -34,7 +34,7 @@ long long timeout_cycles_for(double seconds);
 int num_sms();
 
 // bytes of workspace per dense element (see MixedBufs)
-size_t mixed_bytes_per_elem() { return 8 + 8 + 4 + 8 + 8 + 4 + 4 + 4 + 5 * 4; }
+size_t mixed_bytes_per_elem() { return 8 + 8 + 4 + 8 + 8 + 4 + 4 + 4 + 4 * 4; }
 
 namespace {
 
@@ -53,8 +53,7 @@ struct MixedBufs {
   __nv_bfloat16* Z[2];     // two more BF16 operands (slices)
   float* Fc;               // commuting correction
   float* cx;               // CG solution
-  float* cr;               // CG residual
-  float* cp;               // CG direction
+  float* cr;               // CG residual (the direction lives in Y as a BF16 pair)
   float* cw;               // H * direction
 };
 
@@ -74,7 +73,6 @@ MixedBufs carve(void* ws, int64_t E) {
   b.Fc = reinterpret_cast<float*>(take(4));
   b.cx = reinterpret_cast<float*>(take(4));
   b.cr = reinterpret_cast<float*>(take(4));
-  b.cp = reinterpret_cast<float*>(take(4));
   b.cw = reinterpret_cast<float*>(take(4));
   return b;
 }
@@ -380,13 +378,38 @@ __device__ __forceinline__ double block_sum(float v, double* red) {
   return t;
 }
 
+// four consecutive BF16 (hi, lo) pairs <-> four floats (hi + lo)
+__device__ __forceinline__ float4 load_split4(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int64_t i) {
+  const uint2 h = *reinterpret_cast<const uint2*>(hi + i);
+  const uint2 l = *reinterpret_cast<const uint2*>(lo + i);
+  return make_float4(__uint_as_float(h.x << 16) + __uint_as_float(l.x << 16),
+                     __uint_as_float(h.x & 0xFFFF0000u) + __uint_as_float(l.x & 0xFFFF0000u),
+                     __uint_as_float(h.y << 16) + __uint_as_float(l.y << 16),
+                     __uint_as_float(h.y & 0xFFFF0000u) + __uint_as_float(l.y & 0xFFFF0000u));
+}
+
+__device__ __forceinline__ void store_split4(float4 v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
+  const float x[4] = {v.x, v.y, v.z, v.w};
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(x[k]);
+    h[k] = __bfloat16_as_ushort(b);
+    l[k] = __bfloat16_as_ushort(__float2bfloat16_rn(x[k] - __bfloat162float(b)));
+  }
+  *reinterpret_cast<uint2*>(hi + i) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+  *reinterpret_cast<uint2*>(lo + i) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
+}
+
 // CG step 2, fused with the symmetrisation: TP = W + W^T read through 32x32
 // tile pairs; alpha = rr / pTp; X += alpha P; R -= alpha TP; rr_new = <R, R>.
+// P is kept only as the BF16 (hi, lo) pair that the product reads.
 // Block (8, 32): thread (x, y) owns columns 4x..4x+3 of row y of each tile
 // (float4 accesses).
 __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float* __restrict__ W,
                                                          float* __restrict__ X, float* __restrict__ R,
-                                                         const float* __restrict__ Pd, const double* rr,
+                                                         const __nv_bfloat16* __restrict__ ph,
+                                                         const __nv_bfloat16* __restrict__ pl, const double* rr,
                                                          const double* ptp, double* rr_new,
                                                          const int* __restrict__ cg_done, int* cg_count) {
   __shared__ float ta_[32][33], tb_[32][33];
@@ -417,7 +440,7 @@ __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float*
     __syncthreads();
     {
       float4 xv = *reinterpret_cast<const float4*>(X + iab);
-      float4 pv = *reinterpret_cast<const float4*>(Pd + iab);
+      const float4 pv = load_split4(ph, pl, iab);
       float4 rv = *reinterpret_cast<const float4*>(R + iab);
       const float tp0 = wab.x + tb_[x4][y], tp1 = wab.y + tb_[x4 + 1][y];
       const float tp2 = wab.z + tb_[x4 + 2][y], tp3 = wab.w + tb_[x4 + 3][y];
@@ -432,7 +455,7 @@ __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float*
     }
     if (a != b) {
       float4 xv = *reinterpret_cast<const float4*>(X + iba);
-      float4 pv = *reinterpret_cast<const float4*>(Pd + iba);
+      const float4 pv = load_split4(ph, pl, iba);
       float4 rv = *reinterpret_cast<const float4*>(R + iba);
       const float tp0 = wba.x + ta_[x4][y], tp1 = wba.y + ta_[x4 + 1][y];
       const float tp2 = wba.z + ta_[x4 + 2][y], tp3 = wba.w + ta_[x4 + 3][y];
@@ -457,30 +480,35 @@ __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float*
 }
 
 // CG step 3: P = R + (rr_new / rr) P, split for the next product.
-__global__ void k_cg_dir(WaveDev w, const float* __restrict__ R, float* __restrict__ Pd,
-                         const double* rr, const double* rr_new, __nv_bfloat16* ph,
-                         __nv_bfloat16* pl, const int* __restrict__ cg_done) {
-  if (cg_done[blockIdx.y]) return;
-  const double d = rr[blockIdx.y];
-  const float beta = d > 0.0 ? float(rr_new[blockIdx.y] / d) : 0.0f;
-  FOR_SUB_ELEMS(w) {
-    const int64_t i = base + e;
-    const float p = fmaf(beta, Pd[i], R[i]);
-    Pd[i] = p;
-    split2f(p, ph, pl, i);
+__global__ void k_cg_dir(WaveDev w, const float* __restrict__ R, const double* rr, const double* rr_new,
+                         __nv_bfloat16* ph, __nv_bfloat16* pl, const int* __restrict__ cg_done) {
+  const int s = blockIdx.y;
+  if (cg_done[s]) return;
+  const double d = rr[s];
+  const float beta = d > 0.0 ? float(rr_new[s] / d) : 0.0f;
+  const int ld = w.ld[s];
+  const int64_t base = w.off[s];
+  const int64_t total4 = int64_t(ld) * ld / 4;
+  for (int64_t e4 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e4 < total4;
+       e4 += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = base + 4 * e4;
+    const float4 r = *reinterpret_cast<const float4*>(R + i);
+    const float4 p = load_split4(ph, pl, i);
+    store_split4(make_float4(fmaf(beta, p.x, r.x), fmaf(beta, p.y, r.y), fmaf(beta, p.z, r.z),
+                             fmaf(beta, p.w, r.w)),
+                 ph, pl, i);
   }
 }
 
 // CG start: X = 0, R = P = C (already in R), rr = <C, C>, split P.
-__global__ void k_cg_init(WaveDev w, float* __restrict__ X, const float* __restrict__ R,
-                          float* __restrict__ Pd, double* rr, __nv_bfloat16* ph, __nv_bfloat16* pl) {
+__global__ void k_cg_init(WaveDev w, float* __restrict__ X, const float* __restrict__ R, double* rr,
+                          __nv_bfloat16* ph, __nv_bfloat16* pl) {
   __shared__ double red[32];
   float part = 0.0f;
   FOR_SUB_ELEMS(w) {
     const int64_t i = base + e;
     const float r = R[i];
     X[i] = 0.0f;
-    Pd[i] = r;
     split2f(r, ph, pl, i);
     part = fmaf(r, r, part);
   }
@@ -1035,7 +1063,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       // CG on L -> H L + L H, per submatrix until the relative residual is below cg_tol
       SM_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * 4 * max_wave, st));
       SM_CUDA(cudaMemsetAsync(ms->cg_done, 0, sizeof(int) * max_wave, st));
-      k_cg_init<<<eg, 256, 0, st>>>(wv.dev, b.cx, b.cr, b.cp, rr, b.Y[0], b.Y[1]);
+      k_cg_init<<<eg, 256, 0, st>>>(wv.dev, b.cx, b.cr, rr, b.Y[0], b.Y[1]);
       SM_KCHECK();
       SM_CUDA(cudaMemcpyAsync(rr0, rr, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
       for (int it = 0; it < cg_max; ++it) {
@@ -1043,14 +1071,15 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         SM_CUDA(cudaMemsetAsync(ptp, 0, sizeof(double) * 2 * max_wave, st));  // ptp and rr_new
         TcGemmParams gh = tc(FULL, NFULL, MS_HH, MS_HL, MS_YH, MS_YL, 0, 1.0f, 0.0f);
         gh.out_f32 = b.cw;
-        gh.c0_f32 = b.cp;
+        gh.c0_hi = b.Y[0];
+        gh.c0_lo = b.Y[1];
         gh.dot_c0 = ptp;
         gh.state = ms->cg_done; gh.skip_state = 1;
         SM_CUDA(launch(gh));
-        k_cg_update_pairs<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cw, b.cx, b.cr, b.cp, rr, ptp,
-                                                                 rrn, ms->cg_done, ms->cg_count);
+        k_cg_update_pairs<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cw, b.cx, b.cr, b.Y[0], b.Y[1], rr,
+                                                                 ptp, rrn, ms->cg_done, ms->cg_count);
         SM_KCHECK();
-        k_cg_dir<<<eg, 256, 0, st>>>(wv.dev, b.cr, b.cp, rr, rrn, b.Y[0], b.Y[1], ms->cg_done);
+        k_cg_dir<<<eg, 256, 0, st>>>(wv.dev, b.cr, rr, rrn, b.Y[0], b.Y[1], ms->cg_done);
         SM_KCHECK();
         SM_CUDA(cudaMemcpyAsync(rr, rrn, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
         cg_total += 1;
