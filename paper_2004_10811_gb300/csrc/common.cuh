@@ -84,7 +84,7 @@ struct NsStateDev {
 
 // ---- kernel launchers (kernels.cu) ----
 cudaError_t launch_gather(const PatternDev& g, const WaveDev& w, const int2* items, int nitems,
-                          int nb_max, const double* K, double mu, double* A, NsStateDev ns,
+                          int nb_max, int ld_max, const double* K, double mu, double* A, NsStateDev ns,
                           int* flags, cudaStream_t st);
 cudaError_t launch_beta(const WaveDev& w, NsStateDev ns, int beta_mode, cudaStream_t st);
 cudaError_t launch_scale_f64(const WaveDev& w, const double* A, double* X, const double* beta,

@@ -24,12 +24,17 @@ __device__ __forceinline__ double warp_sum(double v) {
 // of the dense a_j = K[N(j), N(j)] - mu I, for local block row t of
 // submatrix s.  One CTA per (s, t); the CTA of the last block row also zeroes
 // the padding rows n_j..ld-1.  Row abs-sums (Gershgorin) and ||a_j||_F^2 are
-// accumulated for the scaling of X_0.
+// accumulated for the scaling of X_0.  A per-column table (where column c of
+// the block row starts in K, and its row stride) is built once in shared
+// memory, so each element costs one table read and one load.
 __global__ void __launch_bounds__(256) k_gather(PatternDev g, WaveDev w, const int2* items,
                                                 const double* __restrict__ K, double mu,
                                                 double* __restrict__ A, NsStateDev ns,
-                                                int* flags) {
-  extern __shared__ int sm[];
+                                                int* flags, int ld_max) {
+  extern __shared__ __align__(8) unsigned char smraw[];
+  long long* colbase = reinterpret_cast<long long*>(smraw);  // [ld_max]: K index of (0, c) or -1
+  int* colstride = reinterpret_cast<int*>(colbase + ld_max);  // [ld_max]
+  int* sm = colstride + ld_max;
   const int2 it = items[blockIdx.x];
   const int s = it.x, t = it.y;
   const int j = w.sub[s];
@@ -64,6 +69,17 @@ __global__ void __launch_bounds__(256) k_gather(PatternDev g, WaveDev w, const i
   const int br = g.bs[i1];
   double* Aj = A + w.off[s];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int u = warp; u < nb; u += nw) {  // one warp per column block
+    const int q = blk[u];
+    const int c0 = loc[u], wd = loc[u + 1] - c0;
+    const long long b0 = q >= 0 ? static_cast<long long>(g.valptr[q]) : -1;
+    const int stride = g.bs[nbr[u]];
+    for (int cc = lane; cc < wd; cc += 32) {
+      colbase[c0 + cc] = q >= 0 ? b0 + cc : -1;
+      colstride[c0 + cc] = stride;
+    }
+  }
+  __syncthreads();
   const int rows_total = br + ((t == nb - 1) ? (ld - n) : 0);
   float fro = 0.0f;  // norms in FP32 (the FP64 pipe is slow); beta gets a margin
   bool bad = false;
@@ -74,17 +90,10 @@ __global__ void __launch_bounds__(256) k_gather(PatternDev g, WaveDev w, const i
       for (int c = lane; c < ld; c += 32) {
         double v = 0.0;
         if (c < n) {
-          int lo = 0, hi = nb - 1;  // largest u with loc[u] <= c
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (loc[mid] <= c) lo = mid; else hi = mid - 1;
-          }
-          const int q = blk[lo];
-          if (q >= 0) {
-            const int i2 = nbr[lo];
-            const int cc = c - loc[lo];
-            v = K[g.valptr[q] + int64_t(rr) * g.bs[i2] + cc];
-            if (i2 == i1 && cc == rr) v -= mu;
+          const long long b = colbase[c];
+          if (b >= 0) {
+            v = K[b + int64_t(rr) * colstride[c]];
+            if (c == r0 + rr) v -= mu;  // same block, same offset: the diagonal
           }
         }
         if (!isfinite(v)) bad = true;
@@ -423,16 +432,16 @@ void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t launch_gather(const PatternDev& g, const WaveDev& w, const int2* items, int nitems,
-                          int nb_max, const double* K, double mu, double* A, NsStateDev ns,
+                          int nb_max, int ld_max, const double* K, double mu, double* A, NsStateDev ns,
                           int* flags, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
-  const size_t smem = size_t(3 * nb_max + 1) * sizeof(int);
+  const size_t smem = size_t(ld_max) * (sizeof(long long) + sizeof(int)) + size_t(3 * nb_max + 1) * sizeof(int);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));
     if (e != cudaSuccess) return e;
   }
-  k_gather<<<nitems, 256, smem, st>>>(g, w, items, K, mu, A, ns, flags);
+  k_gather<<<nitems, 256, smem, st>>>(g, w, items, K, mu, A, ns, flags, ld_max);
   count_launch();
   return cudaGetLastError();
 }

@@ -447,7 +447,7 @@ submat_status Plan::gather_wave(Wave& wv, const double* K, double mu, double* A,
   SM_CUDA(cudaMemsetAsync(ns.fro2, 0, sizeof(double) * wv.count, st));
   size_t tk;
   SM_TRY(timer.start(KC_GATHER, st, &tk));
-  SM_CUDA(launch_gather(g, wv.dev, wv.gather_items, wv.n_gather, nb_max, K, mu, A, ns, d_flags, st));
+  SM_CUDA(launch_gather(g, wv.dev, wv.gather_items, wv.n_gather, nb_max, max_ld(wv), K, mu, A, ns, d_flags, st));
   SM_TRY(timer.stop(tk, st));
   if (timer.on)
     for (int s = 0; s < wv.count; ++s)
