@@ -87,6 +87,29 @@ __device__ __forceinline__ void split2(double v, __nv_bfloat16* hi, __nv_bfloat1
   split2f(d2f_trunc(v), hi, lo, i);
 }
 
+// four consecutive BF16 (hi, lo) pairs <-> four floats (hi + lo)
+__device__ __forceinline__ float4 load_split4(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int64_t i) {
+  const uint2 h = *reinterpret_cast<const uint2*>(hi + i);
+  const uint2 l = *reinterpret_cast<const uint2*>(lo + i);
+  return make_float4(__uint_as_float(h.x << 16) + __uint_as_float(l.x << 16),
+                     __uint_as_float(h.x & 0xFFFF0000u) + __uint_as_float(l.x & 0xFFFF0000u),
+                     __uint_as_float(h.y << 16) + __uint_as_float(l.y << 16),
+                     __uint_as_float(h.y & 0xFFFF0000u) + __uint_as_float(l.y & 0xFFFF0000u));
+}
+
+__device__ __forceinline__ void store_split4(float4 v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
+  const float x[4] = {v.x, v.y, v.z, v.w};
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(x[k]);
+    h[k] = __bfloat16_as_ushort(b);
+    l[k] = __bfloat16_as_ushort(__float2bfloat16_rn(x[k] - __bfloat162float(b)));
+  }
+  *reinterpret_cast<uint2*>(hi + i) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+  *reinterpret_cast<uint2*>(lo + i) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
+}
+
 #define FOR_SUB_ELEMS(w)                                                                 \
   const int s = blockIdx.y;                                                              \
   const int ld = (w).ld[s];                                                              \
@@ -209,42 +232,52 @@ __global__ void k_slice(WaveDev w, double* X, SlicePtrs out, int* __restrict__ r
 // I - S^2 from the symmetric slice sum Z = sum_{p<q} 2 w s_p s_q + sum_p w s_p^2
 // (s_p symmetric, so s_q s_p = (s_p s_q)^T): S^2 = (Z + Z^T) / 2, exact in
 // 64-bit integers (Z + Z^T is even).  Written straight to the BF16 (hi, lo)
-// split that the next product reads.  32x32 tile pairs through shared memory.
-__global__ void k_hp_finalize_sym(WaveDev w, const long long* __restrict__ Z, const int* __restrict__ ex,
-                                  const int64_t* __restrict__ voff, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+// split that the next product reads.  32x32 tile pairs through shared memory;
+// block (8, 32): thread (x, y) owns columns 4x..4x+3 of row y.  S is on one
+// grid per submatrix, so every entry has the scale 2^(2 e - 48).
+__global__ void __launch_bounds__(256) k_hp_finalize_sym(WaveDev w, const long long* __restrict__ Z,
+                                                         const int* __restrict__ ex,
+                                                         const int64_t* __restrict__ voff,
+                                                         __nv_bfloat16* hi, __nv_bfloat16* lo) {
   __shared__ long long ta_[32][33], tb_[32][33];
   const int s = blockIdx.y;
   const int ld = w.ld[s];
   const int n = w.n[s];
   const int64_t base = w.off[s];
-  const int64_t vo = voff[s];
+  const int k2 = 2 * ex[voff[s]] - HP_BITS * HP_MAX_LEVEL;
   const int T = ld / 32;
   const int npair = T * (T + 1) / 2;
-  const int tx = threadIdx.x;
+  const int x4 = threadIdx.x * 4, y = threadIdx.y;
   for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
     int a = 0, rem = pi;
     while (rem >= T - a) { rem -= T - a; ++a; }
     const int b = a + rem;
+    const int64_t iab = base + int64_t(a * 32 + y) * ld + b * 32 + x4;
+    const int64_t iba = base + int64_t(b * 32 + y) * ld + a * 32 + x4;
+    const longlong2 z0 = *reinterpret_cast<const longlong2*>(Z + iab);
+    const longlong2 z1 = *reinterpret_cast<const longlong2*>(Z + iab + 2);
+    const longlong2 z2 = *reinterpret_cast<const longlong2*>(Z + iba);
+    const longlong2 z3 = *reinterpret_cast<const longlong2*>(Z + iba + 2);
     __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-      ta_[r][tx] = Z[base + int64_t(a * 32 + r) * ld + b * 32 + tx];
-      tb_[r][tx] = Z[base + int64_t(b * 32 + r) * ld + a * 32 + tx];
+    ta_[y][x4] = z0.x; ta_[y][x4 + 1] = z0.y; ta_[y][x4 + 2] = z1.x; ta_[y][x4 + 3] = z1.y;
+    tb_[y][x4] = z2.x; tb_[y][x4 + 1] = z2.y; tb_[y][x4 + 2] = z3.x; tb_[y][x4 + 3] = z3.y;
+    __syncthreads();
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long z = (ta_[y][x4 + k] + tb_[x4 + k][y]) >> 1;
+      double d = i64_to_f64_scaled(z, k2, true);
+      if (a == b && y == x4 + k && a * 32 + y < n) d += 1.0;
+      v[k] = d2f_trunc(d);
     }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-      {
-        const int row = a * 32 + r, col = b * 32 + tx;
-        const long long z = (ta_[r][tx] + tb_[tx][r]) >> 1;
-        double v = i64_to_f64_scaled(z, ex[vo + row] + ex[vo + col] - HP_BITS * HP_MAX_LEVEL, true);
-        if (row == col && row < n) v += 1.0;
-        split2(v, hi, lo, base + int64_t(row) * ld + col);
+    store_split4(make_float4(v[0], v[1], v[2], v[3]), hi, lo, iab);
+    if (a != b) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const long long z = (tb_[y][x4 + k] + ta_[x4 + k][y]) >> 1;
+        v[k] = d2f_trunc(i64_to_f64_scaled(z, k2, true));
       }
-      if (a != b) {
-        const int row = b * 32 + r, col = a * 32 + tx;
-        const long long z = (tb_[r][tx] + ta_[tx][r]) >> 1;
-        const double v = i64_to_f64_scaled(z, ex[vo + row] + ex[vo + col] - HP_BITS * HP_MAX_LEVEL, true);
-        split2(v, hi, lo, base + int64_t(row) * ld + col);
-      }
+      store_split4(make_float4(v[0], v[1], v[2], v[3]), hi, lo, iba);
     }
   }
 }
@@ -318,11 +351,13 @@ __global__ void k_split32(WaveDev w, const float* __restrict__ src, __nv_bfloat1
 //   H = (P + P^T) / 2          -> BF16 split
 // P is either FP64 (Pd) or the exact int64 slice sum Z with row exponents ex
 // (rows of S) and ey (columns): P_ij = Z_ij 2^(ex_i + ey_j - 48).  Both
-// 32x32 tiles of a pair are converted once into shared memory.
-__global__ void k_comm(WaveDev w, const double* __restrict__ Pd, const long long* __restrict__ Z,
-                       const int* __restrict__ ex, const int* __restrict__ ey,
-                       const int64_t* __restrict__ voff, const float* __restrict__ W,
-                       __nv_bfloat16* mh, __nv_bfloat16* ml, __nv_bfloat16* hh, __nv_bfloat16* hl) {
+// 32x32 tiles of a pair are converted once into shared memory; block (8, 32):
+// thread (x, y) owns columns 4x..4x+3 of row y.
+__global__ void __launch_bounds__(256) k_comm(WaveDev w, const double* __restrict__ Pd,
+                                              const long long* __restrict__ Z, const int* __restrict__ ex,
+                                              const int* __restrict__ ey, const int64_t* __restrict__ voff,
+                                              const float* __restrict__ W, __nv_bfloat16* mh, __nv_bfloat16* ml,
+                                              __nv_bfloat16* hh, __nv_bfloat16* hl) {
   __shared__ double pa[32][33], pb[32][33];
   __shared__ float wa[32][33], wb[32][33];
   const int s = blockIdx.y;
@@ -331,38 +366,78 @@ __global__ void k_comm(WaveDev w, const double* __restrict__ Pd, const long long
   const int64_t vo = Z ? voff[s] : 0;
   const int T = ld / 32;
   const int npair = T * (T + 1) / 2;
-  const int tx = threadIdx.x;
-  auto P = [&](int row, int col) -> double {
+  const int x4 = threadIdx.x * 4, y = threadIdx.y;
+  // four entries of row `row`, columns col..col+3, into dst
+  auto load4 = [&](int row, int col, double* dst) {
     const int64_t i = base + int64_t(row) * ld + col;
-    if (!Z) return Pd[i];
-    return i64_to_f64_scaled(Z[i], ex[vo + row] + ey[vo + col] - HP_BITS * HP_MAX_LEVEL, false);
+    if (!Z) {
+      const double2 u = *reinterpret_cast<const double2*>(Pd + i);
+      const double2 v = *reinterpret_cast<const double2*>(Pd + i + 2);
+      dst[0] = u.x; dst[1] = u.y; dst[2] = v.x; dst[3] = v.y;
+      return;
+    }
+    const longlong2 u = *reinterpret_cast<const longlong2*>(Z + i);
+    const longlong2 v = *reinterpret_cast<const longlong2*>(Z + i + 2);
+    const long long z[4] = {u.x, u.y, v.x, v.y};
+    const int er = ex[vo + row] - HP_BITS * HP_MAX_LEVEL;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dst[k] = i64_to_f64_scaled(z[k], er + ey[vo + col + k], false);
   };
-  auto emit = [&](int64_t i, double p, double pt, float wv, float wt) {
-    // p - pt cancels to O(delta): the one FP64 operation; the rest in FP32
-    split2f(d2f_trunc(p - pt) - (wv - wt), mh, ml, i);
-    split2f(0.5f * (d2f_trunc(p) + d2f_trunc(pt)), hh, hl, i);
+  // M = (P - P^T) - (W - W^T), H = (P + P^T) / 2 for four entries; p - pt
+  // cancels to O(delta): the one FP64 operation, the rest in FP32
+  auto emit4 = [&](int64_t i, const double* p, const double* pt, const float* wv, const float* wt) {
+    float m[4], h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      m[k] = d2f_trunc(p[k] - pt[k]) - (wv[k] - wt[k]);
+      h[k] = 0.5f * (d2f_trunc(p[k]) + d2f_trunc(pt[k]));
+    }
+    store_split4(make_float4(m[0], m[1], m[2], m[3]), mh, ml, i);
+    store_split4(make_float4(h[0], h[1], h[2], h[3]), hh, hl, i);
   };
   for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
     int a = 0, rem = pi;
     while (rem >= T - a) { rem -= T - a; ++a; }
     const int b = a + rem;
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-      pa[r][tx] = P(a * 32 + r, b * 32 + tx);
-      wa[r][tx] = W[base + int64_t(a * 32 + r) * ld + b * 32 + tx];
-      if (a != b) {
-        pb[r][tx] = P(b * 32 + r, a * 32 + tx);
-        wb[r][tx] = W[base + int64_t(b * 32 + r) * ld + a * 32 + tx];
-      }
+    const int64_t iab = base + int64_t(a * 32 + y) * ld + b * 32 + x4;
+    const int64_t iba = base + int64_t(b * 32 + y) * ld + a * 32 + x4;
+    double p0[4], p1[4];
+    load4(a * 32 + y, b * 32 + x4, p0);
+    const float4 w0 = *reinterpret_cast<const float4*>(W + iab);
+    float4 w1 = w0;
+    if (a != b) {
+      load4(b * 32 + y, a * 32 + x4, p1);
+      w1 = *reinterpret_cast<const float4*>(W + iba);
     }
     __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-      if (a == b) {
-        emit(base + int64_t(a * 32 + r) * ld + a * 32 + tx, pa[r][tx], pa[tx][r], wa[r][tx], wa[tx][r]);
-      } else {
-        emit(base + int64_t(a * 32 + r) * ld + b * 32 + tx, pa[r][tx], pb[tx][r], wa[r][tx], wb[tx][r]);
-        emit(base + int64_t(b * 32 + r) * ld + a * 32 + tx, pb[r][tx], pa[tx][r], wb[r][tx], wa[tx][r]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pa[y][x4 + k] = p0[k];
+    wa[y][x4] = w0.x; wa[y][x4 + 1] = w0.y; wa[y][x4 + 2] = w0.z; wa[y][x4 + 3] = w0.w;
+    if (a != b) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) pb[y][x4 + k] = p1[k];
+      wb[y][x4] = w1.x; wb[y][x4 + 1] = w1.y; wb[y][x4 + 2] = w1.z; wb[y][x4 + 3] = w1.w;
+    }
+    __syncthreads();
+    double pt[4];
+    float wv[4], wt[4];
+    const double (*pT)[33] = a == b ? pa : pb;  // the partner tile, read transposed
+    const float (*wT)[33] = a == b ? wa : wb;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      pt[k] = pT[x4 + k][y];
+      wv[k] = wa[y][x4 + k];
+      wt[k] = wT[x4 + k][y];
+    }
+    emit4(iab, p0, pt, wv, wt);
+    if (a != b) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        pt[k] = pa[x4 + k][y];
+        wv[k] = wb[y][x4 + k];
+        wt[k] = wa[x4 + k][y];
       }
+      emit4(iba, p1, pt, wv, wt);
     }
   }
 }
@@ -376,29 +451,6 @@ __device__ __forceinline__ double block_sum(float v, double* red) {
     for (int q = 0; q < int(blockDim.x) / 32; ++q) t += red[q];
   __syncthreads();
   return t;
-}
-
-// four consecutive BF16 (hi, lo) pairs <-> four floats (hi + lo)
-__device__ __forceinline__ float4 load_split4(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int64_t i) {
-  const uint2 h = *reinterpret_cast<const uint2*>(hi + i);
-  const uint2 l = *reinterpret_cast<const uint2*>(lo + i);
-  return make_float4(__uint_as_float(h.x << 16) + __uint_as_float(l.x << 16),
-                     __uint_as_float(h.x & 0xFFFF0000u) + __uint_as_float(l.x & 0xFFFF0000u),
-                     __uint_as_float(h.y << 16) + __uint_as_float(l.y << 16),
-                     __uint_as_float(h.y & 0xFFFF0000u) + __uint_as_float(l.y & 0xFFFF0000u));
-}
-
-__device__ __forceinline__ void store_split4(float4 v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
-  const float x[4] = {v.x, v.y, v.z, v.w};
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const __nv_bfloat16 b = __float2bfloat16_rn(x[k]);
-    h[k] = __bfloat16_as_ushort(b);
-    l[k] = __bfloat16_as_ushort(__float2bfloat16_rn(x[k] - __bfloat162float(b)));
-  }
-  *reinterpret_cast<uint2*>(hi + i) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
-  *reinterpret_cast<uint2*>(lo + i) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
 }
 
 // CG step 2, fused with the symmetrisation: TP = W + W^T read through 32x32
@@ -988,7 +1040,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         SM_KCHECK();
         SM_TRY(hp_product(S_SETS, s_keep, S_SETS, s_keep, true, b.T));
         // (I - S^2) straight to its split in Y
-        k_hp_finalize_sym<<<pair_grid(wv), dim3(32, 8), 0, st>>>(
+        k_hp_finalize_sym<<<pair_grid(wv), dim3(8, 32), 0, st>>>(
             wv.dev, reinterpret_cast<const long long*>(b.T), ms->rs_x, ms->d_voff[wi], b.Y[0], b.Y[1]);
         SM_KCHECK();
       } else {
@@ -1052,7 +1104,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       }
       // M = [S, a] - [F_c, a] (split into Y), H = (S a + a S) / 2 (split)
       // (the sliced S a is read as its exact int64 sum, scaled on the fly)
-      k_comm<<<pair_grid(wv), dim3(32, 8), 0, st>>>(
+      k_comm<<<pair_grid(wv), dim3(8, 32), 0, st>>>(
           wv.dev, hp_sliced ? nullptr : b.T, hp_sliced ? reinterpret_cast<const long long*>(b.T) : nullptr,
           ms->rs_x, ms->rs_y, ms->d_voff[wi], b.cw, b.Y[0], b.Y[1], b.Hh[0], b.Hh[1]);
       SM_KCHECK();
