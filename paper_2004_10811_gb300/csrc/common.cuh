@@ -95,9 +95,12 @@ cudaError_t launch_ns_update(const WaveDev& w, NsStateDev ns, double tol, double
                              int max_iter, int* flags, cudaStream_t st);
 cudaError_t launch_ns_post(const WaveDev& w, NsStateDev ns, int par_new, int* d_active,
                            cudaStream_t st);
+// corr_a, corr_b, fallback (mixed path, may be null): the extracted entries of
+// S become S - (corr_a + corr_b), except in submatrices with fallback[s] set
 cudaError_t launch_scatter_f64(const PatternDev& g, const WaveDev& w, NsStateDev ns,
                                const double* buf0, const double* buf1, double* D,
-                               double* trpart, int nb_max, cudaStream_t st);
+                               double* trpart, int nb_max, cudaStream_t st, const float* corr_a = nullptr,
+                               const float* corr_b = nullptr, const int* fallback = nullptr);
 cudaError_t launch_scatter_f32(const PatternDev& g, const WaveDev& w, NsStateDev ns,
                                const float* buf0, const float* buf1, double* D,
                                double* trpart, int nb_max, cudaStream_t st);

@@ -203,7 +203,10 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_scatter(PatternDev g, WaveDev w, NsStateDev ns,
                                                  const T* __restrict__ buf0,
                                                  const T* __restrict__ buf1,
-                                                 double* __restrict__ D, double* trpart) {
+                                                 double* __restrict__ D, double* trpart,
+                                                 const float* __restrict__ corr_a,
+                                                 const float* __restrict__ corr_b,
+                                                 const int* __restrict__ fallback) {
   extern __shared__ int sm[];
   __shared__ double red[8];
   const int s = blockIdx.x;
@@ -216,6 +219,11 @@ __global__ void __launch_bounds__(256) k_scatter(PatternDev g, WaveDev w, NsStat
   if (threadIdx.x == 0) loc[nb] = n;
   __syncthreads();
   const T* S = (ns.par[s] ? buf1 : buf0) + w.off[s];
+  // the mixed path's last correction, S - (F_c + F_a), applied here for the
+  // extracted entries only (not for submatrices re-solved in FP64)
+  const bool correct = corr_a && !fallback[s];
+  const float* ca = corr_a ? corr_a + w.off[s] : nullptr;
+  const float* cb = corr_b ? corr_b + w.off[s] : nullptr;
   const int koff = g.koff[j];
   const int bj = g.bs[j];
   double tr = 0.0;
@@ -230,7 +238,9 @@ __global__ void __launch_bounds__(256) k_scatter(PatternDev g, WaveDev w, NsStat
     }
     const int r = col - loc[lo];
     const int64_t p = g.tpos[rp0 + lo];  // block (N(j)[lo], j)
-    const double sv = double(S[int64_t(koff + c) * ld + col]);
+    const int64_t si = int64_t(koff + c) * ld + col;
+    double sv = double(S[si]);
+    if (correct) sv -= f2d_exact(ca[si] + cb[si]);
     const bool diag = (col == koff + c);
     const double v = (diag ? 0.5 : 0.0) - 0.5 * sv;
     D[g.valptr[p] + int64_t(r) * bj + c] = v;
@@ -324,7 +334,24 @@ __global__ void __launch_bounds__(1024) k_power(WaveDev w, const T* __restrict__
     for (int r = warp; r < n; r += nw) {
       const T* row = Xs + int64_t(r) * ld;
       float acc = 0.0f;
-      for (int c = lane; c < n; c += 32) acc = fmaf(float(row[c]), v[c], acc);
+      if constexpr (sizeof(T) == 2) {
+        // eight BF16 per lane and load (padding columns are zero in X and v)
+        for (int c = lane * 8; c < ld; c += 256) {
+          const uint4 q = *reinterpret_cast<const uint4*>(row + c);
+          const float4 v0 = *reinterpret_cast<const float4*>(v + c);
+          const float4 v1 = *reinterpret_cast<const float4*>(v + c + 4);
+          acc = fmaf(__uint_as_float(q.x << 16), v0.x, acc);
+          acc = fmaf(__uint_as_float(q.x & 0xFFFF0000u), v0.y, acc);
+          acc = fmaf(__uint_as_float(q.y << 16), v0.z, acc);
+          acc = fmaf(__uint_as_float(q.y & 0xFFFF0000u), v0.w, acc);
+          acc = fmaf(__uint_as_float(q.z << 16), v1.x, acc);
+          acc = fmaf(__uint_as_float(q.z & 0xFFFF0000u), v1.y, acc);
+          acc = fmaf(__uint_as_float(q.w << 16), v1.z, acc);
+          acc = fmaf(__uint_as_float(q.w & 0xFFFF0000u), v1.w, acc);
+        }
+      } else {
+        for (int c = lane; c < n; c += 32) acc = fmaf(float(row[c]), v[c], acc);
+      }
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) y[r] = acc;
     }
@@ -483,22 +510,24 @@ cudaError_t launch_ns_post(const WaveDev& w, NsStateDev ns, int par_new, int* d_
 template <typename T>
 static cudaError_t scatter_impl(const PatternDev& g, const WaveDev& w, NsStateDev ns,
                                 const T* buf0, const T* buf1, double* D, double* trpart,
-                                int nb_max, cudaStream_t st) {
+                                int nb_max, cudaStream_t st, const float* corr_a = nullptr,
+                                const float* corr_b = nullptr, const int* fallback = nullptr) {
   const size_t smem = size_t(nb_max + 1) * sizeof(int);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_scatter<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
   }
-  k_scatter<T><<<w.nsub, 256, smem, st>>>(g, w, ns, buf0, buf1, D, trpart);
+  k_scatter<T><<<w.nsub, 256, smem, st>>>(g, w, ns, buf0, buf1, D, trpart, corr_a, corr_b, fallback);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_scatter_f64(const PatternDev& g, const WaveDev& w, NsStateDev ns,
                                const double* buf0, const double* buf1, double* D,
-                               double* trpart, int nb_max, cudaStream_t st) {
-  return scatter_impl<double>(g, w, ns, buf0, buf1, D, trpart, nb_max, st);
+                               double* trpart, int nb_max, cudaStream_t st, const float* corr_a,
+                               const float* corr_b, const int* fallback) {
+  return scatter_impl<double>(g, w, ns, buf0, buf1, D, trpart, nb_max, st, corr_a, corr_b, fallback);
 }
 
 cudaError_t launch_scatter_f32(const PatternDev& g, const WaveDev& w, NsStateDev ns,

@@ -613,6 +613,32 @@ __global__ void k_apply(WaveDev w, double* __restrict__ S, const float* __restri
   }
 }
 
+// Last round: only max |F_c + F_a| per submatrix (the scatter applies the
+// correction to the entries it extracts).
+__global__ void k_corr_max(WaveDev w, const float* __restrict__ Fc, const float* __restrict__ Fa,
+                           unsigned long long* corr) {
+  __shared__ float red[32];
+  const int s = blockIdx.y;
+  const int ld = w.ld[s];
+  const int64_t base = w.off[s];
+  const int64_t total4 = int64_t(ld) * ld / 4;
+  float mx = 0.0f;
+  for (int64_t e4 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e4 < total4;
+       e4 += int64_t(gridDim.x) * blockDim.x) {
+    const float4 a = *reinterpret_cast<const float4*>(Fc + base + 4 * e4);
+    const float4 b = *reinterpret_cast<const float4*>(Fa + base + 4 * e4);
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(a.x + b.x), fabsf(a.y + b.y)), fmaxf(fabsf(a.z + b.z), fabsf(a.w + b.w))));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int q = 0; q < int(blockDim.x) / 32; ++q) t = fmaxf(t, red[q]);
+    atomicMax(&corr[s], (unsigned long long)__double_as_longlong(f2d_exact(t)));
+  }
+}
+
 // Submatrices whose last correction was still large, or whose Lyapunov solve
 // did not converge (a gap far smaller than the spectral radius), are
 // re-solved by FP64 Newton-Schulz: state ACTIVE for those, DONE for the rest.
@@ -1149,8 +1175,12 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         }
       }
       SM_CUDA(cudaMemsetAsync(ms->corr, 0, sizeof(unsigned long long) * max_wave, st));
-      SM_CUDA(cudaMemsetAsync(ms->submax, 0, sizeof(unsigned long long) * max_wave, st));
-      k_apply<<<eg, 256, 0, st>>>(wv.dev, b.S, b.Fc, b.cx, ms->corr, ms->submax);
+      if (rd + 1 < rounds) {  // S itself is needed by the next round
+        SM_CUDA(cudaMemsetAsync(ms->submax, 0, sizeof(unsigned long long) * max_wave, st));
+        k_apply<<<eg, 256, 0, st>>>(wv.dev, b.S, b.Fc, b.cx, ms->corr, ms->submax);
+      } else {
+        k_corr_max<<<eg, 256, 0, st>>>(wv.dev, b.Fc, b.cx, ms->corr);
+      }
       SM_KCHECK();
     }
     // ---- FP64 Newton-Schulz for the submatrices the correction could not settle ----
@@ -1181,7 +1211,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     stats.refine_rounds = rounds;
     SM_CUDA(cudaEventRecord(ev[3], st));
     // ---- extract (Section III-A step 3); ns.par picks S or, for fallbacks, S/T ----
-    SM_CUDA(launch_scatter_f64(g, wv.dev, ns, outS0, outS1, D, d_trpart, nb_max, st));
+    SM_CUDA(launch_scatter_f64(g, wv.dev, ns, outS0, outS1, D, d_trpart, nb_max, st, b.Fc, b.cx, ms->pick));
     SM_TRY(collect_wave(wv, st));
     float t01 = 0, t12 = 0, t23 = 0;
     SM_CUDA(cudaEventElapsedTime(&t01, ev[0], ev[1]));
