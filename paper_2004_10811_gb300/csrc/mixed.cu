@@ -453,6 +453,50 @@ __device__ __forceinline__ double block_sum(float v, double* red) {
   return t;
 }
 
+// Complete a symmetric BF16 (hi, lo) pair from its upper triangle: entry
+// (r, c), r > c, takes (c, r).  32x32 tile pairs; block (8, 32).
+__global__ void __launch_bounds__(256) k_mirror_split(WaveDev w, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                                      const int* __restrict__ state, int skip_state) {
+  __shared__ uint32_t th[32][33], tl[32][33];  // BF16 bits of the upper tile
+  const int s = blockIdx.y;
+  if (state && state[s] == skip_state) return;
+  const int ld = w.ld[s];
+  const int64_t base = w.off[s];
+  const int T = ld / 32;
+  const int npair = T * (T + 1) / 2;
+  const int x4 = threadIdx.x * 4, y = threadIdx.y;
+  const unsigned short* h16 = reinterpret_cast<const unsigned short*>(hi);
+  const unsigned short* l16 = reinterpret_cast<const unsigned short*>(lo);
+  for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
+    int a = 0, rem = pi;
+    while (rem >= T - a) { rem -= T - a; ++a; }
+    const int b = a + rem;  // upper tile (a, b), a <= b; lower tile (b, a)
+    const int64_t iab = base + int64_t(a * 32 + y) * ld + b * 32 + x4;
+    const uint2 hv = *reinterpret_cast<const uint2*>(h16 + iab);
+    const uint2 lv = *reinterpret_cast<const uint2*>(l16 + iab);
+    __syncthreads();
+    th[y][x4] = hv.x & 0xFFFFu; th[y][x4 + 1] = hv.x >> 16; th[y][x4 + 2] = hv.y & 0xFFFFu; th[y][x4 + 3] = hv.y >> 16;
+    tl[y][x4] = lv.x & 0xFFFFu; tl[y][x4 + 1] = lv.x >> 16; tl[y][x4 + 2] = lv.y & 0xFFFFu; tl[y][x4 + 3] = lv.y >> 16;
+    __syncthreads();
+    // lower tile (b, a), row y, columns x4..x4+3 = upper (a, b) column y, rows x4..x4+3
+    const int64_t iba = base + int64_t(b * 32 + y) * ld + a * 32 + x4;
+    if (a != b) {
+      *reinterpret_cast<uint2*>(hi + iba) = make_uint2(th[x4][y] | (th[x4 + 1][y] << 16), th[x4 + 2][y] | (th[x4 + 3][y] << 16));
+      *reinterpret_cast<uint2*>(lo + iba) = make_uint2(tl[x4][y] | (tl[x4 + 1][y] << 16), tl[x4 + 2][y] | (tl[x4 + 3][y] << 16));
+    } else {
+      // diagonal tile: only its strict lower triangle (row y > column x4 + k)
+      unsigned short* hd = reinterpret_cast<unsigned short*>(hi) + iba;
+      unsigned short* ld16 = reinterpret_cast<unsigned short*>(lo) + iba;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (y > x4 + k) {
+          hd[k] = static_cast<unsigned short>(th[x4 + k][y]);
+          ld16[k] = static_cast<unsigned short>(tl[x4 + k][y]);
+        }
+    }
+  }
+}
+
 // CG step 2, fused with the symmetrisation: TP = W + W^T read through 32x32
 // tile pairs; alpha = rr / pTp; X += alpha P; R -= alpha TP; rr_new = <R, R>.
 // P is kept only as the BF16 (hi, lo) pair that the product reads.
@@ -868,13 +912,20 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       g1.out_hi = b.Y[0]; g1.out_lo = b.Y[1];
       g1.res2 = ns.res2;
       g1.state = ns.state; g1.skip_state = ST_DONE;
+      g1.upper_only = 1;
       SM_CUDA(launch(g1));
+      k_mirror_split<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Y[0], b.Y[1], ns.state, ST_DONE);
+      SM_KCHECK();
       SM_CUDA(launch_ns_update(wv.dev, ns, tol_eff, floor_thr, opt.max_iter, d_flags, st));
       TcGemmParams g2 = tc(SYM, NSYM, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
                            MS_YH, MS_YL, 1, 1.0f, 0.0f);
       g2.out_hi = b.X[cur ^ 1][0]; g2.out_lo = b.X[cur ^ 1][1];
       g2.state = ns.state; g2.skip_state = ST_DONE;
+      g2.upper_only = 1;
       SM_CUDA(launch(g2));
+      k_mirror_split<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.X[cur ^ 1][0], b.X[cur ^ 1][1], ns.state,
+                                                           ST_DONE);
+      SM_KCHECK();
       SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
       SM_CUDA(launch_ns_post(wv.dev, ns, cur ^ 1, d_active, st));
       SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));

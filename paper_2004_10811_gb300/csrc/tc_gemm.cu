@@ -455,8 +455,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       // accumulation order
       if (p.sym && sub_tj < item.y) continue;
       const bool diag_sym = p.sym && item.y == sub_tj;
-      const bool mirror = p.sym != 0;
-      const double res_weight = (mirror && !diag_sym) ? 2.0 : 1.0;  // the mirror counts too
+      const bool mirror = p.sym != 0 && !p.upper_only;
+      const double res_weight = (p.sym && !diag_sym) ? 2.0 : 1.0;  // the mirror counts too
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int cg0 = sub_tj * 128 + c * 32;

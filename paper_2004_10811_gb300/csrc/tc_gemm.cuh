@@ -37,7 +37,9 @@ struct TcGemmParams {
   // epilogue: C = alpha * acc + beta * C0 + diag * I_n, written as FP32 or as
   // a BF16 (hi, lo) split
   float alpha, beta, diag;
-  int sym;                        // also write the mirrored tile (items have ti <= tj)
+  int sym;                        // symmetric result: items have ti <= tj; the mirrored tile is
+                                  // written too unless upper_only (then a separate pass copies it)
+  int upper_only;
   float* out_f32;
   __nv_bfloat16* out_hi;
   __nv_bfloat16* out_lo;          // may be null: plain BF16 output
