@@ -497,6 +497,34 @@ __global__ void __launch_bounds__(256) k_mirror_split(WaveDev w, __nv_bfloat16* 
   }
 }
 
+// The same for a symmetric FP32 matrix.
+__global__ void __launch_bounds__(256) k_mirror_f32(WaveDev w, float* C) {
+  __shared__ float t[32][33];
+  const int s = blockIdx.y;
+  const int ld = w.ld[s];
+  const int64_t base = w.off[s];
+  const int T = ld / 32;
+  const int npair = T * (T + 1) / 2;
+  const int x4 = threadIdx.x * 4, y = threadIdx.y;
+  for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
+    int a = 0, rem = pi;
+    while (rem >= T - a) { rem -= T - a; ++a; }
+    const int b = a + rem;
+    const float4 v = *reinterpret_cast<const float4*>(C + base + int64_t(a * 32 + y) * ld + b * 32 + x4);
+    __syncthreads();
+    t[y][x4] = v.x; t[y][x4 + 1] = v.y; t[y][x4 + 2] = v.z; t[y][x4 + 3] = v.w;
+    __syncthreads();
+    float* d = C + base + int64_t(b * 32 + y) * ld + a * 32 + x4;
+    if (a != b) {
+      *reinterpret_cast<float4*>(d) = make_float4(t[x4][y], t[x4 + 1][y], t[x4 + 2][y], t[x4 + 3][y]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (y > x4 + k) d[k] = t[x4 + k][y];
+    }
+  }
+}
+
 // CG step 2, fused with the symmetrisation: TP = W + W^T read through 32x32
 // tile pairs; alpha = rr / pTp; X += alpha P; R -= alpha TP; rr_new = <R, R>.
 // P is kept only as the BF16 (hi, lo) pair that the product reads.
@@ -1138,7 +1166,10 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       // F_c = -1/2 S (I - S^2)
       TcGemmParams g = tc(SYM, NSYM, s_hi, s_lo, MS_YH, MS_YL, 1, -0.5f, 0.0f);
       g.out_f32 = b.Fc;
+      g.upper_only = 1;
       SM_CUDA(launch(g));
+      k_mirror_f32<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Fc);
+      SM_KCHECK();
       // W = F_c a, before S a so that a's split and Y are free for a's slices
       k_split32<<<eg, 256, 0, st>>>(wv.dev, b.Fc, b.Y[0], b.Y[1]);
       SM_KCHECK();
@@ -1188,7 +1219,10 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       // C = M S (symmetric to first order) -> CG residual
       TcGemmParams g4 = tc(SYM, NSYM, MS_YH, MS_YL, c_hi, c_lo, 1, 1.0f, 0.0f);
       g4.out_f32 = b.cr;
+      g4.upper_only = 1;
       SM_CUDA(launch(g4));
+      k_mirror_f32<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cr);
+      SM_KCHECK();
       // CG on L -> H L + L H, per submatrix until the relative residual is below cg_tol
       SM_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * 4 * max_wave, st));
       SM_CUDA(cudaMemsetAsync(ms->cg_done, 0, sizeof(int) * max_wave, st));
