@@ -1122,7 +1122,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     };
     const int rounds = std::max(1, opt.refine_rounds);
     const int cg_max = 60;          // CG cap per round
-    const double cg_tol = 1e-3;     // relative residual that ends CG for a submatrix (round 1)
+    const double cg_tol = 1e-3;     // relative residual that ends CG for a submatrix (first correction)
     const double cg_tol_later = 1e-2;  // later rounds correct an O(1e-9) error: 1e-2 suffices
     const double cg_bad = 1e-2;     // above this after cg_max the submatrix falls back
     const double corr_tol = 1e-8;   // largest acceptable last-round correction
