@@ -87,7 +87,8 @@ typedef struct {
                                   kernel_* fields); adds one event pair per launch */
   int col_begin, col_end;      /* evaluate only block columns [col_begin, col_end) of D (one
                                   contiguous chunk, Section IV-E); 0, 0 = all columns.  The
-                                  other block columns of D are left untouched. */
+                                  other block columns of D are left untouched, and the
+                                  adjoint sums the contributions of these columns only. */
   int hp_mode;                 /* mixed path, the two residual products I - S^2 and S a:
                                   0: BF16 tensor cores on 6-bit integer slices (S on a 24-bit
                                   grid: four slices; a row-scaled: six), exact integer sums

@@ -97,3 +97,21 @@ def test_finite_differences_of_the_gpu_forward(pkg):
             fd = (energy(K0 + e) - energy(K0 - e)) / (2 * h)
             an = grad[i1] + (grad[i2] if i2 != i1 else 0.0)
             assert abs(fd - an) <= 2e-6 * max(1.0, abs(an)), (i1, fd, an)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 2e-5)])
+def test_vjp_matches_daleckii_krein_at_128_molecules(pkg, prec, tol):
+    """The 2048x23 workload's recipe (block 23, cutoff 8 A, submatrices of
+    1288-1840) at 128 molecules: the adjoint of block columns [0, 16) against
+    the oracle's Daleckii-Krein gradient of the same columns."""
+    import torch
+    m = make_water(128, 23, 8.0, (4, -1.0, -0.3), (19, 0.3, 1.5), seed=104)
+    cols = (0, 16)
+    rng = np.random.default_rng(3)
+    dbar = rng.standard_normal(m.vals.shape)
+    want, _dn = oracle.sign_backward(m, dbar, 0.0, columns=range(*cols))
+    with pkg.Plan.from_bsr(m, prec=prec, columns=cols) as plan:
+        kbar = plan.sign_backward(torch.from_numpy(m.vals).cuda(), 0.0, torch.from_numpy(dbar).cuda())
+    got = kbar.cpu().numpy()
+    assert np.max(np.abs(want)) > 0
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))

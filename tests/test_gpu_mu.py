@@ -64,3 +64,22 @@ def test_trace_parity_at_fixed_mu(pkg):
             D = plan.sign(torch.from_numpy(m.vals).cuda(), mu)
             tr = plan.trace(D)
         assert abs(tr - want) / m.n_el <= 1e-9
+
+
+def test_mixed_search_on_the_2048x23_recipe_at_128_molecules(pkg):
+    """The 2048x23 workload's recipe (block 23, cutoff 8 A, submatrices of
+    1288-1840) at 128 molecules, mixed path: from a start above the gap the
+    search lands on the gap's plateau (512.04 electrons here: the method's
+    truncation error moves it off N_el = 512) within the 1e-9 bound, at a mu
+    that Algorithm 1 on the oracle's eigendecompositions agrees with."""
+    import torch
+    m = make_water(128, 23, 8.0, (4, -1.0, -0.3), (19, 0.3, 1.5), seed=105)
+    dec = oracle.decompose_all(m, 0.0)
+    n_target = oracle.n_elec_alg1(dec, 0.0)
+    K = torch.from_numpy(m.vals).cuda()
+    with pkg.Plan.from_bsr(m, prec="mixed") as plan:
+        mu, D, status = plan.mu_search(K, n_target, mu0=0.9, tol=1e-9, max_steps=80)
+        tr = plan.trace(D)
+    assert status == "OK"
+    assert abs(tr - n_target) <= 1e-9 * n_target
+    assert abs(oracle.n_elec_alg1(dec, mu) - n_target) <= 1e-9 * n_target
