@@ -107,3 +107,22 @@ def test_autotune_picks_widths_and_keeps_parity(pkg):
         D1 = plan.sign(K, 0.0)
     for D in (D0, D1):
         assert np.max(np.abs(D.cpu().numpy() - want)) <= TOL_MIXED
+
+
+def test_submatrices_above_2048_one_slice_product_per_accumulator(pkg):
+    """Dims 2139-2645 (ld > 2048): each exact FP32 accumulator takes one slice
+    product (63^2 x ld stays below 2^24 only for one), the planner still pairs
+    accumulators of adjacent levels; block columns [0, 8) against the oracle."""
+    import torch
+    m = make_water(256, 23, 9.0, (4, -1.0, -0.3), (19, 0.3, 1.5), seed=106)
+    cols = (0, 8)
+    want = oracle.density_matrix(m, 0.0, columns=range(*cols))
+    K = torch.from_numpy(m.vals).cuda()
+    with pkg.Plan.from_bsr(m, prec="mixed", columns=cols) as plan:
+        D = plan.sign(K, 0.0).cpu().numpy()
+        st = plan.stats()
+    assert st["n_max"] > 2048 and st["refine_fallback"] == 0, st
+    vp = m.val_ptr
+    mine = [p for p in range(m.nnzb) if cols[0] <= m.col_idx[p] < cols[1]]
+    idx = np.concatenate([np.arange(vp[p], vp[p + 1]) for p in mine])
+    assert np.max(np.abs(D[idx] - want[idx])) <= TOL_MIXED
