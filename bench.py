@@ -149,6 +149,38 @@ def reference_arm(args, m, desc):
     print(json.dumps(line), flush=True)
 
 
+def sweep(args):
+    """Time per D build against system size at a fixed cutoff (the submatrix
+    method's linear scaling, Section V): the 1024x23 recipe at other molecule
+    counts, fixed tile widths, one JSON line per size."""
+    import torch
+    import __graft_entry__ as entry
+    entry.build()
+    import paper_2004_10811_gb300 as pkg
+    from synth.water import make_water
+    for n_mol in (int(x) for x in args.sweep.split(",")):
+        m = make_water(n_mol, 23, 8.0, (4, -1.0, -0.3), (19, 0.3, 1.5), seed=3000 + n_mol)
+        K = torch.from_numpy(m.vals).cuda()
+        D = torch.empty_like(K)
+        with pkg.Plan.from_bsr(m, prec="mixed", tile_n_ns=256, tile_n_corr=256, tile_n_hp=128) as plan:
+            for _ in range(max(1, args.warmup)):
+                plan.sign(K, m.mu, out=D)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                plan.sign(K, m.mu, out=D)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3 / args.steps
+            st = plan.stats()
+        print(json.dumps({"sweep": "water_b23_rc8", "n_mol": n_mol, "n": int(m.n), "s_per_build": t,
+                          "ms_per_molecule": 1e3 * t / n_mol, "sum_n3": st["sum_n3"],
+                          "sub_dim_min": int(st["n_min"]), "sub_dim_max": int(st["n_max"]),
+                          "waves": int(st["waves"]), "iters_max": int(st["iters_max"]),
+                          "fp64_fallback_submatrices": int(st["refine_fallback"])}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -168,8 +200,14 @@ def main():
     ap.add_argument("--tile-n-hp", type=int, default=0, choices=[0, 128, 256])
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the plan's default tile widths (autotuning runs unless widths are given)")
+    ap.add_argument("--sweep", default=None,
+                    help="comma-separated molecule counts: time the mixed path on the 1024x23 recipe "
+                         "(block 23, cutoff 8 A) at each size, one JSON line per size (linear scaling)")
     args = ap.parse_args()
 
+    if args.sweep:
+        sweep(args)
+        return
     cfg_index, desc = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
