@@ -200,6 +200,8 @@ def main():
     ap.add_argument("--tile-n-hp", type=int, default=0, choices=[0, 128, 256])
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the plan's default tile widths (autotuning runs unless widths are given)")
+    ap.add_argument("--iteration", type=int, default=0, choices=[0, 1],
+                    help="sign iteration of the mixed path: 0 Newton-Schulz, 1 third order")
     ap.add_argument("--sweep", default=None,
                     help="comma-separated molecule counts: time the mixed path on the 1024x23 recipe "
                          "(block 23, cutoff 8 A) at each size, one JSON line per size (linear scaling)")
@@ -243,7 +245,8 @@ def main():
     D = torch.empty_like(K)
     columns = tuple(int(x) for x in args.columns.split(":")) if args.columns else None
     plan = pkg.Plan.from_bsr(m, prec=args.prec, timing=True, columns=columns, tile_n_ns=args.tile_n_ns,
-                             tile_n_corr=args.tile_n_corr, tile_n_hp=args.tile_n_hp)
+                             tile_n_corr=args.tile_n_corr, tile_n_hp=args.tile_n_hp,
+                             iteration=args.iteration if args.prec == "mixed" else 0)
     tiles = {"ns": args.tile_n_ns, "correction": args.tile_n_corr, "sliced": args.tile_n_hp, "source": "options"}
     if args.prec == "mixed" and not args.no_autotune and not (args.tile_n_ns or args.tile_n_corr or args.tile_n_hp):
         t0 = time.perf_counter()
@@ -324,6 +327,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64" if args.prec == "mixed" else args.prec,
         "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "prec": args.prec,
+                   "iteration": "third order" if args.iteration == 1 else "Newton-Schulz",
                    "n": int(m.n), "nsub": int(m.nblk), "nnzb": int(m.nnzb),
                    "sub_dim_min": int(stats["n_min"]), "sub_dim_max": int(stats["n_max"]), **line_cols,
                    "tiles": tiles,

@@ -98,7 +98,11 @@ typedef struct {
                                   0 = chosen per wave, or 128 / 256 */
   int tile_n_corr;             /* the same for the correction phase (0 = 256) */
   int tile_n_hp;               /* the same for the sliced residual products (0 = 128) */
-  int reserved[1];             /* must be zero */
+  int iteration;               /* sign iteration of the mixed path: 0 (default) Newton-Schulz
+                                  X <- X (3I - X^2) / 2 (Section II-B); 1 the third-order
+                                  X <- X (15I - 10X^2 + 3X^4) / 8 of the paper's GPU runs
+                                  (Section VI-A), three products per step.  Other
+                                  precisions support 0 only (UNSUPPORTED at plan creation) */
 } submat_options;
 
 /* Aggregate statistics of the last submat_sign / submat_mu_search call. */

@@ -932,11 +932,15 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     // X_{k+1} = X_k Z_k with Z_k = 1.5 I - 0.5 X_k^2: the squaring writes Z
     // (and the residual ||X^2 - I||_F from its raw accumulator), so the
     // update is a plain product whose epilogue loads nothing
+    // Third order (Section VI-A): 8 Z = 15 I - 10 X^2 + 3 X^4 = 3 W^2 + (20/3) I
+    // with W = X^2 - (5/3) I, so that no epilogue loads a second operand:
+    // W from the squaring, Z = 3/8 W^2 + 5/6 I from a second symmetric product.
+    const bool third = opt.iteration == 1;
     int cur = 0;
     for (int k = 0; k < opt.max_iter; ++k) {
       TcGemmParams g1 = tc(SYM, NSYM, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
-                           cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0, 1, -0.5f, 0.0f);
-      g1.diag = 1.5f;
+                           cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0, 1, third ? 1.0f : -0.5f, 0.0f);
+      g1.diag = third ? -5.0f / 3.0f : 1.5f;
       g1.out_hi = b.Y[0]; g1.out_lo = b.Y[1];
       g1.res2 = ns.res2;
       g1.state = ns.state; g1.skip_state = ST_DONE;
@@ -945,8 +949,20 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       k_mirror_split<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Y[0], b.Y[1], ns.state, ST_DONE);
       SM_KCHECK();
       SM_CUDA(launch_ns_update(wv.dev, ns, tol_eff, floor_thr, opt.max_iter, d_flags, st));
-      TcGemmParams g2 = tc(SYM, NSYM, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
-                           MS_YH, MS_YL, 1, 1.0f, 0.0f);
+      int z_hi = MS_YH, z_lo = MS_YL;
+      if (third) {  // Z = 3/8 W^2 + 5/6 I into H's buffers
+        TcGemmParams gw = tc(SYM, NSYM, MS_YH, MS_YL, MS_YH, MS_YL, 1, 0.375f, 0.0f);
+        gw.diag = 5.0f / 6.0f;
+        gw.out_hi = b.Hh[0]; gw.out_lo = b.Hh[1];
+        gw.state = ns.state; gw.skip_state = ST_DONE;
+        gw.upper_only = 1;
+        SM_CUDA(launch(gw));
+        k_mirror_split<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Hh[0], b.Hh[1], ns.state, ST_DONE);
+        SM_KCHECK();
+        z_hi = MS_HH;
+        z_lo = MS_HL;
+      }
+      TcGemmParams g2 = tc(SYM, NSYM, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0, z_hi, z_lo, 1, 1.0f, 0.0f);
       g2.out_hi = b.X[cur ^ 1][0]; g2.out_lo = b.X[cur ^ 1][1];
       g2.state = ns.state; g2.skip_state = ST_DONE;
       g2.upper_only = 1;
@@ -1324,7 +1340,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       // algorithmic flops: a product with a symmetric result needs n^2 (n + 1),
       // a general one 2 n^3; the three-term split counts once
       const double sym = n * n * (n + 1.0);
-      stats.kernel_work[KC_TC_NS] += 2.0 * sym * lp_iters[s];
+      stats.kernel_work[KC_TC_NS] += (third ? 3.0 : 2.0) * sym * lp_iters[s];
       stats.kernel_work[KC_TC_REF] += (2.0 * sym + 2.0 * n3) * rounds + 2.0 * n3 * cgc[s];
       // the two residual products: I - S^2 (all tiles: 2 n^3) and S a (2 n^3)
       if (hp_sliced) stats.kernel_work[KC_TC_HP] += 4.0 * n3 * rounds;
@@ -1337,7 +1353,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       const double sym_tiles_ns = ns_width == 256 ? double(sym256_count(int(t128), int(tns))) : t128 * (t128 + 1) / 2;
       const double tile_ns = 2.0 * 128.0 * ns_width * ldd;
       const double tile128 = 2.0 * 128.0 * 128.0 * ldd;
-      stats.kernel_exec[KC_TC_NS] += 2.0 * lp_iters[s] * 3.0 * sym_tiles_ns * tile_ns;
+      stats.kernel_exec[KC_TC_NS] += (third ? 3.0 : 2.0) * lp_iters[s] * 3.0 * sym_tiles_ns * tile_ns;
       const double symt = t128 * (t128 + 1) / 2, fullt = t128 * t128;
       stats.kernel_exec[KC_TC_REF] += rounds * 3.0 * (2.0 * symt + fullt) * tile128 + cgc[s] * 3.0 * fullt * tile128;
       if (hp_sliced) stats.kernel_exec[KC_TC_HP] += double(hp_launch_products) * fullt * tile128;

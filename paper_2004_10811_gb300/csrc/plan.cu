@@ -605,7 +605,7 @@ void Plan::finish_stats() {
     imin = std::min(imin, res_iters[j]);
     imax = std::max(imax, res_iters[j]);
     nc += res_notconv[j];
-    flops += 4.0 * double(nsub[j]) * nsub[j] * nsub[j] * res_iters[j];
+    flops += (opt.iteration == 1 ? 6.0 : 4.0) * double(nsub[j]) * nsub[j] * nsub[j] * res_iters[j];
     rmax = std::max(rmax, res_resid[j]);
   }
   stats.iters_min = imin == INT32_MAX ? 0 : imin;
@@ -755,8 +755,14 @@ submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int
       submat::set_error("tile widths must be 0, 128 or 256");
       return SUBMAT_ERR_INVALID_ARG;
     }
-    for (int r : o.reserved)
-      if (r != 0) { submat::set_error("reserved option fields must be zero"); return SUBMAT_ERR_INVALID_ARG; }
+    if (o.iteration != 0 && o.iteration != 1) {
+      submat::set_error("iteration must be 0 (Newton-Schulz) or 1 (third order)");
+      return SUBMAT_ERR_INVALID_ARG;
+    }
+    if (o.iteration == 1 && o.prec != SUBMAT_MIXED_BF16_REFINE) {
+      submat::set_error("the third-order iteration is available on the mixed path only");
+      return SUBMAT_ERR_UNSUPPORTED;
+    }
     if (o.col_begin < 0 || o.col_end < 0 || o.col_end > nblk || (o.col_end > 0 && o.col_begin >= o.col_end)) {
       submat::set_error("bad column range [%d, %d) for %d block columns", o.col_begin, o.col_end, nblk);
       return SUBMAT_ERR_INVALID_ARG;

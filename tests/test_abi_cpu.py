@@ -64,7 +64,7 @@ def test_options_default(lib):
     assert o.prec == 0 and o.tol == 0.0 and o.max_iter == 0
 
 
-def _create(lib, bs, rp, ci):
+def _create(lib, bs, rp, ci, **opts):
     from paper_2004_10811_gb300.submat import Options
     bs = np.ascontiguousarray(bs, np.int32)
     rp = np.ascontiguousarray(rp, np.int64)
@@ -72,6 +72,8 @@ def _create(lib, bs, rp, ci):
     h = C.c_void_p()
     o = Options()
     lib.submat_options_default(C.byref(o))
+    for k, v in opts.items():
+        setattr(o, k, v)
     st = lib.submat_plan_create(len(bs), bs.ctypes.data_as(C.POINTER(C.c_int32)),
                                 rp.ctypes.data_as(C.POINTER(C.c_int64)),
                                 ci.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(o), None, C.byref(h))
@@ -107,3 +109,15 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(submat, "_lib", None)
     with pytest.raises(submat.SubmatLibraryMissing):
         submat.load(str(tmp_path / "nope.so"))
+
+
+@pytest.mark.parametrize("opts,status,what", [
+    (dict(tile_n_ns=192), 1, "tile widths"),
+    (dict(iteration=2), 1, "iteration"),
+    (dict(prec=0, iteration=1), 9, "mixed path only"),   # third order: mixed path only
+    (dict(prec=1, iteration=1), 9, "mixed path only"),
+])
+def test_bad_options_rejected_on_host(lib, opts, status, what):
+    st, msg = _create(lib, [2, 2], [0, 2, 4], [0, 1, 0, 1], **opts)
+    assert st == status, (st, msg)
+    assert what in msg

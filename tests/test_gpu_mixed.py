@@ -126,3 +126,17 @@ def test_submatrices_above_2048_one_slice_product_per_accumulator(pkg):
     mine = [p for p in range(m.nnzb) if cols[0] <= m.col_idx[p] < cols[1]]
     idx = np.concatenate([np.arange(vp[p], vp[p + 1]) for p in mine])
     assert np.max(np.abs(D[idx] - want[idx])) <= TOL_MIXED
+
+
+def test_third_order_iteration(pkg):
+    """iteration = 1: the paper's GPU iteration X (15I - 10X^2 + 3X^4) / 8,
+    three symmetric products per step, fewer steps than Newton-Schulz, the
+    same D within the mixed bound."""
+    m = make_water(40, 23, 6.0, (4, -1.0, -0.3), (19, 0.3, 1.5), seed=81)
+    want = oracle.density_matrix(m, 0.0, workers=4)
+    got3, tr3, st3 = run(pkg, m, 0.0, iteration=1)
+    got2, _tr2, st2 = run(pkg, m, 0.0)
+    assert st3["refine_fallback"] == 0
+    assert st3["iters_max"] < st2["iters_max"], (st3["iters_max"], st2["iters_max"])
+    assert np.max(np.abs(got3 - want)) <= TOL_MIXED
+    assert abs(tr3 - oracle.trace_bsr(m, want)) / m.n_el <= 1e-9
