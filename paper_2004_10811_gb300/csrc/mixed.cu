@@ -161,6 +161,43 @@ __device__ __forceinline__ double i64_to_f64_scaled(long long I, int k, bool neg
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
+// The final Newton-Schulz iterate as its BF16 (hi, lo) pair, in buffer 0 or
+// 1 per submatrix (par).  The value hi + lo is exact in FP32.
+struct PairSrc {
+  const __nv_bfloat16* hi[2];
+  const __nv_bfloat16* lo[2];
+  const int* par;
+};
+
+__device__ __forceinline__ float pair_value(const PairSrc& src, int s, int64_t i) {
+  const int k = src.par[s] ? 1 : 0;
+  return __bfloat162float(src.hi[k][i]) + __bfloat162float(src.lo[k][i]);
+}
+
+// submax[s] = bit pattern of max |hi + lo| over the iterate of submatrix s
+__global__ void k_submax_pair(WaveDev w, PairSrc src, unsigned long long* submax) {
+  __shared__ float red[32];
+  const int s = blockIdx.y;
+  const int ld = w.ld[s];
+  const int64_t base = w.off[s];
+  const int k = src.par[s] ? 1 : 0;
+  const int64_t total4 = int64_t(ld) * ld / 4;
+  float mx = 0.0f;
+  for (int64_t e4 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e4 < total4;
+       e4 += int64_t(gridDim.x) * blockDim.x) {
+    const float4 v = load_split4(src.hi[k], src.lo[k], base + 4 * e4);
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int q = 0; q < int(blockDim.x) / 32; ++q) t = fmaxf(t, red[q]);
+    atomicMax(&submax[s], (unsigned long long)__double_as_longlong(f2d_exact(t)));
+  }
+}
+
 // Row-scaled integer slices (the splitting of Ozaki et al.): for row r with
 // max_c |X_rc| < 2^e,  X_rc = 2^e sum_{p=1..6} t_p 2^{-6p} + O(2^{e-36}), with
 // integers |t_p| <= 63, exact in BF16.  A product of two slice matrices is a sum
@@ -173,9 +210,12 @@ __device__ __forceinline__ double i64_to_f64_scaled(long long I, int k, bool neg
 // value written back to X (still symmetric for a symmetric X) and represented
 // exactly by its slices.  The sign iterate goes through this mode, so that
 // its square needs keep^2 slice products, all exact.
+//
+// With src.par set (grid mode), the input values are read from that BF16 pair
+// instead of X, and the rounded values are written to X.
 __global__ void k_slice(WaveDev w, double* X, SlicePtrs out, int* __restrict__ rowexp,
                         const int64_t* __restrict__ voff, const unsigned long long* __restrict__ submax,
-                        int keep, __nv_bfloat16* split_hi, __nv_bfloat16* split_lo) {
+                        int keep, __nv_bfloat16* split_hi, __nv_bfloat16* split_lo, PairSrc src) {
   const int s = blockIdx.y;
   const int ld = w.ld[s];
   const int64_t base = w.off[s];
@@ -202,7 +242,10 @@ __global__ void k_slice(WaveDev w, double* X, SlicePtrs out, int* __restrict__ r
     }
     if (lane == 0) rowexp[voff[s] + r] = e;
     for (int c = lane; c < ld; c += 32) {
-      const unsigned long long b = row[c];
+      const unsigned long long b =
+          src.par ? static_cast<unsigned long long>(__double_as_longlong(
+                        f2d_exact(pair_value(src, s, base + int64_t(r) * ld + c))))
+                  : row[c];
       const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
       const int ex = int(a >> 52) - 1023;
       // fixed = trunc(|x| 2^(36 - e)) = mantissa * 2^(ex - 16 - e), ex < e
@@ -988,16 +1031,23 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     std::vector<int> lp_iters(wv.count);
     SM_CUDA(cudaMemcpyAsync(lp_iters.data(), ns.iters, sizeof(int) * wv.count, cudaMemcpyDeviceToHost, st));
     SM_CUDA(cudaMemsetAsync(ms->cg_count, 0, sizeof(int) * max_wave, st));
-    SM_CUDA(cudaMemsetAsync(ms->submax, 0, sizeof(unsigned long long) * max_wave, st));
-    k_widen<<<eg, 256, 0, st>>>(wv.dev, ns.par, b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.S, ms->submax);
-    SM_KCHECK();
-    k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
-    SM_KCHECK();
     // sliced products are exact for K extents up to 4096 (two per accumulator up to 2048)
     int64_t max_ld = 0;
     for (int64_t l : wv.bucket_ld) max_ld = std::max(max_ld, l);
     const bool hp_sliced = opt.hp_mode == 0 && max_ld <= 4096;
     const int per_acc = max_ld <= 2048 ? 2 : 1;
+    SM_CUDA(cudaMemsetAsync(ms->submax, 0, sizeof(unsigned long long) * max_wave, st));
+    // the final iterate: the sliced path reads its BF16 pair directly (the
+    // first slicing writes S); the FP64 residual path widens it to S here
+    const PairSrc iterate{{b.X[0][0], b.X[1][0]}, {b.X[0][1], b.X[1][1]}, ns.par};
+    if (hp_sliced) {
+      k_submax_pair<<<eg, 256, 0, st>>>(wv.dev, iterate, ms->submax);
+    } else {
+      k_widen<<<eg, 256, 0, st>>>(wv.dev, ns.par, b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.S, ms->submax);
+    }
+    SM_KCHECK();
+    k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
+    SM_KCHECK();
     static const int S_SETS[HP_SLICES] = {MS_XH0, MS_XL0, MS_XH1, MS_XL1, MS_YH, MS_YL};
     static const int A_SETS[HP_SLICES] = {MS_AH, MS_AL, MS_HH, MS_HL, MS_Z0, MS_Z1};
     SlicePtrs sl_s{{b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.Y[0], b.Y[1]}};
@@ -1157,7 +1207,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       if (hp_sliced) {
         // slices of S in X (and Y for six), S's BF16 split in Z
         k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi], ms->submax, s_keep,
-                                            b.Z[0], b.Z[1]);
+                                            b.Z[0], b.Z[1], rd == 0 ? iterate : PairSrc{});
         SM_KCHECK();
         SM_TRY(hp_product(S_SETS, s_keep, S_SETS, s_keep, true, b.T));
         // (I - S^2) straight to its split in Y
@@ -1201,17 +1251,17 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
           static const int A_SETS4[HP_SLICES] = {MS_AH, MS_AL, MS_HH, MS_HL, MS_YH, MS_YL};
           SlicePtrs sl_a4{{b.Ah[0], b.Ah[1], b.Hh[0], b.Hh[1], b.Y[0], b.Y[1]}};
           k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.A, sl_a4, ms->rs_y, ms->d_voff[wi], nullptr, HP_SLICES,
-                                              nullptr, nullptr);
+                                              nullptr, nullptr, PairSrc{});
           SM_KCHECK();
           SM_TRY(hp_product(S_SETS, s_keep, A_SETS4, HP_SLICES, false, b.T));
         } else {
           // six slices of S again (5 and 6 lived in Y), a's slices over Z,
           // then S's split back in X0
           k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.S, sl_s, ms->rs_x, ms->d_voff[wi], ms->submax, s_keep,
-                                              nullptr, nullptr);
+                                              nullptr, nullptr, PairSrc{});
           SM_KCHECK();
           k_slice<<<slice_grid, 256, 0, st>>>(wv.dev, b.A, sl_a, ms->rs_y, ms->d_voff[wi], nullptr, HP_SLICES,
-                                              nullptr, nullptr);
+                                              nullptr, nullptr, PairSrc{});
           SM_KCHECK();
           SM_TRY(hp_product(S_SETS, s_keep, A_SETS, HP_SLICES, false, b.T));
           k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
