@@ -71,7 +71,7 @@ typedef struct {
                                   0 selects 1e-14 for FP64, 1e-6 for FP32, 2e-5 for the
                                   BF16x3 stage of the mixed path */
   int max_iter;                /* Newton-Schulz iteration cap; 0 selects 100 */
-  int beta_mode;               /* X_0 = a / beta.  0 (default): beta = 1.05 x a 20-step
+  int beta_mode;               /* X_0 = a / beta.  0 (default): beta = 1.05 x a 10-step
                                   power-iteration estimate of the spectral radius when that
                                   is below the bound of mode 1 (any beta > rho / sqrt(3)
                                   converges; a tighter beta saves iterations);
@@ -128,10 +128,11 @@ typedef struct {
    *   3 gather (assembly) kernel;  4 tensor-core GEMM, sliced FP64-accurate
    *   residual products;  5 unused.
    * kernel_ms: summed launch durations.  kernel_work: algorithmic work of
-   * those launches -- flops for the GEMM classes (2 n^3 per general n x n
-   * product, n^2 (n + 1) per product with a symmetric result; a split or
-   * sliced product counts once, as the product it represents), bytes moved
-   * for the gather (8 per dense element written plus 8 per K value read).
+   * those launches -- flops for the GEMM classes at the standard count (2 n^3
+   * per n x n product the method needs, also where the kernels compute only
+   * the upper tiles of a symmetric result; a split or sliced product counts
+   * once, as the product it represents), bytes moved for the gather (8 per
+   * dense element written plus 8 per K value read).
    * kernel_exec: MMA flops the tensor cores executed (every slice product,
    * tile padding included); 0 for the other classes. */
   double  kernel_ms[6];

@@ -497,10 +497,11 @@ __device__ __forceinline__ double block_sum(float v, double* red) {
 }
 
 // Complete a symmetric BF16 (hi, lo) pair from its upper triangle: entry
-// (r, c), r > c, takes (c, r).  32x32 tile pairs; block (8, 32).
+// (r, c), r > c, takes (c, r).  32x32 tile pairs, two per iteration so that
+// twice the loads are in flight; block (8, 32).
 __global__ void __launch_bounds__(256) k_mirror_split(WaveDev w, __nv_bfloat16* hi, __nv_bfloat16* lo,
                                                       const int* __restrict__ state, int skip_state) {
-  __shared__ uint32_t th[32][33], tl[32][33];  // BF16 bits of the upper tile
+  __shared__ uint32_t th[2][32][33], tl[2][32][33];  // BF16 bits of the upper tiles
   const int s = blockIdx.y;
   if (state && state[s] == skip_state) return;
   const int ld = w.ld[s];
@@ -510,32 +511,54 @@ __global__ void __launch_bounds__(256) k_mirror_split(WaveDev w, __nv_bfloat16* 
   const int x4 = threadIdx.x * 4, y = threadIdx.y;
   const unsigned short* h16 = reinterpret_cast<const unsigned short*>(hi);
   const unsigned short* l16 = reinterpret_cast<const unsigned short*>(lo);
-  for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
-    int a = 0, rem = pi;
-    while (rem >= T - a) { rem -= T - a; ++a; }
-    const int b = a + rem;  // upper tile (a, b), a <= b; lower tile (b, a)
-    const int64_t iab = base + int64_t(a * 32 + y) * ld + b * 32 + x4;
-    const uint2 hv = *reinterpret_cast<const uint2*>(h16 + iab);
-    const uint2 lv = *reinterpret_cast<const uint2*>(l16 + iab);
-    __syncthreads();
-    th[y][x4] = hv.x & 0xFFFFu; th[y][x4 + 1] = hv.x >> 16; th[y][x4 + 2] = hv.y & 0xFFFFu; th[y][x4 + 3] = hv.y >> 16;
-    tl[y][x4] = lv.x & 0xFFFFu; tl[y][x4 + 1] = lv.x >> 16; tl[y][x4 + 2] = lv.y & 0xFFFFu; tl[y][x4 + 3] = lv.y >> 16;
-    __syncthreads();
-    // lower tile (b, a), row y, columns x4..x4+3 = upper (a, b) column y, rows x4..x4+3
-    const int64_t iba = base + int64_t(b * 32 + y) * ld + a * 32 + x4;
-    if (a != b) {
-      *reinterpret_cast<uint2*>(hi + iba) = make_uint2(th[x4][y] | (th[x4 + 1][y] << 16), th[x4 + 2][y] | (th[x4 + 3][y] << 16));
-      *reinterpret_cast<uint2*>(lo + iba) = make_uint2(tl[x4][y] | (tl[x4 + 1][y] << 16), tl[x4 + 2][y] | (tl[x4 + 3][y] << 16));
-    } else {
-      // diagonal tile: only its strict lower triangle (row y > column x4 + k)
-      unsigned short* hd = reinterpret_cast<unsigned short*>(hi) + iba;
-      unsigned short* ld16 = reinterpret_cast<unsigned short*>(lo) + iba;
+  for (int p0 = blockIdx.x; p0 < npair; p0 += 2 * gridDim.x) {
+    int ta[2], tb[2];
+    uint2 hv[2], lv[2];
+    const int np = p0 + int(gridDim.x) < npair ? 2 : 1;
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (y > x4 + k) {
-          hd[k] = static_cast<unsigned short>(th[x4 + k][y]);
-          ld16[k] = static_cast<unsigned short>(tl[x4 + k][y]);
-        }
+    for (int q = 0; q < 2; ++q) {
+      if (q < np) {
+        int a = 0, rem = p0 + q * int(gridDim.x);
+        while (rem >= T - a) { rem -= T - a; ++a; }
+        ta[q] = a; tb[q] = a + rem;  // upper tile (a, b), a <= b; lower tile (b, a)
+        const int64_t iab = base + int64_t(a * 32 + y) * ld + tb[q] * 32 + x4;
+        hv[q] = *reinterpret_cast<const uint2*>(h16 + iab);
+        lv[q] = *reinterpret_cast<const uint2*>(l16 + iab);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (q < np) {
+        th[q][y][x4] = hv[q].x & 0xFFFFu; th[q][y][x4 + 1] = hv[q].x >> 16;
+        th[q][y][x4 + 2] = hv[q].y & 0xFFFFu; th[q][y][x4 + 3] = hv[q].y >> 16;
+        tl[q][y][x4] = lv[q].x & 0xFFFFu; tl[q][y][x4 + 1] = lv[q].x >> 16;
+        tl[q][y][x4 + 2] = lv[q].y & 0xFFFFu; tl[q][y][x4 + 3] = lv[q].y >> 16;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (q >= np) continue;
+      const int a = ta[q], b = tb[q];
+      // lower tile (b, a), row y, columns x4..x4+3 = upper (a, b) column y, rows x4..x4+3
+      const int64_t iba = base + int64_t(b * 32 + y) * ld + a * 32 + x4;
+      if (a != b) {
+        *reinterpret_cast<uint2*>(hi + iba) = make_uint2(th[q][x4][y] | (th[q][x4 + 1][y] << 16),
+                                                         th[q][x4 + 2][y] | (th[q][x4 + 3][y] << 16));
+        *reinterpret_cast<uint2*>(lo + iba) = make_uint2(tl[q][x4][y] | (tl[q][x4 + 1][y] << 16),
+                                                         tl[q][x4 + 2][y] | (tl[q][x4 + 3][y] << 16));
+      } else {
+        // diagonal tile: only its strict lower triangle (row y > column x4 + k)
+        unsigned short* hd = reinterpret_cast<unsigned short*>(hi) + iba;
+        unsigned short* ld16 = reinterpret_cast<unsigned short*>(lo) + iba;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (y > x4 + k) {
+            hd[k] = static_cast<unsigned short>(th[q][x4 + k][y]);
+            ld16[k] = static_cast<unsigned short>(tl[q][x4 + k][y]);
+          }
+      }
     }
   }
 }
@@ -569,14 +592,12 @@ __global__ void __launch_bounds__(256) k_mirror_f32(WaveDev w, float* C) {
 }
 
 // CG step 2, fused with the symmetrisation: TP = W + W^T read through 32x32
-// tile pairs; alpha = rr / pTp; X += alpha P; R -= alpha TP; rr_new = <R, R>.
-// P is kept only as the BF16 (hi, lo) pair that the product reads.
+// tile pairs; alpha = rr / pTp; R -= alpha TP; rr_new = <R, R>.  (X moves in
+// the direction kernel, which reads P anyway.)
 // Block (8, 32): thread (x, y) owns columns 4x..4x+3 of row y of each tile
 // (float4 accesses).
 __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float* __restrict__ W,
-                                                         float* __restrict__ X, float* __restrict__ R,
-                                                         const __nv_bfloat16* __restrict__ ph,
-                                                         const __nv_bfloat16* __restrict__ pl, const double* rr,
+                                                         float* __restrict__ R, const double* rr,
                                                          const double* ptp, double* rr_new,
                                                          const int* __restrict__ cg_done, int* cg_count) {
   __shared__ float ta_[32][33], tb_[32][33];
@@ -606,31 +627,21 @@ __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float*
     tb_[y][x4] = wba.x; tb_[y][x4 + 1] = wba.y; tb_[y][x4 + 2] = wba.z; tb_[y][x4 + 3] = wba.w;
     __syncthreads();
     {
-      float4 xv = *reinterpret_cast<const float4*>(X + iab);
-      const float4 pv = load_split4(ph, pl, iab);
       float4 rv = *reinterpret_cast<const float4*>(R + iab);
       const float tp0 = wab.x + tb_[x4][y], tp1 = wab.y + tb_[x4 + 1][y];
       const float tp2 = wab.z + tb_[x4 + 2][y], tp3 = wab.w + tb_[x4 + 3][y];
-      xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
-      xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
       rv.x = fmaf(-alpha, tp0, rv.x); rv.y = fmaf(-alpha, tp1, rv.y);
       rv.z = fmaf(-alpha, tp2, rv.z); rv.w = fmaf(-alpha, tp3, rv.w);
-      *reinterpret_cast<float4*>(X + iab) = xv;
       *reinterpret_cast<float4*>(R + iab) = rv;
       part = fmaf(rv.x, rv.x, part); part = fmaf(rv.y, rv.y, part);
       part = fmaf(rv.z, rv.z, part); part = fmaf(rv.w, rv.w, part);
     }
     if (a != b) {
-      float4 xv = *reinterpret_cast<const float4*>(X + iba);
-      const float4 pv = load_split4(ph, pl, iba);
       float4 rv = *reinterpret_cast<const float4*>(R + iba);
       const float tp0 = wba.x + ta_[x4][y], tp1 = wba.y + ta_[x4 + 1][y];
       const float tp2 = wba.z + ta_[x4 + 2][y], tp3 = wba.w + ta_[x4 + 3][y];
-      xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
-      xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
       rv.x = fmaf(-alpha, tp0, rv.x); rv.y = fmaf(-alpha, tp1, rv.y);
       rv.z = fmaf(-alpha, tp2, rv.z); rv.w = fmaf(-alpha, tp3, rv.w);
-      *reinterpret_cast<float4*>(X + iba) = xv;
       *reinterpret_cast<float4*>(R + iba) = rv;
       part = fmaf(rv.x, rv.x, part); part = fmaf(rv.y, rv.y, part);
       part = fmaf(rv.z, rv.z, part); part = fmaf(rv.w, rv.w, part);
@@ -646,12 +657,18 @@ __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float*
   }
 }
 
-// CG step 3: P = R + (rr_new / rr) P, split for the next product.
-__global__ void k_cg_dir(WaveDev w, const float* __restrict__ R, const double* rr, const double* rr_new,
-                         __nv_bfloat16* ph, __nv_bfloat16* pl, const int* __restrict__ cg_done) {
+// CG step 3: X += alpha P (X = alpha P on the first step), then
+// P = R + (rr_new / rr) P, split for the next product.  Runs exactly when the
+// step's update ran (cg_done changes only after this kernel).  P is kept only
+// as the BF16 (hi, lo) pair that the product reads.
+__global__ void k_cg_dir(WaveDev w, const float* __restrict__ R, float* __restrict__ X, const double* rr,
+                         const double* ptp, const double* rr_new, __nv_bfloat16* ph, __nv_bfloat16* pl,
+                         const int* __restrict__ cg_done, int first) {
   const int s = blockIdx.y;
   if (cg_done[s]) return;
   const double d = rr[s];
+  const double den = ptp[s];
+  const float alpha = (den > 0.0 && d > 0.0) ? float(d / den) : 0.0f;
   const float beta = d > 0.0 ? float(rr_new[s] / d) : 0.0f;
   const int ld = w.ld[s];
   const int64_t base = w.off[s];
@@ -661,13 +678,18 @@ __global__ void k_cg_dir(WaveDev w, const float* __restrict__ R, const double* r
     const int64_t i = base + 4 * e4;
     const float4 r = *reinterpret_cast<const float4*>(R + i);
     const float4 p = load_split4(ph, pl, i);
+    float4 x = first ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(X + i);
+    x.x = fmaf(alpha, p.x, x.x); x.y = fmaf(alpha, p.y, x.y);
+    x.z = fmaf(alpha, p.z, x.z); x.w = fmaf(alpha, p.w, x.w);
+    *reinterpret_cast<float4*>(X + i) = x;
     store_split4(make_float4(fmaf(beta, p.x, r.x), fmaf(beta, p.y, r.y), fmaf(beta, p.z, r.z),
                              fmaf(beta, p.w, r.w)),
                  ph, pl, i);
   }
 }
 
-// CG start: X = 0, R = P = C (already in R), rr = <C, C>, split P.
+// CG start: R = P = C (already in R), rr = <C, C>, split P.  X is first
+// written by the first direction update (X = 0 here when no step runs).
 __global__ void k_cg_init(WaveDev w, float* __restrict__ X, const float* __restrict__ R, double* rr,
                           __nv_bfloat16* ph, __nv_bfloat16* pl) {
   __shared__ double red[32];
@@ -675,7 +697,7 @@ __global__ void k_cg_init(WaveDev w, float* __restrict__ X, const float* __restr
   FOR_SUB_ELEMS(w) {
     const int64_t i = base + e;
     const float r = R[i];
-    X[i] = 0.0f;
+    if (X) X[i] = 0.0f;
     split2f(r, ph, pl, i);
     part = fmaf(r, r, part);
   }
@@ -1292,7 +1314,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       // CG on L -> H L + L H, per submatrix until the relative residual is below cg_tol
       SM_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * 4 * max_wave, st));
       SM_CUDA(cudaMemsetAsync(ms->cg_done, 0, sizeof(int) * max_wave, st));
-      k_cg_init<<<eg, 256, 0, st>>>(wv.dev, b.cx, b.cr, rr, b.Y[0], b.Y[1]);
+      k_cg_init<<<eg, 256, 0, st>>>(wv.dev, cg_max > 0 ? nullptr : b.cx, b.cr, rr, b.Y[0], b.Y[1]);
       SM_KCHECK();
       SM_CUDA(cudaMemcpyAsync(rr0, rr, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
       for (int it = 0; it < cg_max; ++it) {
@@ -1305,10 +1327,10 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         gh.dot_c0 = ptp;
         gh.state = ms->cg_done; gh.skip_state = 1;
         SM_CUDA(launch(gh));
-        k_cg_update_pairs<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cw, b.cx, b.cr, b.Y[0], b.Y[1], rr,
-                                                                 ptp, rrn, ms->cg_done, ms->cg_count);
+        k_cg_update_pairs<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cw, b.cr, rr, ptp, rrn, ms->cg_done,
+                                                                 ms->cg_count);
         SM_KCHECK();
-        k_cg_dir<<<eg, 256, 0, st>>>(wv.dev, b.cr, rr, rrn, b.Y[0], b.Y[1], ms->cg_done);
+        k_cg_dir<<<eg, 256, 0, st>>>(wv.dev, b.cr, b.cx, rr, ptp, rrn, b.Y[0], b.Y[1], ms->cg_done, it == 0);
         SM_KCHECK();
         SM_CUDA(cudaMemcpyAsync(rr, rrn, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
         cg_total += 1;
@@ -1387,15 +1409,19 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       const double n = double(wv.host_n[s]);
       const double n3 = n * n * n;
       const int extra = res_iters[wv.first + s] - lp_iters[s];  // FP64 fallback iterations
-      // algorithmic flops: a product with a symmetric result needs n^2 (n + 1),
-      // a general one 2 n^3; the three-term split counts once
-      const double sym = n * n * (n + 1.0);
-      stats.kernel_work[KC_TC_NS] += (third ? 3.0 : 2.0) * sym * lp_iters[s];
-      stats.kernel_work[KC_TC_REF] += (2.0 * sym + 2.0 * n3) * rounds + 2.0 * n3 * cgc[s];
-      // the two residual products: I - S^2 (all tiles: 2 n^3) and S a (2 n^3)
+      // algorithmic flops at the standard count, 2 n^3 per n x n product,
+      // whatever the kernels skip on symmetric results (a split or sliced
+      // product counts once): 4 n^3 per Newton-Schulz step (6 n^3 third
+      // order), and per correction round (CG steps + 4) 2 n^3 -- the two
+      // residual products, two of the three split products (F_c, W = F_c a
+      // and C = M S are executed; the round's cost model counts four) and one
+      // per CG step
+      stats.kernel_work[KC_TC_NS] += (third ? 3.0 : 2.0) * 2.0 * n3 * lp_iters[s];
+      stats.kernel_work[KC_TC_REF] += 2.0 * 2.0 * n3 * rounds + 2.0 * n3 * cgc[s];
+      // the two residual products I - S^2 and S a
       if (hp_sliced) stats.kernel_work[KC_TC_HP] += 4.0 * n3 * rounds;
-      else stats.kernel_work[KC_SIMT] += (sym + 2.0 * n3) * rounds;
-      stats.kernel_work[KC_SIMT] += 2.0 * sym * extra;
+      else stats.kernel_work[KC_SIMT] += 4.0 * n3 * rounds;
+      stats.kernel_work[KC_SIMT] += 4.0 * n3 * extra;
       // executed MMA work: tiles x 2 * 128 * width * K per product
       const double ldd = double(wv.host_ld[s]);
       const double t128 = std::ceil(ldd / 128.0);

@@ -617,10 +617,10 @@ void Plan::finish_stats() {
   if (timer.on) {
     timer.collect(stats.kernel_ms, stats.kernel_launches);
     if (opt.prec != SUBMAT_MIXED_BF16_REFINE) {
-      // two symmetric products per iteration: n^2 (n + 1) flops each
+      // two products per iteration, 2 n^3 flops each at the standard count
       for (int j = col_lo; j < col_hi; ++j) {
         const double n = nsub[j];
-        stats.kernel_work[KC_SIMT] += 2.0 * n * n * (n + 1.0) * res_iters[j];
+        stats.kernel_work[KC_SIMT] += 4.0 * n * n * n * res_iters[j];
       }
     }
   }
