@@ -40,6 +40,8 @@ WORKLOADS = {
 }
 METRIC = "s per D build & TFLOP/s: BF16+refine vs FP64 path, same GB300, max|dD|<=1e-7"
 FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 rate (recipe's nominal table)
+# FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (maximum SM clock)
+FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07
 L2_BYTES = 129 << 20           # GB300 L2
 CLASS_NAMES = ["tc_gemm_newton_schulz", "tc_gemm_correction", "simt_gemm_fp64", "gather",
                "tc_gemm_sliced_fp64", "unused"]
@@ -193,6 +195,10 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=32, help="block columns timed on the FP64 path")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--adjoint-sample", type=int, default=32,
+                    help="block columns timed for the adjoint (submat_sign_backward); 0 skips it")
+    ap.add_argument("--mu-search", action="store_true",
+                    help="also time submat_mu_search for the workload's electron count")
     ap.add_argument("--columns", default=None,
                     help="a:b -- evaluate only block columns [a, b) (small cases for profiling)")
     ap.add_argument("--tile-n-ns", type=int, default=0, choices=[0, 128, 256])
@@ -307,6 +313,20 @@ def main():
         tt = torch.tensor([t_e2e], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_e2e = float(tt.item())
+    # ---- mu search (bisection on Tr D(mu) = N_el), opt-in: each step is one build ----
+    mu_line = None
+    if args.mu_search and world == 1 and not columns:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        # started 1.0 above the workload's mu, inside the virtual band, so
+        # that the bracket has to be bisected down into the gap
+        mu0 = m.mu + 1.0
+        mu_found, _Dm, status = plan.mu_search(K, m.n_el, mu0=mu0, tol=1e-9, max_steps=60, out=D)
+        torch.cuda.synchronize()
+        tm = time.perf_counter() - t0
+        steps = int(plan.stats()["mu_steps"])
+        mu_line = {"mu0": mu0, "mu": mu_found, "status": status, "s_total": tm, "steps": steps,
+                   "s_per_step": tm / max(1, steps), "n_el": float(m.n_el)}
     plan.close()
 
     if rank != 0:
@@ -445,6 +465,51 @@ def main():
                              "chunk_s": t64, "iters_max": int(s64["iters_max"]),
                              "tflops": s64["flops_ns"] / t64 / 1e12,
                              "speedup_mixed_vs_fp64": est / value}
+    # ---- the adjoint (vector-Jacobian product) on a contiguous chunk of block columns ----
+    if args.adjoint_sample > 0 and world == 1 and not columns:
+        nc = min(args.adjoint_sample, m.nblk)
+        rng = np.random.default_rng(20041)
+        dbar_h = rng.standard_normal(m.vals.shape)
+        Dbar = torch.from_numpy(dbar_h).to(dev)
+        with pkg.Plan.from_bsr(m, prec=args.prec, columns=(0, nc), timing=True) as pa:
+            Kbar = torch.empty_like(K)
+            pa.sign_backward(K, m.mu, Dbar, out=Kbar)  # warm-up: the adjoint's workspace
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            pa.sign_backward(K, m.mu, Dbar, out=Kbar)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ta = a0.elapsed_time(a1) / 1e3
+            sa = pa.stats()
+            suba = pa.sub_stats()
+        simt_s = sa["kernel_ms"][2] / 1e3
+        work = sa["kernel_work"][2]
+        adj_prec = "fp64" if args.prec == "fp64" else "fp32"
+        peak = FP64_NOMINAL_GFLOPS / 1e3 if adj_prec == "fp64" else FP32_NOMINAL_GFLOPS / 1e3
+        sub_n3 = float(np.sum(sub["dims"].astype(np.float64) ** 3))
+        chunk_n3 = float(np.sum(sub["dims"][:nc].astype(np.float64) ** 3))
+        adj = {"prec": adj_prec, "gemm": "SIMT", "sample": f"block columns [0, {nc}) timed, scaled by sum n^3",
+               "chunk_s": ta, "s_per_build_est": ta * sub_n3 / chunk_n3,
+               "iters_max": int(suba["iters"][:nc].max()), "tflops": sa["flops_ns"] / ta / 1e12,
+               "roofline": {"kernel": "k_gemm_simt", "bound": "alu", "achieved": work / simt_s / 1e12,
+                            "peak": peak, "unit": "TFLOP/s", "frac": work / simt_s / 1e12 / peak,
+                            "peak_source": "nominal FP64" if adj_prec == "fp64" else
+                            "nominal FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)"}}
+        if not args.no_cpu and rank == 0:
+            # parity on a few of the timed columns against the oracle's Daleckii-Krein gradient
+            pc = min(4, nc)
+            with pkg.Plan.from_bsr(m, prec=args.prec, columns=(0, pc)) as pp:
+                got = pp.sign_backward(K, m.mu, Dbar).cpu().numpy()
+            import oracle
+            want, _ = oracle.sign_backward(m, dbar_h, m.mu, columns=range(pc))
+            adj["max_rel_err_vs_oracle"] = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+            adj["parity_sample"] = f"block columns [0, {pc})"
+        line["adjoint"] = adj
+
+    if mu_line is not None:
+        line["mu_search"] = mu_line
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -116,7 +116,9 @@ typedef struct {
   int32_t refine_cg_iters; /* conjugate-gradient launches over all rounds and waves */
   int32_t refine_fallback; /* submatrices re-solved in FP64 because the correction did not settle */
   double  sum_n2, sum_n3;  /* sum over submatrices of n_j^2 and n_j^3 */
-  double  flops_ns;        /* standard-count Newton-Schulz flops: sum_j 4 n_j^3 iters_j */
+  double  flops_ns;        /* standard-count Newton-Schulz flops: sum_j 4 n_j^3 iters_j
+                              (after submat_sign_backward: the adjoint's
+                              sum_j 12 n_j^3 (iters_j + 2)) */
   double  flops_refine;    /* standard-count refinement flops */
   double  max_resid;       /* largest final ||X^2 - I||_F / sqrt(n_j) */
   double  ms_gather, ms_ns, ms_refine, ms_scatter; /* phase times (CUDA events) */
@@ -139,6 +141,7 @@ typedef struct {
   int32_t kernel_launches[6];
   double  kernel_work[6];
   double  kernel_exec[6];
+  int32_t mu_steps;        /* sign evaluations of the last submat_mu_search (0 otherwise) */
 } submat_stats;
 
 /* Fill *opt with defaults (FP64, default tolerances, beta_mode 0). */

@@ -261,7 +261,7 @@ submat_status Plan::backward(const double* K, double mu, const double* Dbar, dou
     else SM_TRY(backward_wave<float>(wv, K, mu, Dbar, Kbar, dN_dmu ? d_dnpart : nullptr, bws, st));
   }
   SM_CUDA(cudaStreamSynchronize(st));
-  finish_stats();
+  finish_stats(true);
   if (dN_dmu) *dN_dmu = dn_acc;
   SM_TRY(read_flags(st, &fl));
   if (fl & FLAG_NONFINITE) {

@@ -35,11 +35,16 @@ submat_status Plan::mu_search(const double* K, double n_el, double mu0, double t
     return SUBMAT_OK;
   };
   int steps = 0;
+  // every evaluation resets the statistics; the step count is set on return
+  auto done = [&](submat_status s) {
+    stats.mu_steps = steps;
+    return s;
+  };
   double n0 = 0;
   SM_TRY(eval(mu0, &n0));
   ++steps;
   double last_mu = mu0;
-  if (std::fabs(n0 - n_el) <= tol * std::fabs(n_el)) { *mu_out = mu0; return SUBMAT_OK; }
+  if (std::fabs(n0 - n_el) <= tol * std::fabs(n_el)) { *mu_out = mu0; return done(SUBMAT_OK); }
   // spectral bound: every eigenvalue of a_j = K_sub - mu0 I lies in [-beta_j, beta_j]
   double bmax = 0;
   for (double b : res_beta) bmax = std::max(bmax, b);
@@ -55,21 +60,22 @@ submat_status Plan::mu_search(const double* K, double n_el, double mu0, double t
     ++steps;
     last_mu = mid;
     if (std::fabs(nm - n_el) < std::fabs(best_n - n_el)) { best_mu = mid; best_n = nm; }
-    if (std::fabs(nm - n_el) <= tol * std::fabs(n_el)) { *mu_out = mid; return SUBMAT_OK; }
+    if (std::fabs(nm - n_el) <= tol * std::fabs(n_el)) { *mu_out = mid; return done(SUBMAT_OK); }
     if (nm < n_el) lo = mid; else hi = mid;
   }
   if (last_mu != best_mu) {
     double nb = 0;
     SM_TRY(eval(best_mu, &nb));
+    ++steps;
   }
   *mu_out = best_mu;
   if ((hi - lo) <= width_floor) {
     set_error("Tr D jumps over n_el inside [%.17g, %.17g] (N = %.17g at mu = %.17g)", lo, hi, best_n,
               best_mu);
-    return SUBMAT_ERR_MU_NO_ROOT;
+    return done(SUBMAT_ERR_MU_NO_ROOT);
   }
   set_error("mu search used %d sign evaluations without meeting tol (best N = %.17g)", steps, best_n);
-  return SUBMAT_ERR_NOT_CONVERGED;
+  return done(SUBMAT_ERR_NOT_CONVERGED);
 }
 
 }  // namespace submat

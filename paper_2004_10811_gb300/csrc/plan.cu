@@ -598,14 +598,17 @@ void Plan::reset_stats() {
   launches_at_start = launch_count();
 }
 
-void Plan::finish_stats() {
+// adjoint: the coupled iteration runs six products per step, 12 n^3 flops at
+// the standard count, for the iterations of X plus the two in which E settles
+void Plan::finish_stats(bool adjoint) {
   int imin = INT32_MAX, imax = 0, nc = 0;
   double flops = 0.0, rmax = 0.0;
   for (int j = col_lo; j < col_hi; ++j) {
     imin = std::min(imin, res_iters[j]);
     imax = std::max(imax, res_iters[j]);
     nc += res_notconv[j];
-    flops += (opt.iteration == 1 ? 6.0 : 4.0) * double(nsub[j]) * nsub[j] * nsub[j] * res_iters[j];
+    const double n3 = double(nsub[j]) * nsub[j] * nsub[j];
+    flops += adjoint ? 12.0 * n3 * (res_iters[j] + 2) : (opt.iteration == 1 ? 6.0 : 4.0) * n3 * res_iters[j];
     rmax = std::max(rmax, res_resid[j]);
   }
   stats.iters_min = imin == INT32_MAX ? 0 : imin;
@@ -616,7 +619,9 @@ void Plan::finish_stats() {
   stats.launches = launch_count() - launches_at_start;
   if (timer.on) {
     timer.collect(stats.kernel_ms, stats.kernel_launches);
-    if (opt.prec != SUBMAT_MIXED_BF16_REFINE) {
+    if (adjoint) {
+      stats.kernel_work[KC_SIMT] += flops;  // every adjoint product runs on the SIMT GEMM
+    } else if (opt.prec != SUBMAT_MIXED_BF16_REFINE) {
       // two products per iteration, 2 n^3 flops each at the standard count
       for (int j = col_lo; j < col_hi; ++j) {
         const double n = nsub[j];

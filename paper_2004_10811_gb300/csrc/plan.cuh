@@ -135,7 +135,7 @@ struct Plan {
   submat_status collect_wave(const Wave& wv, cudaStream_t st);
   submat_status add_phase_times();
   void reset_stats();
-  void finish_stats();
+  void finish_stats(bool adjoint = false);
   submat_status sign_fp64(const double* K, double mu, double* D, cudaStream_t st);
   submat_status sign_fp32(const double* K, double mu, double* D, cudaStream_t st);
   submat_status sign_mixed(const double* K, double mu, double* D, cudaStream_t st);

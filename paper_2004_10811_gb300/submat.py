@@ -63,7 +63,7 @@ class Stats(C.Structure):
         ("ms_gather", C.c_double), ("ms_ns", C.c_double), ("ms_refine", C.c_double),
         ("ms_scatter", C.c_double), ("workspace_bytes", C.c_size_t), ("launches", C.c_int64),
         ("kernel_ms", C.c_double * 6), ("kernel_launches", C.c_int32 * 6), ("kernel_work", C.c_double * 6),
-        ("kernel_exec", C.c_double * 6),
+        ("kernel_exec", C.c_double * 6), ("mu_steps", C.c_int32),
     ]
 
     def as_dict(self):

@@ -29,8 +29,10 @@ def test_target_on_a_plateau_is_met(pkg, prec):
     K = torch.from_numpy(m.vals).cuda()
     with pkg.Plan.from_bsr(m, prec=prec) as plan:
         mu, D, status = plan.mu_search(K, n_target, mu0=0.9, tol=1e-9, max_steps=80)
+        steps = plan.stats()["mu_steps"]
         tr = plan.trace(D)
     assert status == "OK"
+    assert 1 <= steps <= 80
     assert abs(tr - n_target) <= 1e-9 * n_target
     # the oracle agrees that this mu is in the plateau
     assert abs(oracle.n_elec_alg1(dec, mu) - n_target) <= 1e-9 * n_target
