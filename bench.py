@@ -44,7 +44,7 @@ FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 rate (recipe's nominal table)
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07
 L2_BYTES = 129 << 20           # GB300 L2
 CLASS_NAMES = ["tc_gemm_newton_schulz", "tc_gemm_correction", "simt_gemm_fp64", "gather",
-               "tc_gemm_sliced_fp64", "unused"]
+               "tc_gemm_sliced_fp64", "tc_gemm_adjoint"]
 
 
 def load_peaks():
@@ -471,42 +471,57 @@ def main():
         rng = np.random.default_rng(20041)
         dbar_h = rng.standard_normal(m.vals.shape)
         Dbar = torch.from_numpy(dbar_h).to(dev)
-        with pkg.Plan.from_bsr(m, prec=args.prec, columns=(0, nc), timing=True) as pa:
-            Kbar = torch.empty_like(K)
-            pa.sign_backward(K, m.mu, Dbar, out=Kbar)  # warm-up: the adjoint's workspace
-            torch.cuda.synchronize()
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            pa.sign_backward(K, m.mu, Dbar, out=Kbar)
-            a1.record(stream)
-            torch.cuda.synchronize()
-            ta = a0.elapsed_time(a1) / 1e3
-            sa = pa.stats()
-            suba = pa.sub_stats()
-        simt_s = sa["kernel_ms"][2] / 1e3
-        work = sa["kernel_work"][2]
-        adj_prec = "fp64" if args.prec == "fp64" else "fp32"
-        peak = FP64_NOMINAL_GFLOPS / 1e3 if adj_prec == "fp64" else FP32_NOMINAL_GFLOPS / 1e3
         sub_n3 = float(np.sum(sub["dims"].astype(np.float64) ** 3))
         chunk_n3 = float(np.sum(sub["dims"][:nc].astype(np.float64) ** 3))
-        adj = {"prec": adj_prec, "gemm": "SIMT", "sample": f"block columns [0, {nc}) timed, scaled by sum n^3",
-               "chunk_s": ta, "s_per_build_est": ta * sub_n3 / chunk_n3,
-               "iters_max": int(suba["iters"][:nc].max()), "tflops": sa["flops_ns"] / ta / 1e12,
-               "roofline": {"kernel": "k_gemm_simt", "bound": "alu", "achieved": work / simt_s / 1e12,
-                            "peak": peak, "unit": "TFLOP/s", "frac": work / simt_s / 1e12 / peak,
-                            "peak_source": "nominal FP64" if adj_prec == "fp64" else
-                            "nominal FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)"}}
+        want = None
+        pc = min(4, nc)
         if not args.no_cpu and rank == 0:
-            # parity on a few of the timed columns against the oracle's Daleckii-Krein gradient
-            pc = min(4, nc)
-            with pkg.Plan.from_bsr(m, prec=args.prec, columns=(0, pc)) as pp:
-                got = pp.sign_backward(K, m.mu, Dbar).cpu().numpy()
             import oracle
             want, _ = oracle.sign_backward(m, dbar_h, m.mu, columns=range(pc))
-            adj["max_rel_err_vs_oracle"] = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
-            adj["parity_sample"] = f"block columns [0, {pc})"
-        line["adjoint"] = adj
+        # mode 0: SIMT GEMM in the plan's precision; mode 1 (mixed plans): tensor cores
+        for mode in ((0, 1) if args.prec == "mixed" else (0,)):
+            with pkg.Plan.from_bsr(m, prec=args.prec, columns=(0, nc), timing=True, adjoint_mode=mode) as pa:
+                Kbar = torch.empty_like(K)
+                pa.sign_backward(K, m.mu, Dbar, out=Kbar)  # warm-up: the adjoint's workspace
+                torch.cuda.synchronize()
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                pa.sign_backward(K, m.mu, Dbar, out=Kbar)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                ta = a0.elapsed_time(a1) / 1e3
+                sa = pa.stats()
+                suba = pa.sub_stats()
+            if mode == 0:
+                cls = 2
+                adj_prec = "fp64" if args.prec == "fp64" else "fp32"
+                peak = FP64_NOMINAL_GFLOPS / 1e3 if adj_prec == "fp64" else FP32_NOMINAL_GFLOPS / 1e3
+                roof = {"kernel": "k_gemm_simt", "bound": "alu", "peak": peak,
+                        "peak_source": "nominal FP64" if adj_prec == "fp64" else
+                        "nominal FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)"}
+            else:
+                cls = 5
+                adj_prec = "bf16x3"
+                roof = {"kernel": "k_tc_gemm", "bound": "tensor", "peak": peaks["bf16_tflops_sustained"],
+                        "peak_source": peak_src + " (bf16 sustained)"}
+            k_s = sa["kernel_ms"][cls] / 1e3
+            achieved = sa["kernel_work"][cls] / k_s / 1e12
+            roof.update(achieved=achieved, unit="TFLOP/s", frac=achieved / roof["peak"])
+            if mode == 1:
+                roof["executed_frac"] = sa["kernel_exec"][cls] / k_s / 1e12 / roof["peak"]
+            adj = {"prec": adj_prec, "gemm": "SIMT" if mode == 0 else "tcgen05",
+                   "sample": f"block columns [0, {nc}) timed, scaled by sum n^3",
+                   "chunk_s": ta, "s_per_build_est": ta * sub_n3 / chunk_n3,
+                   "iters_max": int(suba["iters"][:nc].max()), "tflops": sa["flops_ns"] / ta / 1e12,
+                   "roofline": roof}
+            if want is not None:
+                # parity on a few of the timed columns against the oracle's Daleckii-Krein gradient
+                with pkg.Plan.from_bsr(m, prec=args.prec, columns=(0, pc), adjoint_mode=mode) as pp:
+                    got = pp.sign_backward(K, m.mu, Dbar).cpu().numpy()
+                adj["max_rel_err_vs_oracle"] = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+                adj["parity_sample"] = f"block columns [0, {pc})"
+            line["adjoint" if mode == 0 else "adjoint_tc"] = adj
 
     if mu_line is not None:
         line["mu_search"] = mu_line

@@ -103,6 +103,10 @@ typedef struct {
                                   X <- X (15I - 10X^2 + 3X^4) / 8 of the paper's GPU runs
                                   (Section VI-A), three products per step.  Other
                                   precisions support 0 only (UNSUPPORTED at plan creation) */
+  int adjoint_mode;            /* GEMMs of submat_sign_backward: 0 (default) SIMT in the plan's
+                                  precision (FP32 for mixed plans); 1 BF16x3 tensor cores, mixed
+                                  plans only (UNSUPPORTED otherwise) -- about 15x faster, with
+                                  about 10x the error of mode 0 (BF16x3 carries ~16 bits) */
 } submat_options;
 
 /* Aggregate statistics of the last submat_sign / submat_mu_search call. */
@@ -128,7 +132,7 @@ typedef struct {
    *   0 tensor-core GEMM, Newton-Schulz;  1 tensor-core GEMM, correction
    *   (split products and the Lyapunov CG);  2 FP64/FP32 SIMT GEMM;
    *   3 gather (assembly) kernel;  4 tensor-core GEMM, sliced FP64-accurate
-   *   residual products;  5 unused.
+   *   residual products;  5 tensor-core GEMM, adjoint (adjoint_mode 1).
    * kernel_ms: summed launch durations.  kernel_work: algorithmic work of
    * those launches -- flops for the GEMM classes at the standard count (2 n^3
    * per n x n product the method needs, also where the kernels compute only
@@ -226,6 +230,10 @@ submat_status submat_mu_search(submat_plan* plan, const double* K_vals, double n
  *   Dbar_vals  device double[value count]  (upstream gradient, K's layout)
  *   Kbar_vals  device double[value count]  (output, overwritten)
  *   dN_dmu     host double or NULL: 1/2 sum_j sum_{c in block j} L_sign(a_j, I)_cc
+ * The products run on the SIMT GEMM in the plan's precision (FP32 for mixed
+ * plans), or with options.adjoint_mode = 1 as BF16x3 split products on the
+ * tensor cores, E's transpose kept beside it for the products that read E as
+ * their right operand.
  */
 submat_status submat_sign_backward(submat_plan* plan, const double* K_vals, double mu,
                                    const double* Dbar_vals, double* Kbar_vals,

@@ -138,7 +138,34 @@ struct GemmFor<float> {
 
 }  // namespace
 
-size_t backward_bytes_per_elem(int prec) { return prec == SUBMAT_FP64 ? 8 * 7 : 8 + 4 * 6; }
+cudaError_t launch_bwd_seed_f32(const PatternDev& g, const Wave& wv, const double* Dbar, const double* beta,
+                                float* E, int identity, cudaStream_t st) {
+  k_bwd_seed<float><<<wv.n_gather, dim3(32, 8), 0, st>>>(g, wv.dev, wv.gather_items, Dbar, beta, E, identity);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_scatter_add_f32(const PatternDev& g, const Wave& wv, int nb_max, const float* E,
+                                       double* Kbar, cudaStream_t st) {
+  const size_t smem = size_t(3 * nb_max + 1) * sizeof(int);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_bwd_scatter_add<float>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  k_bwd_scatter_add<float><<<wv.n_gather, 256, smem, st>>>(g, wv.dev, wv.gather_items, E, Kbar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_dn_f32(const PatternDev& g, const Wave& wv, const float* E, double* part,
+                              cudaStream_t st) {
+  k_bwd_dn<float><<<(wv.count + 255) / 256, 256, 0, st>>>(g, wv.dev, E, part);
+  return cudaGetLastError();
+}
+
+size_t backward_bytes_per_elem(int prec, int adjoint_mode) {
+  if (adjoint_mode == 1) return adjoint_tc_bytes_per_elem();
+  return prec == SUBMAT_FP64 ? 8 * 7 : 8 + 4 * 6;
+}
 
 template <typename T>
 submat_status Plan::backward_wave(Wave& wv, const double* K, double mu, const double* Dbar,
@@ -236,7 +263,8 @@ submat_status Plan::backward(const double* K, double mu, const double* Dbar, dou
     return SUBMAT_ERR_NONFINITE;
   }
   const bool f64 = opt.prec == SUBMAT_FP64;
-  const size_t bpe = backward_bytes_per_elem(opt.prec);
+  const bool tc = opt.adjoint_mode == 1;  // tensor cores (mixed plans only)
+  const size_t bpe = backward_bytes_per_elem(opt.prec, opt.adjoint_mode);
   // the adjoint keeps its own waves and workspace, sized for its six buffers
   if (bwaves.empty()) {
     size_t fre = 0, tot = 0;
@@ -256,8 +284,10 @@ submat_status Plan::backward(const double* K, double mu, const double* Dbar, dou
   }
   SM_CUDA(cudaMemsetAsync(Kbar, 0, sizeof(double) * size_t(nvals), st));
   dn_acc = 0.0;
-  for (auto& wv : bwaves) {
-    if (f64) SM_TRY(backward_wave<double>(wv, K, mu, Dbar, Kbar, dN_dmu ? d_dnpart : nullptr, bws, st));
+  for (size_t wi = 0; wi < bwaves.size(); ++wi) {
+    Wave& wv = bwaves[wi];
+    if (tc) SM_TRY(backward_wave_tc(wi, K, mu, Dbar, Kbar, dN_dmu ? d_dnpart : nullptr, st));
+    else if (f64) SM_TRY(backward_wave<double>(wv, K, mu, Dbar, Kbar, dN_dmu ? d_dnpart : nullptr, bws, st));
     else SM_TRY(backward_wave<float>(wv, K, mu, Dbar, Kbar, dN_dmu ? d_dnpart : nullptr, bws, st));
   }
   SM_CUDA(cudaStreamSynchronize(st));

@@ -1399,9 +1399,8 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     double fl = 0.0;
     for (int s = 0; s < wv.count; ++s) {
       const double n = double(wv.host_n[s]);
-      // per round: 2 FP64 products (4 n^3 standard count) and 3 split products
-      // (6 n^3); per CG iteration one split product (2 n^3)
-      fl += (rounds * 10.0 + 2.0 * cgc[s]) * n * n * n;
+      // the cost model's standard count: (CG steps + 4) 2 n^3 per round
+      fl += (rounds * 8.0 + 2.0 * cgc[s]) * n * n * n;
     }
     stats.flops_refine += fl;
     stats.refine_cg_iters += cg_total;
@@ -1440,5 +1439,289 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
 }
 
 void free_mixed(void* state) { delete static_cast<MixedState*>(state); }
+
+// ---------------------------------------------------------------------------
+// The adjoint on the tensor cores (adjoint_mode = 1)
+// ---------------------------------------------------------------------------
+// The coupled Newton-Schulz iteration of the adjoint (backward.cu: X, E with
+// X_0 = a / beta, E_0 = G / beta) with every product a BF16x3 split product on
+// tcgen05.  With Z = 1.5 I - 0.5 X^2 one step is
+//     E' = E Z + Z E - 1.5 E - 0.5 X E X,      X' = X Z,
+// six products in all: Z (symmetric), U = X E, T = E Z - 1.5 E, T += Z E,
+// E' = T - 0.5 U X, and X' = X Z (symmetric).  A product C = A B^T reads B by
+// rows, so the two products with E on the right read E's transpose, kept as
+// a BF16 pair of its own (a tile-pair transpose after each update).  As in
+// the SIMT adjoint every submatrix keeps iterating until all X have converged,
+// then two more steps let E settle; the last step leaves E in FP32.
+namespace {
+
+enum AdjSet {
+  AS_X0H, AS_X0L, AS_X1H, AS_X1L, AS_ZH, AS_ZL, AS_E0H, AS_E0L, AS_E1H, AS_E1L,
+  AS_TH, AS_TL, AS_UH, AS_UL, AS_COUNT
+};
+
+struct AdjState {
+  std::vector<CUtensorMap*> d_maps, d_maps_b;  // per adjoint wave: [AS_COUNT][nbucket]
+};
+
+// dst = src^T for a BF16 (hi, lo) pair (src and dst distinct): 32x32 tile
+// pairs (a, b), a <= b, both loaded before either is written; block (8, 32).
+__global__ void __launch_bounds__(256) k_transpose_split(WaveDev w, const __nv_bfloat16* __restrict__ sh,
+                                                         const __nv_bfloat16* __restrict__ sl,
+                                                         __nv_bfloat16* __restrict__ dh,
+                                                         __nv_bfloat16* __restrict__ dl) {
+  __shared__ uint32_t th[2][32][33], tl[2][32][33];  // BF16 bits of tiles (a, b) and (b, a)
+  const int s = blockIdx.y;
+  const int ld = w.ld[s];
+  const int64_t base = w.off[s];
+  const int T = ld / 32;
+  const int npair = T * (T + 1) / 2;
+  const int x4 = threadIdx.x * 4, y = threadIdx.y;
+  const unsigned short* h16 = reinterpret_cast<const unsigned short*>(sh);
+  const unsigned short* l16 = reinterpret_cast<const unsigned short*>(sl);
+  for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
+    int a = 0, rem = pi;
+    while (rem >= T - a) { rem -= T - a; ++a; }
+    const int b = a + rem;
+    const int64_t iab = base + int64_t(a * 32 + y) * ld + b * 32 + x4;
+    const int64_t iba = base + int64_t(b * 32 + y) * ld + a * 32 + x4;
+    uint2 hv[2], lv[2];
+    hv[0] = *reinterpret_cast<const uint2*>(h16 + iab);
+    lv[0] = *reinterpret_cast<const uint2*>(l16 + iab);
+    hv[1] = a != b ? *reinterpret_cast<const uint2*>(h16 + iba) : hv[0];
+    lv[1] = a != b ? *reinterpret_cast<const uint2*>(l16 + iba) : lv[0];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      th[q][y][x4] = hv[q].x & 0xFFFFu; th[q][y][x4 + 1] = hv[q].x >> 16;
+      th[q][y][x4 + 2] = hv[q].y & 0xFFFFu; th[q][y][x4 + 3] = hv[q].y >> 16;
+      tl[q][y][x4] = lv[q].x & 0xFFFFu; tl[q][y][x4 + 1] = lv[q].x >> 16;
+      tl[q][y][x4 + 2] = lv[q].y & 0xFFFFu; tl[q][y][x4 + 3] = lv[q].y >> 16;
+    }
+    __syncthreads();
+    // dst tile (b, a), row y = src tile (a, b), column y
+    *reinterpret_cast<uint2*>(dh + iba) = make_uint2(th[0][x4][y] | (th[0][x4 + 1][y] << 16),
+                                                     th[0][x4 + 2][y] | (th[0][x4 + 3][y] << 16));
+    *reinterpret_cast<uint2*>(dl + iba) = make_uint2(tl[0][x4][y] | (tl[0][x4 + 1][y] << 16),
+                                                     tl[0][x4 + 2][y] | (tl[0][x4 + 3][y] << 16));
+    if (a != b) {  // dst tile (a, b), row y = src tile (b, a), column y
+      *reinterpret_cast<uint2*>(dh + iab) = make_uint2(th[1][x4][y] | (th[1][x4 + 1][y] << 16),
+                                                       th[1][x4 + 2][y] | (th[1][x4 + 3][y] << 16));
+      *reinterpret_cast<uint2*>(dl + iab) = make_uint2(tl[1][x4][y] | (tl[1][x4 + 1][y] << 16),
+                                                       tl[1][x4 + 2][y] | (tl[1][x4 + 3][y] << 16));
+    }
+  }
+}
+
+// out = hi + lo in FP32
+__global__ void k_join32(WaveDev w, const __nv_bfloat16* __restrict__ hi, const __nv_bfloat16* __restrict__ lo,
+                         float* __restrict__ out) {
+  FOR_SUB_ELEMS(w) out[base + e] = __bfloat162float(hi[base + e]) + __bfloat162float(lo[base + e]);
+}
+
+}  // namespace
+
+size_t adjoint_tc_bytes_per_elem() { return 8 + 4 + 2 * AS_COUNT; }  // A, T, the BF16 sets
+
+void free_adjoint_tc(void* state) { delete static_cast<AdjState*>(state); }
+
+submat_status Plan::backward_wave_tc(size_t wi, const double* K, double mu, const double* Dbar, double* Kbar,
+                                     double* dn_part, cudaStream_t st) {
+  Wave& wv = bwaves[wi];
+  const int64_t E = bws_elems;
+  double* A = static_cast<double*>(bws);
+  float* T = reinterpret_cast<float*>(A + E);
+  __nv_bfloat16* P[AS_COUNT];
+  for (int i = 0; i < AS_COUNT; ++i) P[i] = reinterpret_cast<__nv_bfloat16*>(T + E) + int64_t(i) * E;
+  auto* as = static_cast<AdjState*>(adj_tc);
+  if (!as) {
+    as = new AdjState();
+    adj_tc = as;
+  }
+  // tensor maps of every adjoint wave (128-row boxes; 256-row boxes for the
+  // B operands of 128 x 256 tiles), built once
+  while (as->d_maps.size() < bwaves.size()) {
+    const Wave& mw = bwaves[as->d_maps.size()];
+    const int nb2 = int(mw.bucket_ld.size());
+    CUtensorMap* d[2] = {nullptr, nullptr};
+    for (int v = 0; v < 2; ++v) {
+      std::vector<CUtensorMap> maps(size_t(AS_COUNT) * nb2);
+      for (int m = 0; m < AS_COUNT; ++m)
+        for (int k = 0; k < nb2; ++k)
+          if (make_bucket_map(&maps[size_t(m) * nb2 + k], P[m] + mw.bucket_base[k], int(mw.bucket_ld[k]),
+                              mw.bucket_count[k], v ? 256 : 128) != 0) {
+            set_error("cuTensorMapEncodeTiled failed");
+            return SUBMAT_ERR_CUDA;
+          }
+      SM_TRY(alloc(&d[v], maps.size(), "tensor maps"));
+      SM_CUDA(cudaMemcpyAsync(d[v], maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+      SM_CUDA(cudaStreamSynchronize(st));  // the host array goes out of scope
+    }
+    as->d_maps.push_back(d[0]);
+    as->d_maps_b.push_back(d[1]);
+  }
+  const int nbk = int(wv.bucket_ld.size());
+  const long long tmo = timeout_cycles_for(2.0);
+  const int nsm = num_sms();
+  constexpr int bn = 256;
+  const dim3 eg = elem_grid(wv);
+  const dim3 pg = pair_grid(wv);
+  const double floor_thr = 1e-3;
+  // a BF16x3 split product C = alpha (A B^T) + ..., A and B from the pairs at a0, b0
+  auto prm = [&](const int4* items, int nitems, int a0, int b0, int sym) {
+    TcGemmParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.items = items;
+    p.nitems = nitems;
+    p.maps = as->d_maps[wi];
+    p.maps_b = as->d_maps_b[wi];
+    p.bn = bn;
+    p.nbucket = nbk;
+    p.nmaps = AS_COUNT * nbk;
+    p.na = 2; p.nb = 2;
+    p.a_set[0] = a0; p.a_set[1] = a0 + 1;
+    p.b_set[0] = b0; p.b_set[1] = b0 + 1;
+    p.nprod = 3;
+    const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
+    for (int i = 0; i < 3; ++i) { p.prod_a[i] = pa[i]; p.prod_b[i] = pb[i]; p.prod_acc[i] = 0; p.prod_first[i] = i == 0; }
+    p.nacc = 1;
+    p.nstage = tc_pick_stages(2, 2, bn);
+    p.tmem_cols = 2 * bn;
+    p.off = wv.dev.off; p.ld = wv.dev.ld; p.n = wv.dev.n;
+    p.state = nullptr;
+    p.skip_state = -1;
+    p.alpha = 1.0f; p.beta = 0.0f; p.diag = 0.0f;
+    p.sym = sym;
+    p.upper_only = sym;  // symmetric results: upper tiles, then a mirror pass
+    p.flags = d_flags;
+    p.timeout_cycles = tmo;
+    return p;
+  };
+  auto launch = [&](const TcGemmParams& p) -> cudaError_t {
+    size_t tk;
+    if (timer.start(KC_TC_ADJ, st, &tk) != SUBMAT_OK) return cudaErrorUnknown;
+    cudaError_t e = launch_tc_gemm(p, std::min(p.nitems, nsm), st);
+    if (e == cudaSuccess && timer.stop(tk, st) != SUBMAT_OK) return cudaErrorUnknown;
+    return e;
+  };
+  const int passes = dn_part ? 2 : 1;
+  for (int pass = 0; pass < passes; ++pass) {
+    // X_0 = a / beta (the power estimate tightens beta as in the forward path)
+    SM_TRY(gather_wave(wv, K, mu, A, st));
+    k_scale_split<<<eg, 256, 0, st>>>(wv.dev, A, ns.beta, P[AS_X0H], P[AS_X0L]);
+    SM_KCHECK();
+    if (opt.beta_mode == 0) {
+      SM_CUDA(launch_power_bf16(wv.dev, P[AS_X0H], kPowerIters, ns.state, ns.rprev, max_ld(wv), st));
+      k_rescale_split<<<eg, 256, 0, st>>>(wv.dev, P[AS_X0H], P[AS_X0L], ns.rprev, ns.beta, ns.state);
+      SM_KCHECK();
+      SM_CUDA(launch_reset_rprev(wv.dev, ns, st));
+    }
+    // E_0 = G / beta (pass 1: I / beta) with the final beta, its pair and transpose
+    SM_CUDA(launch_bwd_seed_f32(g, wv, Dbar, ns.beta, T, pass, st));
+    k_split32<<<eg, 256, 0, st>>>(wv.dev, T, P[AS_E0H], P[AS_E0L]);
+    SM_KCHECK();
+    k_transpose_split<<<pg, dim3(8, 32), 0, st>>>(wv.dev, P[AS_E0H], P[AS_E0L], P[AS_TH], P[AS_TL]);
+    SM_KCHECK();
+    int cur = 0, extra = -1, steps = 0, updates = 0;
+    bool in_t = false;  // E left in T (FP32) by the last step
+    for (int k = 0; k < opt.max_iter + 2; ++k) {
+      const bool last = extra == 1;
+      const int xs = cur ? AS_X1H : AS_X0H, xn = cur ? AS_X0H : AS_X1H;
+      const int es = cur ? AS_E1H : AS_E0H, en = cur ? AS_E0H : AS_E1H;
+      // Z = 1.5 I - 0.5 X^2, with the involution residual while X iterates
+      TcGemmParams g1 = prm(wv.sym256, wv.n_sym256, xs, xs, 1);
+      g1.alpha = -0.5f;
+      g1.diag = 1.5f;
+      g1.out_hi = P[AS_ZH]; g1.out_lo = P[AS_ZL];
+      if (extra < 0) g1.res2 = ns.res2;
+      SM_CUDA(launch(g1));
+      k_mirror_split<<<pg, dim3(8, 32), 0, st>>>(wv.dev, P[AS_ZH], P[AS_ZL], nullptr, 0);
+      SM_KCHECK();
+      if (extra < 0) SM_CUDA(launch_ns_update(wv.dev, ns, tol_eff, floor_thr, opt.max_iter, d_flags, st));
+      // U = X E (B: E^T)
+      TcGemmParams gu = prm(wv.full256, wv.n_full256, xs, AS_TH, 0);
+      gu.out_hi = P[AS_UH]; gu.out_lo = P[AS_UL];
+      SM_CUDA(launch(gu));
+      // T = E Z - 1.5 E
+      TcGemmParams ga = prm(wv.full256, wv.n_full256, es, AS_ZH, 0);
+      ga.beta = -1.5f;
+      ga.c0_hi = P[es]; ga.c0_lo = P[es + 1];
+      ga.out_f32 = T;
+      SM_CUDA(launch(ga));
+      // T += Z E (B: E^T)
+      TcGemmParams gb = prm(wv.full256, wv.n_full256, AS_ZH, AS_TH, 0);
+      gb.beta = 1.0f;
+      gb.c0_f32 = T;
+      gb.out_f32 = T;
+      SM_CUDA(launch(gb));
+      // E' = T - 0.5 U X
+      TcGemmParams gc = prm(wv.full256, wv.n_full256, AS_UH, xs, 0);
+      gc.alpha = -0.5f;
+      gc.beta = 1.0f;
+      gc.c0_f32 = T;
+      if (last) {
+        gc.out_f32 = T;
+      } else {
+        gc.out_hi = P[en]; gc.out_lo = P[en + 1];
+      }
+      SM_CUDA(launch(gc));
+      ++steps;
+      if (last) {
+        in_t = true;
+        break;
+      }
+      // X' = X Z, then E'^T for the next step
+      TcGemmParams g2 = prm(wv.sym256, wv.n_sym256, xs, AS_ZH, 1);
+      g2.out_hi = P[xn]; g2.out_lo = P[xn + 1];
+      SM_CUDA(launch(g2));
+      ++updates;
+      k_mirror_split<<<pg, dim3(8, 32), 0, st>>>(wv.dev, P[xn], P[xn + 1], nullptr, 0);
+      SM_KCHECK();
+      k_transpose_split<<<pg, dim3(8, 32), 0, st>>>(wv.dev, P[en], P[en + 1], P[AS_TH], P[AS_TL]);
+      SM_KCHECK();
+      if (extra < 0) {
+        SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
+        SM_CUDA(launch_ns_post(wv.dev, ns, cur ^ 1, d_active, st));
+        SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SM_CUDA(cudaStreamSynchronize(st));
+        if (reinterpret_cast<int*>(h_pinned)[0] == 0) extra = 2;  // E settles in two more steps
+      } else {
+        --extra;
+      }
+      cur ^= 1;
+    }
+    if (!in_t) {  // the step cap ended the loop: E is the current pair
+      const int es = cur ? AS_E1H : AS_E0H;
+      k_join32<<<eg, 256, 0, st>>>(wv.dev, P[es], P[es + 1], T);
+      SM_KCHECK();
+    }
+    if (pass == 0) {
+      SM_CUDA(launch_bwd_scatter_add_f32(g, wv, nb_max, T, Kbar, st));
+    } else {
+      SM_CUDA(launch_bwd_dn_f32(g, wv, T, dn_part, st));
+      std::vector<double> part(wv.count);
+      SM_CUDA(cudaMemcpyAsync(part.data(), dn_part, sizeof(double) * wv.count, cudaMemcpyDeviceToHost, st));
+      SM_CUDA(cudaStreamSynchronize(st));
+      for (double v : part) dn_acc += v;
+    }
+    if (timer.on) {  // executed MMA work: three MMAs per split product, tiles x 2 * 128 * 256 * K
+      for (int s = 0; s < wv.count; ++s) {
+        const double ldd = double(wv.host_ld[s]);
+        const int t128 = int(std::ceil(ldd / 128.0)), t256 = int(std::ceil(ldd / 256.0));
+        const double tile = 2.0 * 128.0 * 256.0 * ldd;
+        stats.kernel_exec[KC_TC_ADJ] +=
+            3.0 * tile * (double(sym256_count(t128, t256)) * (steps + updates) + 4.0 * t128 * t256 * steps);
+      }
+    }
+  }
+  int fl = 0;
+  SM_TRY(read_flags(st, &fl));
+  if (fl & FLAG_TIMEOUT) {
+    set_error("a bounded device wait timed out (tensor-core adjoint)");
+    return SUBMAT_ERR_TIMEOUT;
+  }
+  SM_TRY(collect_wave(wv, st));
+  return SUBMAT_OK;
+}
 
 }  // namespace submat

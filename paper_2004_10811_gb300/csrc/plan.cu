@@ -51,6 +51,7 @@ submat_status dev_alloc(void** p, size_t bytes, const char* what) {
 
 Plan::~Plan() {
   free_mixed(mixed);
+  free_adjoint_tc(adj_tc);
   for (void* p : owned) cudaFree(p);
   if (h_pinned) cudaFreeHost(h_pinned);
   for (auto& e : ev) if (e) cudaEventDestroy(e);
@@ -619,8 +620,8 @@ void Plan::finish_stats(bool adjoint) {
   stats.launches = launch_count() - launches_at_start;
   if (timer.on) {
     timer.collect(stats.kernel_ms, stats.kernel_launches);
-    if (adjoint) {
-      stats.kernel_work[KC_SIMT] += flops;  // every adjoint product runs on the SIMT GEMM
+    if (adjoint) {  // every adjoint product runs on one GEMM kind
+      stats.kernel_work[opt.adjoint_mode == 1 ? KC_TC_ADJ : KC_SIMT] += flops;
     } else if (opt.prec != SUBMAT_MIXED_BF16_REFINE) {
       // two products per iteration, 2 n^3 flops each at the standard count
       for (int j = col_lo; j < col_hi; ++j) {
@@ -763,6 +764,14 @@ submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int
     if (o.iteration != 0 && o.iteration != 1) {
       submat::set_error("iteration must be 0 (Newton-Schulz) or 1 (third order)");
       return SUBMAT_ERR_INVALID_ARG;
+    }
+    if (o.adjoint_mode != 0 && o.adjoint_mode != 1) {
+      submat::set_error("adjoint_mode must be 0 (SIMT GEMM) or 1 (tensor cores)");
+      return SUBMAT_ERR_INVALID_ARG;
+    }
+    if (o.adjoint_mode == 1 && o.prec != SUBMAT_MIXED_BF16_REFINE) {
+      submat::set_error("the tensor-core adjoint is available on the mixed path only");
+      return SUBMAT_ERR_UNSUPPORTED;
     }
     if (o.iteration == 1 && o.prec != SUBMAT_MIXED_BF16_REFINE) {
       submat::set_error("the third-order iteration is available on the mixed path only");

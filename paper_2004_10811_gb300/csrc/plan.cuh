@@ -15,8 +15,11 @@ submat_status validate_pattern_public(int nblk, const int32_t* bs, const int64_t
                                       const int32_t* ci);
 const char* last_error();
 size_t mixed_bytes_per_elem();
+size_t adjoint_tc_bytes_per_elem();
 constexpr int kPowerIters = 10;  // power steps of the spectral estimate
 void free_mixed(void* state);
+void free_adjoint_tc(void* state);
+
 
 struct Wave {
   int first = 0;           // first global block column of the wave
@@ -47,6 +50,16 @@ struct Wave {
   void* tc = nullptr;
 };
 
+// Adjoint helpers (backward.cu) on an FP32 E in the wave layout: the seed
+// E_0 = G / beta (or I / beta), the scatter-add of -1/2 E into Kbar, and the
+// per-submatrix dN/dmu part.
+cudaError_t launch_bwd_seed_f32(const PatternDev& g, const Wave& wv, const double* Dbar, const double* beta,
+                                float* E, int identity, cudaStream_t st);
+cudaError_t launch_bwd_scatter_add_f32(const PatternDev& g, const Wave& wv, int nb_max, const float* E,
+                                       double* Kbar, cudaStream_t st);
+cudaError_t launch_bwd_dn_f32(const PatternDev& g, const Wave& wv, const float* E, double* part,
+                              cudaStream_t st);
+
 // Event pairs around kernel launches, grouped in classes (submat_stats kernel_*).
 struct KernelTimer {
   bool on = false;
@@ -59,7 +72,7 @@ struct KernelTimer {
   submat_status collect(double* ms, int32_t* count);  // after a stream sync
 };
 
-enum KernelClass { KC_TC_NS = 0, KC_TC_REF = 1, KC_SIMT = 2, KC_GATHER = 3, KC_TC_HP = 4 };
+enum KernelClass { KC_TC_NS = 0, KC_TC_REF = 1, KC_SIMT = 2, KC_GATHER = 3, KC_TC_HP = 4, KC_TC_ADJ = 5 };
 
 int max_ld(const Wave& wv);
 
@@ -97,6 +110,7 @@ struct Plan {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<void*> owned;
   void* mixed = nullptr;       // mixed-path state (mixed.cu)
+  void* adj_tc = nullptr;      // tensor-core adjoint state (mixed.cu)
   // adjoint: its own waves and workspace (six dense buffers per submatrix)
   std::vector<Wave> bwaves;
   int max_bwave = 0;
@@ -143,6 +157,8 @@ struct Plan {
   template <typename T>
   submat_status backward_wave(Wave& wv, const double* K, double mu, const double* Dbar, double* Kbar,
                               double* dn_part, void* bws, cudaStream_t st);
+  submat_status backward_wave_tc(size_t wi, const double* K, double mu, const double* Dbar, double* Kbar,
+                                 double* dn_part, cudaStream_t st);
   submat_status grow_ns_state(int count);
   template <typename T, typename Args>
   submat_status ns_simt(const Wave& wv, T* buf0, T* buf1, T* Y, double tol, double floor_thr,

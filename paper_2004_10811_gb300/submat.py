@@ -49,7 +49,7 @@ class Options(C.Structure):
         ("symmetrize", C.c_int), ("workspace_cap_bytes", C.c_size_t),
         ("refine_rounds", C.c_int), ("timing", C.c_int), ("col_begin", C.c_int), ("col_end", C.c_int),
         ("hp_mode", C.c_int), ("tile_n_ns", C.c_int), ("tile_n_corr", C.c_int), ("tile_n_hp", C.c_int),
-        ("iteration", C.c_int),
+        ("iteration", C.c_int), ("adjoint_mode", C.c_int),
     ]
 
 
@@ -151,7 +151,7 @@ class Plan:
     def __init__(self, block_sizes, row_ptr, col_idx, prec="fp64", tol=0.0, max_iter=0,
                  beta_mode=0, symmetrize=False, workspace_cap_bytes=0, refine_rounds=0,
                  timing=False, columns=None, hp_mode=0, tile_n_ns=0, tile_n_corr=0, tile_n_hp=0,
-                 iteration=0, stream=None):
+                 iteration=0, adjoint_mode=0, stream=None):
         lib = load()
         self._lib = lib
         self.block_sizes = np.ascontiguousarray(block_sizes, dtype=np.int32)
@@ -172,6 +172,7 @@ class Plan:
         opt.tile_n_corr = int(tile_n_corr)
         opt.tile_n_hp = int(tile_n_hp)
         opt.iteration = int(iteration)
+        opt.adjoint_mode = int(adjoint_mode)
         if columns is not None:
             opt.col_begin, opt.col_end = int(columns[0]), int(columns[1])
         self.options = opt

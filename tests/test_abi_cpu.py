@@ -116,6 +116,8 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     (dict(iteration=2), 1, "iteration"),
     (dict(prec=0, iteration=1), 9, "mixed path only"),   # third order: mixed path only
     (dict(prec=1, iteration=1), 9, "mixed path only"),
+    (dict(adjoint_mode=2), 1, "adjoint_mode"),
+    (dict(prec=0, adjoint_mode=1), 9, "mixed path only"),  # tensor-core adjoint: mixed plans only
 ])
 def test_bad_options_rejected_on_host(lib, opts, status, what):
     st, msg = _create(lib, [2, 2], [0, 2, 4], [0, 1, 0, 1], **opts)

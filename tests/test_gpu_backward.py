@@ -35,19 +35,22 @@ def transpose_index(m):
     return perm
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 2e-5)])
-def test_vjp_matches_daleckii_krein(pkg, prec, tol):
+# adjoint_mode 1: the coupled iteration on the tensor cores (BF16x3 split
+# products, about 16 bits), hence the wider bounds
+@pytest.mark.parametrize("prec,mode,tol,dn_tol", [("fp64", 0, 1e-9, 1e-6), ("mixed", 0, 2e-5, 1e-6),
+                                                  ("mixed", 1, 2e-4, 1e-3)])
+def test_vjp_matches_daleckii_krein(pkg, prec, mode, tol, dn_tol):
     import torch
     m = small_case(n_mol=20, block=4, r_c=5.5, seed=101)
     rng = np.random.default_rng(1)
     dbar = rng.standard_normal(m.vals.shape)
     want, dn_want = oracle.sign_backward(m, dbar, 0.05)
-    with pkg.Plan.from_bsr(m, prec=prec) as plan:
+    with pkg.Plan.from_bsr(m, prec=prec, adjoint_mode=mode) as plan:
         kbar, dn = plan.sign_backward(torch.from_numpy(m.vals).cuda(), 0.05,
                                       torch.from_numpy(dbar).cuda(), want_dn_dmu=True)
     got = kbar.cpu().numpy()
     assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
-    assert abs(dn) < 1e-6 and abs(dn_want) < 1e-9   # L_sign(a, I) = 0 at T = 0
+    assert abs(dn) < dn_tol and abs(dn_want) < 1e-9   # L_sign(a, I) = 0 at T = 0
 
 
 def test_band_energy_gradient_through_autograd(pkg):
@@ -99,8 +102,8 @@ def test_finite_differences_of_the_gpu_forward(pkg):
             assert abs(fd - an) <= 2e-6 * max(1.0, abs(an)), (i1, fd, an)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 2e-5)])
-def test_vjp_matches_daleckii_krein_at_128_molecules(pkg, prec, tol):
+@pytest.mark.parametrize("prec,mode,tol", [("fp64", 0, 1e-9), ("fp32", 0, 2e-5), ("mixed", 1, 2e-4)])
+def test_vjp_matches_daleckii_krein_at_128_molecules(pkg, prec, mode, tol):
     """The 2048x23 workload's recipe (block 23, cutoff 8 A, submatrices of
     1288-1840) at 128 molecules: the adjoint of block columns [0, 16) against
     the oracle's Daleckii-Krein gradient of the same columns."""
@@ -110,7 +113,7 @@ def test_vjp_matches_daleckii_krein_at_128_molecules(pkg, prec, tol):
     rng = np.random.default_rng(3)
     dbar = rng.standard_normal(m.vals.shape)
     want, _dn = oracle.sign_backward(m, dbar, 0.0, columns=range(*cols))
-    with pkg.Plan.from_bsr(m, prec=prec, columns=cols) as plan:
+    with pkg.Plan.from_bsr(m, prec=prec, columns=cols, adjoint_mode=mode) as plan:
         kbar = plan.sign_backward(torch.from_numpy(m.vals).cuda(), 0.0, torch.from_numpy(dbar).cuda())
     got = kbar.cpu().numpy()
     assert np.max(np.abs(want)) > 0
