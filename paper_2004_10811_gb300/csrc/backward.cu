@@ -185,9 +185,22 @@ submat_status Plan::backward_wave(Wave& wv, const double* K, double mu, const do
     // X_0 = a / beta, E_0 = G / beta (or I / beta)
     if (sizeof(T) == 8) SM_CUDA(launch_scale_f64(wv.dev, A, reinterpret_cast<double*>(X[0]), ns.beta, wv.max_ld2, st));
     else SM_CUDA(launch_scale_f32(wv.dev, A, reinterpret_cast<float*>(X[0]), ns.beta, wv.max_ld2, st));
+    if (opt.beta_mode == 0) {  // the power estimate tightens beta as in the forward paths
+      if (sizeof(T) == 8) {
+        double* x0 = reinterpret_cast<double*>(X[0]);
+        SM_CUDA(launch_power_f64(wv.dev, x0, kPowerIters, ns.state, ns.rprev, max_ld(wv), st));
+        SM_CUDA(launch_rescale_f64(wv.dev, x0, ns.rprev, ns.beta, ns.state, wv.max_ld2, st));
+      } else {
+        float* x0 = reinterpret_cast<float*>(X[0]);
+        SM_CUDA(launch_power_f32(wv.dev, x0, kPowerIters, ns.state, ns.rprev, max_ld(wv), st));
+        SM_CUDA(launch_rescale_f32(wv.dev, x0, ns.rprev, ns.beta, ns.state, wv.max_ld2, st));
+      }
+    }
     k_bwd_seed<T><<<wv.n_gather, dim3(32, 8), 0, st>>>(g, wv.dev, wv.gather_items, Dbar, ns.beta, Ed[0], pass);
     SM_KCHECK();
-    SM_CUDA(launch_beta(wv.dev, ns, opt.beta_mode, st));  // resets the iteration state (beta unchanged)
+    // resets the iteration state (and beta to the bound, which the next pass
+    // scales by again; E_0 above took the final beta)
+    SM_CUDA(launch_beta(wv.dev, ns, opt.beta_mode, st));
     int cur = 0, extra = -1;
     for (int k = 0; k < opt.max_iter + 2; ++k) {
       Args a{};
