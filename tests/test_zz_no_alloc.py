@@ -4,9 +4,10 @@ Some callers cannot allocate: codes that reserve the whole GPU for their own
 memory pool, allocators that forbid foreign allocations, and time steps where
 an allocation's implicit device synchronisation is not acceptable.  For them
 the dense one-matrix evaluation keeps all its scratch in a fixed device array
-inside the library.  This checks it against the regular entry point (a plan
-with one dense block, FP64 path) on two calls in a row, with the FP64
-tolerance of the other parity tests, and that oversize input is refused.
+inside the library.  This checks it against the oracle's dense sign and
+against the regular entry point (a plan with one dense block, FP64 path) on
+two calls in a row, with the FP64 tolerance of the other parity tests, and
+that oversize input is refused.
 """
 import numpy as np
 import pytest
@@ -50,9 +51,14 @@ def test_noalloc_matches_plan_path_on_two_calls(sm):
         K = torch.from_numpy(a).cuda()
         d, iters = sm.dense_sign_noalloc(K, mu)
         torch.cuda.synchronize()
+        got = d.cpu().numpy()
         want = reference_dense(sm, a, mu)
-        err = np.max(np.abs(d.cpu().numpy() - want))
+        err = np.max(np.abs(got - want))
         assert err <= TOL_FP64, (n, err)
+        # the oracle: D = (I - sign(a - mu I)) / 2 by eigendecomposition
+        import oracle
+        d_or = 0.5 * (np.eye(n) - oracle.dense_sign(a - mu * np.eye(n)))
+        assert np.max(np.abs(got - d_or)) <= TOL_FP64, n
         assert 5 < iters < 60
 
 
