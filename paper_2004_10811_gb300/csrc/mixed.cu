@@ -592,12 +592,17 @@ __global__ void __launch_bounds__(256) k_mirror_f32(WaveDev w, float* C) {
 }
 
 // CG step 2, fused with the symmetrisation: TP = W + W^T read through 32x32
-// tile pairs; alpha = rr / pTp; R -= alpha TP; rr_new = <R, R>.  (X moves in
-// the direction kernel, which reads P anyway.)
+// tile pairs; alpha = rr / pTp; R -= alpha TP; rr_new = <R, R>; and, when X is
+// given, X += alpha P.  (On large submatrices X moves in the direction kernel
+// instead, which reads P anyway; on small ones the direction kernel's blocks
+// are short and the extra bytes cost more there.)
 // Block (8, 32): thread (x, y) owns columns 4x..4x+3 of row y of each tile
 // (float4 accesses).
+template <bool MOVE_X>
 __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float* __restrict__ W,
-                                                         float* __restrict__ R, const double* rr,
+                                                         float* __restrict__ X, float* __restrict__ R,
+                                                         const __nv_bfloat16* __restrict__ ph,
+                                                         const __nv_bfloat16* __restrict__ pl, const double* rr,
                                                          const double* ptp, double* rr_new,
                                                          const int* __restrict__ cg_done, int* cg_count) {
   __shared__ float ta_[32][33], tb_[32][33];
@@ -626,10 +631,21 @@ __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float*
     ta_[y][x4] = wab.x; ta_[y][x4 + 1] = wab.y; ta_[y][x4 + 2] = wab.z; ta_[y][x4 + 3] = wab.w;
     tb_[y][x4] = wba.x; tb_[y][x4 + 1] = wba.y; tb_[y][x4 + 2] = wba.z; tb_[y][x4 + 3] = wba.w;
     __syncthreads();
+    // each tile: every load (R, and X with the P pair) issued before any store
     {
       float4 rv = *reinterpret_cast<const float4*>(R + iab);
+      float4 xv = make_float4(0.f, 0.f, 0.f, 0.f), pv = xv;
+      if constexpr (MOVE_X) {
+        xv = *reinterpret_cast<const float4*>(X + iab);
+        pv = load_split4(ph, pl, iab);
+      }
       const float tp0 = wab.x + tb_[x4][y], tp1 = wab.y + tb_[x4 + 1][y];
       const float tp2 = wab.z + tb_[x4 + 2][y], tp3 = wab.w + tb_[x4 + 3][y];
+      if constexpr (MOVE_X) {
+        xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
+        xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
+        *reinterpret_cast<float4*>(X + iab) = xv;
+      }
       rv.x = fmaf(-alpha, tp0, rv.x); rv.y = fmaf(-alpha, tp1, rv.y);
       rv.z = fmaf(-alpha, tp2, rv.z); rv.w = fmaf(-alpha, tp3, rv.w);
       *reinterpret_cast<float4*>(R + iab) = rv;
@@ -638,8 +654,18 @@ __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float*
     }
     if (a != b) {
       float4 rv = *reinterpret_cast<const float4*>(R + iba);
+      float4 xv = make_float4(0.f, 0.f, 0.f, 0.f), pv = xv;
+      if constexpr (MOVE_X) {
+        xv = *reinterpret_cast<const float4*>(X + iba);
+        pv = load_split4(ph, pl, iba);
+      }
       const float tp0 = wba.x + ta_[x4][y], tp1 = wba.y + ta_[x4 + 1][y];
       const float tp2 = wba.z + ta_[x4 + 2][y], tp3 = wba.w + ta_[x4 + 3][y];
+      if constexpr (MOVE_X) {
+        xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
+        xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
+        *reinterpret_cast<float4*>(X + iba) = xv;
+      }
       rv.x = fmaf(-alpha, tp0, rv.x); rv.y = fmaf(-alpha, tp1, rv.y);
       rv.z = fmaf(-alpha, tp2, rv.z); rv.w = fmaf(-alpha, tp3, rv.w);
       *reinterpret_cast<float4*>(R + iba) = rv;
@@ -657,13 +683,15 @@ __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float*
   }
 }
 
-// CG step 3: X += alpha P (X = alpha P on the first step), then
-// P = R + (rr_new / rr) P, split for the next product.  Runs exactly when the
-// step's update ran (cg_done changes only after this kernel).  P is kept only
-// as the BF16 (hi, lo) pair that the product reads.
-__global__ void k_cg_dir(WaveDev w, const float* __restrict__ R, float* __restrict__ X, const double* rr,
-                         const double* ptp, const double* rr_new, __nv_bfloat16* ph, __nv_bfloat16* pl,
-                         const int* __restrict__ cg_done, int first) {
+// CG step 3: when X is given, X += alpha P (X = alpha P on the first step);
+// then P = R + (rr_new / rr) P, split for the next product.  Runs exactly when
+// the step's update ran (cg_done changes only after this kernel).  P is kept
+// only as the BF16 (hi, lo) pair that the product reads.
+template <bool MOVE_X>
+__global__ void __launch_bounds__(256) k_cg_dir(WaveDev w, const float* __restrict__ R, float* __restrict__ X,
+                                                const double* rr, const double* ptp, const double* rr_new,
+                                                __nv_bfloat16* ph, __nv_bfloat16* pl,
+                                                const int* __restrict__ cg_done, int first) {
   const int s = blockIdx.y;
   if (cg_done[s]) return;
   const double d = rr[s];
@@ -678,18 +706,20 @@ __global__ void k_cg_dir(WaveDev w, const float* __restrict__ R, float* __restri
     const int64_t i = base + 4 * e4;
     const float4 r = *reinterpret_cast<const float4*>(R + i);
     const float4 p = load_split4(ph, pl, i);
-    float4 x = first ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(X + i);
-    x.x = fmaf(alpha, p.x, x.x); x.y = fmaf(alpha, p.y, x.y);
-    x.z = fmaf(alpha, p.z, x.z); x.w = fmaf(alpha, p.w, x.w);
-    *reinterpret_cast<float4*>(X + i) = x;
+    if constexpr (MOVE_X) {
+      float4 x = first ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(X + i);
+      x.x = fmaf(alpha, p.x, x.x); x.y = fmaf(alpha, p.y, x.y);
+      x.z = fmaf(alpha, p.z, x.z); x.w = fmaf(alpha, p.w, x.w);
+      *reinterpret_cast<float4*>(X + i) = x;
+    }
     store_split4(make_float4(fmaf(beta, p.x, r.x), fmaf(beta, p.y, r.y), fmaf(beta, p.z, r.z),
                              fmaf(beta, p.w, r.w)),
                  ph, pl, i);
   }
 }
 
-// CG start: R = P = C (already in R), rr = <C, C>, split P.  X is first
-// written by the first direction update (X = 0 here when no step runs).
+// CG start: R = P = C (already in R), rr = <C, C>, split P; X = 0 when X is
+// given (else the first direction update writes it).
 __global__ void k_cg_init(WaveDev w, float* __restrict__ X, const float* __restrict__ R, double* rr,
                           __nv_bfloat16* ph, __nv_bfloat16* pl) {
   __shared__ double red[32];
@@ -1314,7 +1344,11 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       // CG on L -> H L + L H, per submatrix until the relative residual is below cg_tol
       SM_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * 4 * max_wave, st));
       SM_CUDA(cudaMemsetAsync(ms->cg_done, 0, sizeof(int) * max_wave, st));
-      k_cg_init<<<eg, 256, 0, st>>>(wv.dev, cg_max > 0 ? nullptr : b.cx, b.cr, rr, b.Y[0], b.Y[1]);
+      // where X moves: in the direction kernel on large submatrices, in the
+      // update on small ones (measured: 14.5 against 6.9 ms per direction
+      // launch on 504-672-dim submatrices when the direction kernel moves X)
+      const bool x_in_dir = max_ld >= 1024 && cg_max > 0;
+      k_cg_init<<<eg, 256, 0, st>>>(wv.dev, x_in_dir ? nullptr : b.cx, b.cr, rr, b.Y[0], b.Y[1]);
       SM_KCHECK();
       SM_CUDA(cudaMemcpyAsync(rr0, rr, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
       for (int it = 0; it < cg_max; ++it) {
@@ -1327,10 +1361,20 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         gh.dot_c0 = ptp;
         gh.state = ms->cg_done; gh.skip_state = 1;
         SM_CUDA(launch(gh));
-        k_cg_update_pairs<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cw, b.cr, rr, ptp, rrn, ms->cg_done,
-                                                                 ms->cg_count);
-        SM_KCHECK();
-        k_cg_dir<<<eg, 256, 0, st>>>(wv.dev, b.cr, b.cx, rr, ptp, rrn, b.Y[0], b.Y[1], ms->cg_done, it == 0);
+        // the X-free variants compile as lean as the kernels without X
+        if (x_in_dir) {
+          k_cg_update_pairs<false><<<pair_grid(wv), dim3(8, 32), 0, st>>>(
+              wv.dev, b.cw, nullptr, b.cr, b.Y[0], b.Y[1], rr, ptp, rrn, ms->cg_done, ms->cg_count);
+          SM_KCHECK();
+          k_cg_dir<true><<<eg, 256, 0, st>>>(wv.dev, b.cr, b.cx, rr, ptp, rrn, b.Y[0], b.Y[1], ms->cg_done,
+                                             it == 0);
+        } else {
+          k_cg_update_pairs<true><<<pair_grid(wv), dim3(8, 32), 0, st>>>(
+              wv.dev, b.cw, b.cx, b.cr, b.Y[0], b.Y[1], rr, ptp, rrn, ms->cg_done, ms->cg_count);
+          SM_KCHECK();
+          k_cg_dir<false><<<eg, 256, 0, st>>>(wv.dev, b.cr, nullptr, rr, ptp, rrn, b.Y[0], b.Y[1], ms->cg_done,
+                                              0);
+        }
         SM_KCHECK();
         SM_CUDA(cudaMemcpyAsync(rr, rrn, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
         cg_total += 1;
