@@ -878,6 +878,78 @@ struct MixedState {
 
 }  // namespace
 
+// Launch plan of an exact sliced product: groups of slice products (one level
+// and one weight per exact FP32 accumulator, at most per_acc products),
+// sorted by decreasing weight, and launches of one group or of two groups
+// whose weights differ by at most 2^6 and whose slices fit in six operand
+// tiles per stage (see the comments at the product's use below).
+void slice_sets(const SliceGroup* g0, const SliceGroup* g1, int* as, int* na_out, int* bs, int* nb_out) {
+  int na = 0, nb = 0;
+  for (const SliceGroup* g : {g0, g1}) {
+    if (!g) continue;
+    for (int i = 0; i < g->np; ++i) {
+      bool fa = false, fb = false;
+      for (int k = 0; k < na; ++k) fa |= as[k] == g->pr[i][0];
+      for (int k = 0; k < nb; ++k) fb |= bs[k] == g->pr[i][1];
+      if (!fa) as[na++] = g->pr[i][0];
+      if (!fb) bs[nb++] = g->pr[i][1];
+    }
+  }
+  *na_out = na;
+  *nb_out = nb;
+}
+
+void slice_plan(int nx, int ny, bool sym_pairs, int per_acc, std::vector<SliceGroup>* groups_out,
+                std::vector<SliceLaunch>* launches) {
+  std::vector<SliceGroup>& groups = *groups_out;
+  groups.clear();
+  launches->clear();
+  for (int t = 2; t <= HP_MAX_LEVEL; ++t) {
+    int pairs[HP_SLICES][2];
+    int np = 0;
+    int diag_p = 0;
+    for (int pp = 1; pp <= nx; ++pp) {
+      const int qq = t - pp;
+      if (qq < 1 || qq > ny) continue;
+      if (sym_pairs && pp > qq) continue;
+      if (sym_pairs && pp == qq) { diag_p = pp; continue; }
+      pairs[np][0] = pp; pairs[np][1] = qq; ++np;
+    }
+    const int shift = HP_BITS * (HP_MAX_LEVEL - t);
+    for (int c0 = 0; c0 < np; c0 += per_acc) {
+      SliceGroup gr{};
+      gr.np = std::min(per_acc, np - c0);
+      for (int i = 0; i < gr.np; ++i) { gr.pr[i][0] = pairs[c0 + i][0]; gr.pr[i][1] = pairs[c0 + i][1]; }
+      gr.shift = shift + (sym_pairs ? 1 : 0);
+      groups.push_back(gr);
+    }
+    if (diag_p) {
+      SliceGroup gr{};
+      gr.np = 1; gr.pr[0][0] = gr.pr[0][1] = diag_p; gr.shift = shift;
+      groups.push_back(gr);
+    }
+  }
+  std::stable_sort(groups.begin(), groups.end(),
+                   [](const SliceGroup& x, const SliceGroup& y) { return x.shift > y.shift; });
+  std::vector<char> used(groups.size(), 0);
+  for (size_t i = 0; i < groups.size(); ++i) {
+    if (used[i]) continue;
+    used[i] = 1;
+    int best = -1, best_tiles = 1 << 30;
+    for (size_t j = i + 1; j < groups.size(); ++j) {
+      if (used[j] || groups[i].shift - groups[j].shift > 6) continue;
+      if (groups[i].np + groups[j].np > 4) continue;
+      int as[8], bs[8], na = 0, nb = 0;
+      slice_sets(&groups[i], &groups[j], as, &na, bs, &nb);
+      if (na + nb <= 6 && na + nb < best_tiles) { best = int(j); best_tiles = na + nb; }
+    }
+    if (best >= 0) used[best] = 1;
+    launches->push_back(SliceLaunch{int(i), best});
+  }
+}
+
+int slice_slices_max() { return HP_SLICES; }
+
 submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream_t st) {
   MixedBufs b = carve(ws, ws_elems);
   auto* ms = static_cast<MixedState*>(mixed);
@@ -1119,56 +1191,14 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     // tiles per stage: fewer launches, so fewer int64 passes.
     auto hp_product = [&](const int* xs, int nx, const int* ys, int ny, bool sym_pairs,
                           double* out) -> submat_status {
-      struct Group { int np; int pr[2][2]; int shift; };
-      std::vector<Group> groups;  // decreasing shift
-      for (int t = 2; t <= HP_MAX_LEVEL; ++t) {
-        int pairs[HP_SLICES][2];
-        int np = 0;
-        int diag_p = 0;
-        for (int pp = 1; pp <= nx; ++pp) {
-          const int qq = t - pp;
-          if (qq < 1 || qq > ny) continue;
-          if (sym_pairs && pp > qq) continue;
-          if (sym_pairs && pp == qq) { diag_p = pp; continue; }
-          pairs[np][0] = pp; pairs[np][1] = qq; ++np;
-        }
-        const int shift = HP_BITS * (HP_MAX_LEVEL - t);
-        for (int c0 = 0; c0 < np; c0 += per_acc) {
-          Group gr{};
-          gr.np = std::min(per_acc, np - c0);
-          for (int i = 0; i < gr.np; ++i) { gr.pr[i][0] = pairs[c0 + i][0]; gr.pr[i][1] = pairs[c0 + i][1]; }
-          gr.shift = shift + (sym_pairs ? 1 : 0);
-          groups.push_back(gr);
-        }
-        if (diag_p) {
-          Group gr{};
-          gr.np = 1; gr.pr[0][0] = gr.pr[0][1] = diag_p; gr.shift = shift;
-          groups.push_back(gr);
-        }
-      }
-      std::stable_sort(groups.begin(), groups.end(),
-                       [](const Group& x, const Group& y) { return x.shift > y.shift; });
-      // distinct A and B slices of a set of groups
-      auto count_sets = [&](const Group* g0, const Group* g1, int* as, int* na_out, int* bs_, int* nb_out) {
-        int na = 0, nb = 0;
-        for (const Group* g : {g0, g1}) {
-          if (!g) continue;
-          for (int i = 0; i < g->np; ++i) {
-            bool fa = false, fb = false;
-            for (int k = 0; k < na; ++k) fa |= as[k] == g->pr[i][0];
-            for (int k = 0; k < nb; ++k) fb |= bs_[k] == g->pr[i][1];
-            if (!fa) as[na++] = g->pr[i][0];
-            if (!fb) bs_[nb++] = g->pr[i][1];
-          }
-        }
-        *na_out = na;
-        *nb_out = nb;
-      };
+      std::vector<SliceGroup> groups;
+      std::vector<SliceLaunch> launches;
+      slice_plan(nx, ny, sym_pairs, per_acc, &groups, &launches);
       bool first = true;
       const int saved_bn = bn;
-      auto issue = [&](const Group* g0, const Group* g1) -> submat_status {
+      auto issue = [&](const SliceGroup* g0, const SliceGroup* g1) -> submat_status {
         int as[8], bs_[8], na = 0, nb = 0;
-        count_sets(g0, g1, as, &na, bs_, &nb);
+        slice_sets(g0, g1, as, &na, bs_, &nb);
         // 256-wide tiles when two pipeline stages of the launch's slices fit
         int w = opt.tile_n_hp ? opt.tile_n_hp : 128;
         if (w == 256 && tc_smem_bytes(na, nb, 2, 256) > 227 * 1024) w = 128;
@@ -1186,9 +1216,9 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         for (int k = 0; k < na; ++k) p.a_set[k] = xs[as[k] - 1];
         for (int k = 0; k < nb; ++k) p.b_set[k] = ys[bs_[k] - 1];
         int np = 0;
-        const Group* gs[2] = {g0, g1};
+        const SliceGroup* gs[2] = {g0, g1};
         for (int acc = 0; acc < 2; ++acc) {
-          const Group* g = gs[acc];
+          const SliceGroup* g = gs[acc];
           if (!g) continue;
           for (int i = 0; i < g->np; ++i, ++np) {
             int ia = 0, ib = 0;
@@ -1220,21 +1250,8 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         first = false;
         return SUBMAT_OK;
       };
-      std::vector<char> used(groups.size(), 0);
-      for (size_t i = 0; i < groups.size(); ++i) {
-        if (used[i]) continue;
-        used[i] = 1;
-        int best = -1, best_tiles = 1 << 30;
-        for (size_t j = i + 1; j < groups.size(); ++j) {
-          if (used[j] || groups[i].shift - groups[j].shift > 6) continue;
-          if (groups[i].np + groups[j].np > 4) continue;
-          int as[8], bs_[8], na = 0, nb = 0;
-          count_sets(&groups[i], &groups[j], as, &na, bs_, &nb);
-          if (na + nb <= 6 && na + nb < best_tiles) { best = int(j); best_tiles = na + nb; }
-        }
-        if (best >= 0) used[best] = 1;
-        SM_TRY(issue(&groups[i], best >= 0 ? &groups[best] : nullptr));
-      }
+      for (const SliceLaunch& L : launches)
+        SM_TRY(issue(&groups[L.g0], L.g1 >= 0 ? &groups[L.g1] : nullptr));
       use_width(saved_bn);
       return SUBMAT_OK;
     };

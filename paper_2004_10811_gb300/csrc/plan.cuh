@@ -20,6 +20,17 @@ constexpr int kPowerIters = 10;  // power steps of the spectral estimate
 void free_mixed(void* state);
 void free_adjoint_tc(void* state);
 
+// Launch plan of an exact sliced product (mixed.cu).  Slices are numbered
+// 1..n; a group is one exact accumulator: np products (pr[i] = (p, q)) of one
+// level and weight 2^shift.  A launch carries group g0 and, if g1 >= 0, group
+// g1 in a second accumulator (g0's weight the larger).
+struct SliceGroup { int np; int pr[2][2]; int shift; };
+struct SliceLaunch { int g0, g1; };
+void slice_plan(int nx, int ny, bool sym_pairs, int per_acc, std::vector<SliceGroup>* groups,
+                std::vector<SliceLaunch>* launches);
+void slice_sets(const SliceGroup* g0, const SliceGroup* g1, int* as, int* na, int* bs, int* nb);
+int slice_slices_max();
+
 
 struct Wave {
   int first = 0;           // first global block column of the wave

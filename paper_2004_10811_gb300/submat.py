@@ -28,7 +28,7 @@ EXPORTS = (
     "submat_options_default", "submat_plan_create", "submat_plan_destroy", "submat_sign",
     "submat_sign_host", "submat_trace", "submat_mu_search", "submat_sign_backward",
     "submat_plan_value_count", "submat_get_stats", "submat_get_sub_stats", "submat_last_error",
-    "submat_debug_tc_gemm", "submat_dense_sign_noalloc", "submat_autotune",
+    "submat_debug_tc_gemm", "submat_dense_sign_noalloc", "submat_autotune", "submat_debug_slice_plan",
 )
 
 
@@ -104,11 +104,14 @@ def load(path: str = LIB_PATH):
     lib.submat_debug_tc_gemm.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, C.c_int,
                                          vp, vp, C.c_int, C.c_double, C.c_int, vp]
     lib.submat_dense_sign_noalloc.argtypes = [C.c_int, vp, C.c_double, vp, C.POINTER(C.c_int), vp]
+    lib.submat_debug_slice_plan.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int,
+                                            C.POINTER(C.c_int32)]
     lib.submat_last_error.argtypes = []
     lib.submat_last_error.restype = C.c_char_p
     for name in ("submat_plan_create", "submat_plan_destroy", "submat_sign", "submat_sign_host",
                  "submat_trace", "submat_mu_search", "submat_sign_backward", "submat_get_stats",
-                 "submat_get_sub_stats", "submat_debug_tc_gemm", "submat_dense_sign_noalloc"):
+                 "submat_get_sub_stats", "submat_debug_tc_gemm", "submat_dense_sign_noalloc",
+                 "submat_debug_slice_plan"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -320,6 +323,19 @@ def debug_tc_gemm(A_hi, B_hi, A_lo=None, B_lo=None, n=None, sym=False, res2=None
                                   int(bool(skip_arrive)), float(timeout_s), int(tile_n), _stream(stream))
     _check(st, allow=(8,) if allow_timeout else ())
     return C_, STATUS[st]
+
+
+def debug_slice_plan(nx, ny, sym_pairs, per_acc):
+    """Host-only test hook (include/submat_debug.h): the launch plan of an exact
+    sliced product as an int32 array of (launch, accumulator, p, q, shift) rows."""
+    lib = load()
+    n = C.c_int32()
+    _check(lib.submat_debug_slice_plan(int(nx), int(ny), int(bool(sym_pairs)), int(per_acc), None, 0,
+                                       C.byref(n)))
+    out = np.zeros((max(1, n.value), 5), np.int32)
+    _check(lib.submat_debug_slice_plan(int(nx), int(ny), int(bool(sym_pairs)), int(per_acc),
+                                       out.ctypes.data_as(C.c_void_p), n.value, C.byref(n)))
+    return out[:n.value]
 
 
 NOALLOC_MAX_N = 512
