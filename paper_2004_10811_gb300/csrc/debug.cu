@@ -151,7 +151,7 @@ extern "C" submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, 
                                                  int cap, int32_t* count) {
   using namespace submat;
   clear_error();
-  const int smax = slice_slices_max();
+  const int smax = slice_max_slices();
   if (!count || nx < 1 || ny < 1 || nx > smax || ny > smax || (per_acc != 1 && per_acc != 2) ||
       (sym_pairs && nx != ny) || cap < 0) {
     set_error("bad argument to submat_debug_slice_plan");

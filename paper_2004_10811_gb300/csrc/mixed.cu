@@ -948,7 +948,7 @@ void slice_plan(int nx, int ny, bool sym_pairs, int per_acc, std::vector<SliceGr
   }
 }
 
-int slice_slices_max() { return HP_SLICES; }
+int slice_max_slices() { return HP_SLICES; }
 
 submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream_t st) {
   MixedBufs b = carve(ws, ws_elems);

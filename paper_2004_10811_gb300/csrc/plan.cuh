@@ -29,7 +29,7 @@ struct SliceLaunch { int g0, g1; };
 void slice_plan(int nx, int ny, bool sym_pairs, int per_acc, std::vector<SliceGroup>* groups,
                 std::vector<SliceLaunch>* launches);
 void slice_sets(const SliceGroup* g0, const SliceGroup* g1, int* as, int* na, int* bs, int* nb);
-int slice_slices_max();
+int slice_max_slices();
 
 
 struct Wave {
