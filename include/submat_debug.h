@@ -60,6 +60,23 @@ submat_status submat_debug_tc_gemm(int count, int ld, int n, const void* A_hi, c
 submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, int per_acc, int32_t* out, int cap,
                                       int32_t* count);
 
+/*
+ * Host-only (no GPU needed): the bisection of submat_mu_search (Section IV-G,
+ * Algorithm 1's outer loop) on the electron count of a given set of levels,
+ *   N(mu) = sum_i 1/2 (1 - sign(levels[i] - mu))   (sign(0) = 0),
+ * i.e. the trace of D for a diagonal K, with the spectral bound
+ * max_i |levels[i] - mu0|.
+ *   levels     host double[nlev]
+ *   n_el, mu0, tol, max_steps   as in submat_mu_search
+ *   mu_out     host double: the final mu
+ *   steps      host int32: evaluations of N
+ *   n_out      host double or NULL: N(mu_out)
+ * Returns what submat_mu_search returns: OK, MU_NO_ROOT, NOT_CONVERGED, or
+ * INVALID_ARG.
+ */
+submat_status submat_debug_mu_bisect(const double* levels, int nlev, double n_el, double mu0, double tol,
+                                     int max_steps, double* mu_out, int32_t* steps, double* n_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -180,4 +181,36 @@ extern "C" submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, 
     return SUBMAT_ERR_INVALID_ARG;
   }
   return SUBMAT_OK;
+}
+
+extern "C" submat_status submat_debug_mu_bisect(const double* levels, int nlev, double n_el, double mu0,
+                                                double tol, int max_steps, double* mu_out, int32_t* steps,
+                                                double* n_out) {
+  using namespace submat;
+  clear_error();
+  if (nlev < 0 || (nlev > 0 && !levels) || !mu_out || !steps || max_steps < 1 || !(tol > 0) ||
+      !std::isfinite(n_el) || !std::isfinite(mu0)) {
+    set_error("bad argument to submat_debug_mu_bisect");
+    return SUBMAT_ERR_INVALID_ARG;
+  }
+  auto count = [&](double mu) {
+    double c = 0.0;
+    for (int i = 0; i < nlev; ++i) c += levels[i] < mu ? 1.0 : (levels[i] == mu ? 0.5 : 0.0);
+    return c;
+  };
+  auto eval = [&](double mu, double* n) -> submat_status {
+    *n = count(mu);
+    return SUBMAT_OK;
+  };
+  auto bound = [&]() {
+    double b = 0.0;
+    for (int i = 0; i < nlev; ++i) b = std::max(b, std::fabs(levels[i] - mu0));
+    return b;
+  };
+  MuSearchOut r;
+  const submat_status s = mu_bisect(eval, bound, n_el, mu0, tol, max_steps, &r);
+  *mu_out = r.mu;
+  *steps = r.steps;
+  if (n_out) *n_out = count(r.mu);
+  return s;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include "common.cuh"
@@ -30,6 +31,19 @@ void slice_plan(int nx, int ny, bool sym_pairs, int per_acc, std::vector<SliceGr
                 std::vector<SliceLaunch>* launches);
 void slice_sets(const SliceGroup* g0, const SliceGroup* g1, int* as, int* na, int* bs, int* nb);
 int slice_max_slices();
+
+// The mu search's bracketing bisection on any evaluator of N(mu) (driver.cu).
+// bound() gives the spectral bound b at mu0 after the first evaluation.
+// Returns OK, MU_NO_ROOT (bracket below 1e-10 b), NOT_CONVERGED (max_steps)
+// or the evaluator's error; out->mu is the final mu, where the last
+// evaluation was made.
+struct MuSearchOut {
+  double mu = 0, n_best = 0, lo = 0, hi = 0;
+  int steps = 0;
+};
+submat_status mu_bisect(const std::function<submat_status(double, double*)>& eval,
+                        const std::function<double()>& bound, double n_el, double mu0, double tol,
+                        int max_steps, MuSearchOut* out);
 
 
 struct Wave {

@@ -29,6 +29,7 @@ EXPORTS = (
     "submat_sign_host", "submat_trace", "submat_mu_search", "submat_sign_backward",
     "submat_plan_value_count", "submat_get_stats", "submat_get_sub_stats", "submat_last_error",
     "submat_debug_tc_gemm", "submat_dense_sign_noalloc", "submat_autotune", "submat_debug_slice_plan",
+    "submat_debug_mu_bisect",
 )
 
 
@@ -106,12 +107,14 @@ def load(path: str = LIB_PATH):
     lib.submat_dense_sign_noalloc.argtypes = [C.c_int, vp, C.c_double, vp, C.POINTER(C.c_int), vp]
     lib.submat_debug_slice_plan.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int,
                                             C.POINTER(C.c_int32)]
+    lib.submat_debug_mu_bisect.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
+                                           C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_double)]
     lib.submat_last_error.argtypes = []
     lib.submat_last_error.restype = C.c_char_p
     for name in ("submat_plan_create", "submat_plan_destroy", "submat_sign", "submat_sign_host",
                  "submat_trace", "submat_mu_search", "submat_sign_backward", "submat_get_stats",
                  "submat_get_sub_stats", "submat_debug_tc_gemm", "submat_dense_sign_noalloc",
-                 "submat_debug_slice_plan"):
+                 "submat_debug_slice_plan", "submat_debug_mu_bisect"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -336,6 +339,19 @@ def debug_slice_plan(nx, ny, sym_pairs, per_acc):
     _check(lib.submat_debug_slice_plan(int(nx), int(ny), int(bool(sym_pairs)), int(per_acc),
                                        out.ctypes.data_as(C.c_void_p), n.value, C.byref(n)))
     return out[:n.value]
+
+
+def debug_mu_bisect(levels, n_el, mu0, tol=1e-9, max_steps=60):
+    """Host-only test hook (include/submat_debug.h): the mu search's bisection on
+    the electron count of the given levels.  Returns (mu, steps, N(mu), status)."""
+    lib = load()
+    lv = np.ascontiguousarray(levels, dtype=np.float64)
+    mu, n = C.c_double(), C.c_double()
+    steps = C.c_int32()
+    st = lib.submat_debug_mu_bisect(lv.ctypes.data_as(C.c_void_p), len(lv), float(n_el), float(mu0),
+                                    float(tol), int(max_steps), C.byref(mu), C.byref(steps), C.byref(n))
+    _check(st, allow=(6, 7))
+    return mu.value, steps.value, n.value, STATUS[st]
 
 
 NOALLOC_MAX_N = 512
