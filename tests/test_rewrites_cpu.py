@@ -1,0 +1,105 @@
+"""The CUDA path arranges the paper's iterations into products whose
+epilogues load no second operand.  These FP64 NumPy checks pin each
+rearrangement to the form it replaces, and the adjoint's arrangement to the
+oracle's Daleckii-Krein derivative, so a dropped term, a wrong factor or a
+transposed operand in the arrangement fails here on the CPU."""
+import numpy as np
+
+import oracle
+
+
+def sym(n, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((n, n)) * scale
+    return 0.5 * (a + a.T)
+
+
+def test_newton_schulz_as_x_times_z():
+    """Section II-B: X (3I - X^2) / 2 = X Z with Z = 1.5 I - 0.5 X^2 (the squaring writes Z)."""
+    x = sym(40, 1, 0.2)
+    i = np.eye(40)
+    z = 1.5 * i - 0.5 * x @ x
+    assert np.allclose(x @ z, 0.5 * x @ (3 * i - x @ x), rtol=0, atol=1e-14)
+
+
+def test_third_order_step_as_two_symmetric_products():
+    """Section VI-A: X (15I - 10X^2 + 3X^4) / 8 = X Z, Z = 3/8 W^2 + 5/6 I, W = X^2 - 5/3 I."""
+    x = sym(40, 2, 0.2)
+    i = np.eye(40)
+    x2 = x @ x
+    w = x2 - 5.0 / 3.0 * i
+    z = 0.375 * w @ w + 5.0 / 6.0 * i
+    assert np.allclose(x @ z, x @ (15 * i - 10 * x2 + 3 * x2 @ x2) / 8.0, rtol=0, atol=1e-13)
+
+
+def coupled_step_paper(x, e):
+    """[[X, E], [0, X]] <- 1/2 M (3I - M^2), written out for the blocks."""
+    i = np.eye(len(x))
+    return 0.5 * x @ (3 * i - x @ x), 0.5 * (e @ (3 * i - x @ x) - x @ (x @ e + e @ x))
+
+
+def upper_mirrored(c):
+    """A symmetric result as the kernels write it: upper tiles, then the mirror."""
+    return np.triu(c) + np.triu(c, 1).T
+
+
+def coupled_step_tensor_cores(x, e):
+    """The tensor-core adjoint's products, each C = A B^T with B read by rows:
+    Z = 1.5 I - 0.5 X X^T; U = X (E^T)^T; T = E Z^T - 1.5 E; T += Z (E^T)^T;
+    E' = T - 0.5 U X^T; X' = X Z^T.  Z and X' are symmetric results, written
+    from their upper triangles: without that exact symmetry X X^T differs from
+    X^2, and the antisymmetric part of X doubles every step."""
+    i = np.eye(len(x))
+    et = e.T.copy()                      # the transposed copy kept beside E
+    z = upper_mirrored(-0.5 * (x @ x.T) + 1.5 * i)
+    u = x @ et.T
+    t = e @ z.T - 1.5 * e
+    t = t + z @ et.T
+    e_new = t - 0.5 * (u @ x.T)
+    return upper_mirrored(x @ z.T), e_new
+
+
+def test_without_exact_symmetry_the_antisymmetric_part_grows():
+    """Why the symmetric products are mirrored: X <- X (1.5 I - 0.5 X X^T) doubles
+    an antisymmetric perturbation of X at the fixed point sign(a)."""
+    n = 20
+    rng = np.random.default_rng(6)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = (q * np.where(np.arange(n) < 7, -1.0, 1.0)) @ q.T
+    p = rng.standard_normal((n, n)) * 1e-12
+    x = s + (p - p.T)
+    i = np.eye(n)
+    for _ in range(10):
+        x = x @ (1.5 * i - 0.5 * x @ x.T)
+    assert np.max(np.abs(x - x.T)) > 100 * 2e-12
+    x = s + (p - p.T)
+    for _ in range(10):
+        x = upper_mirrored(x @ upper_mirrored(1.5 * i - 0.5 * x @ x.T))
+    assert np.max(np.abs(x - x.T)) == 0.0
+
+
+def test_adjoint_step_arrangement_equals_the_coupled_iteration():
+    x = sym(30, 3, 0.15)
+    rng = np.random.default_rng(4)
+    e = rng.standard_normal((30, 30)) * 0.1   # nonsymmetric, like G
+    xp, ep = coupled_step_paper(x, e)
+    xt, et = coupled_step_tensor_cores(x, e)
+    assert np.allclose(xt, xp, rtol=0, atol=1e-14)
+    assert np.allclose(et, ep, rtol=0, atol=1e-14)
+
+
+def test_adjoint_arrangement_converges_to_the_daleckii_krein_derivative():
+    n = 24
+    rng = np.random.default_rng(5)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([rng.uniform(-1.0, -0.3, 8), rng.uniform(0.3, 1.2, n - 8)])
+    a = (q * lam) @ q.T
+    a = 0.5 * (a + a.T)
+    g = rng.standard_normal((n, n))
+    beta = 1.05 * np.max(np.abs(lam))
+    x, e = a / beta, g / beta
+    for _ in range(40):
+        x, e = coupled_step_tensor_cores(x, e)
+    lam_o, q_o = np.linalg.eigh(a)
+    want = oracle.frechet_sign(lam_o, q_o, g)
+    assert np.max(np.abs(e - want)) <= 1e-10 * np.max(np.abs(want))
