@@ -103,3 +103,41 @@ def test_adjoint_arrangement_converges_to_the_daleckii_krein_derivative():
     lam_o, q_o = np.linalg.eigh(a)
     want = oracle.frechet_sign(lam_o, q_o, g)
     assert np.max(np.abs(e - want)) <= 1e-10 * np.max(np.abs(want))
+
+
+def correction_round(a, s_tilde, fc_sign=1.0, keep_fc_commutator=True):
+    """One correction round of the mixed path, in FP64 with exact products:
+    F_c = -1/2 S (I - S^2); H = (S a + a S) / 2; C = ([S, a] - [F_c, a]) S;
+    H F_a + F_a H = C (solved in H's eigenbasis); S <- S - F_c - F_a."""
+    i = np.eye(len(a))
+    fc = fc_sign * -0.5 * s_tilde @ (i - s_tilde @ s_tilde)
+    h = 0.5 * (s_tilde @ a + a @ s_tilde)
+    comm = s_tilde @ a - a @ s_tilde
+    if keep_fc_commutator:
+        comm = comm - (fc @ a - a @ fc)
+    c = comm @ s_tilde
+    w, q = np.linalg.eigh(h)
+    fa = q @ ((q.T @ c @ q) / (w[:, None] + w[None, :])) @ q.T
+    return s_tilde - fc - fa
+
+
+def test_correction_round_squares_the_error():
+    """The Newton step on {S^2 = I, [S, a] = 0}: an error delta of either symmetry
+    type leaves O(delta^2 |a| / gap); a flipped F_c or a dropped [F_c, a] does not."""
+    n = 60
+    rng = np.random.default_rng(7)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([rng.uniform(-1.0, -0.3, 20), rng.uniform(0.3, 1.4, n - 20)])
+    a = (q * lam) @ q.T
+    a = 0.5 * (a + a.T)
+    s = (q * np.sign(lam)) @ q.T
+    errs = []
+    for delta in (1e-4, 1e-5):
+        st = s + delta * sym(n, int(1e6 * delta))
+        before = np.max(np.abs(st - s))
+        after = np.max(np.abs(correction_round(a, st) - s))
+        assert after <= 50 * before ** 2, (delta, before, after)
+        errs.append(after)
+        assert np.max(np.abs(correction_round(a, st, fc_sign=-1.0) - s)) > 0.5 * before
+        assert np.max(np.abs(correction_round(a, st, keep_fc_commutator=False) - s)) > 50 * after
+    assert errs[0] / errs[1] > 30  # quadratic, not linear, in delta
