@@ -141,3 +141,61 @@ def test_correction_round_squares_the_error():
         assert np.max(np.abs(correction_round(a, st, fc_sign=-1.0) - s)) > 0.5 * before
         assert np.max(np.abs(correction_round(a, st, keep_fc_commutator=False) - s)) > 50 * after
     assert errs[0] / errs[1] > 30  # quadratic, not linear, in delta
+
+
+def six_bit_digits(m, k):
+    """Signed base-64 digits of integers |m| < 2^(6k), most significant first."""
+    s = np.sign(m)
+    a = np.abs(m)
+    return [s * ((a >> (6 * (k - p))) & 63) for p in range(1, k + 1)]
+
+
+def test_sliced_residual_products_are_exact_where_the_method_needs_it():
+    """The exact residual products of the mixed path (Section 5), in NumPy int64:
+    S on a 24-bit grid as four 6-bit slices, a's rows scaled to their maxima
+    and sliced six times, slice products of level p + q <= 8 summed with
+    weights 2^(6 (8 - p - q)).  S^2 from the p <= q products (p < q doubled)
+    plus an exact symmetrisation equals S_grid^2 exactly; S a comes within
+    ~2e-10 of the FP64 product (level <= 7 alone would leave ~4e-9)."""
+    n = 400
+    rng = np.random.default_rng(3)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([rng.uniform(-1.0, -0.3, 100), rng.uniform(0.3, 1.4, n - 100)])
+    a = (q * lam) @ q.T
+    a = 0.5 * (a + a.T)
+    s = (q * np.sign(lam)) @ q.T
+    e = int(np.ceil(np.log2(np.max(np.abs(s)))))
+    m = np.round(s / 2.0 ** (e - 24)).astype(np.int64)
+    m = (m + m.T) // 2 if not np.array_equal(m, m.T) else m
+    sl = six_bit_digits(m, 4)
+    assert np.array_equal(sum(d << (6 * (4 - p)) for p, d in enumerate(sl, 1)), m)
+    # every slice product's sum stays exact in FP32 (below 2^24) for K <= 2048
+    assert max(int(np.max(np.abs(x) @ np.abs(y).T)) for x in sl for y in sl) * (2048 // n) < 2 ** 24
+    # S^2: p <= q with p < q doubled, then the exact symmetric part
+    z = np.zeros((n, n), np.int64)
+    for p in range(1, 5):
+        for r in range(p, 5):
+            w = 2 if p < r else 1
+            z += w * (sl[p - 1] @ sl[r - 1].T) << (6 * (8 - p - r))
+    z_sym = (z + z.T) // 2
+    assert np.array_equal(z + z.T, 2 * z_sym)  # the symmetrisation is exact
+    assert np.array_equal(z_sym, m @ m)
+    # S a with a's rows scaled and sliced, levels <= 8 (and <= 7 for contrast)
+    rexp = np.ceil(np.log2(np.max(np.abs(a), axis=1))).astype(int)
+    ai = np.trunc(a / 2.0 ** (rexp[:, None] - 36)).astype(np.int64)
+    tl = six_bit_digits(ai, 6)
+    ref = (m * 2.0 ** (e - 24)) @ a
+
+    def sliced(max_level):
+        zz = np.zeros((n, n), np.int64)
+        for p in range(1, 5):
+            for r in range(1, 7):
+                if p + r <= max_level:
+                    zz += (sl[p - 1] @ tl[r - 1].T) << (6 * (8 - p - r))
+        assert np.max(np.abs(zz)) < 2 ** 62
+        return zz * 2.0 ** (e - 48) * 2.0 ** rexp[None, :]
+
+    scale = np.max(np.abs(ref))
+    err8 = np.max(np.abs(sliced(8) - ref)) / scale
+    err7 = np.max(np.abs(sliced(7) - ref)) / scale
+    assert err8 < 5e-10 and err7 > 1e-9, (err8, err7)
