@@ -199,3 +199,30 @@ def test_sliced_residual_products_are_exact_where_the_method_needs_it():
     err8 = np.max(np.abs(sliced(8) - ref)) / scale
     err7 = np.max(np.abs(sliced(7) - ref)) / scale
     assert err8 < 5e-10 and err7 > 1e-9, (err8, err7)
+
+
+def test_one_round_with_an_inexact_lyapunov_solve_meets_the_acceptance_bound():
+    """The one-round acceptance rule: with the Lyapunov solve to a relative 1e-3
+    (the CG tolerance) and delta <= 1e-5, the remaining error
+    delta^2 |a| / gap + delta 1e-3 stays below ~4e-8."""
+    n = 60
+    rng = np.random.default_rng(8)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([rng.uniform(-1.0, -0.3, 20), rng.uniform(0.3, 1.4, n - 20)])
+    a = (q * lam) @ q.T
+    a = 0.5 * (a + a.T)
+    s = (q * np.sign(lam)) @ q.T
+    i = np.eye(n)
+    p = sym(n, 9)
+    st = s + 1e-5 * p / np.max(np.abs(p))
+    delta = np.max(np.abs(st - s))
+    assert delta <= 1.0000001e-5
+    fc = -0.5 * st @ (i - st @ st)
+    h = 0.5 * (st @ a + a @ st)
+    c = ((st @ a - a @ st) - (fc @ a - a @ fc)) @ st
+    w, qh = np.linalg.eigh(h)
+    fa = qh @ ((qh.T @ c @ qh) / (w[:, None] + w[None, :])) @ qh.T
+    noise = sym(n, 10)
+    fa_cg = fa + 1e-3 * np.linalg.norm(fa) / np.linalg.norm(noise) * noise  # relative residual ~1e-3
+    err = np.max(np.abs(st - fc - fa_cg - s))
+    assert err < 4e-8, err
