@@ -1,11 +1,14 @@
 #!/usr/bin/env python
 """Benchmark: seconds per density-matrix build D = 1/2 (I - sign(K - mu I)).
 
-The workload is the 1,024-molecule water-like system with 23 functions per
-molecule (n = 23,552), an 8 Angstrom cutoff and mu = 0 (synthetic, seeded;
-the paper's CP2K water matrices are not available).  One step is one whole
+The default workload is the large-scale one: 20,736 water-like molecules
+with 6 functions each (n = 124,416), a 9 Angstrom cutoff (504-672-dim
+submatrices), the gap shrunk to +-0.15 and mu = 0 (synthetic, seeded; the
+paper's CP2K water matrices are not available).  One step is one whole
 build: gather, BF16x3 tensor-core Newton-Schulz, FP64-anchored correction,
-scatter -- every submatrix of the system.
+scatter -- every submatrix of the system.  Beside it the plain FP64 and FP32
+GPU paths are each timed over one whole build, and the CPU oracle on a
+bounded sample of block columns.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -44,7 +47,36 @@ FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 rate (recipe's nominal table)
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07
 L2_BYTES = 129 << 20           # GB300 L2
 CLASS_NAMES = ["tc_gemm_newton_schulz", "tc_gemm_correction", "simt_gemm_fp64", "gather",
-               "tc_gemm_sliced_fp64", "tc_gemm_adjoint"]
+               "tc_gemm_sliced_fp64", "tc_gemm_adjoint", "scatter", "reserved"]
+NCLASS = len(CLASS_NAMES)
+HBM_CLASSES = (3, 6)   # byte-counted kernels: gather, scatter
+
+
+def host_cores():
+    """(cores this process may run on, os.cpu_count(), the affinity list as a
+    compact string)."""
+    try:
+        aff = sorted(os.sched_getaffinity(0))
+    except Exception:  # pragma: no cover
+        aff = list(range(os.cpu_count() or 1))
+    runs, start = [], None
+    for i, c in enumerate(aff):
+        if start is None:
+            start = c
+        if i + 1 == len(aff) or aff[i + 1] != c + 1:
+            runs.append(f"{start}-{c}" if c != start else f"{c}")
+            start = None
+    return len(aff), os.cpu_count(), ",".join(runs)
+
+
+def oracle_sample(m, target_s, workers, cap=None):
+    """Block columns for a CPU oracle sample of about target_s seconds: a probe
+    of 2 x workers columns fixes the rate, the count follows from it."""
+    probe = sample_columns(m.nblk, min(m.nblk, 2 * workers))
+    _d, t = run_oracle_sample(m, probe, workers)
+    count = int(len(probe) * target_s / max(t, 1e-3))
+    count = max(len(probe), min(m.nblk, count if cap is None else min(cap, count)))
+    return sample_columns(m.nblk, count), len(probe), t
 
 
 def load_peaks():
@@ -128,10 +160,13 @@ def reference_arm(args, m, desc):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    workers = min(16, os.cpu_count() or 1)
-    cols = sample_columns(m.nblk, args.cpu_sample)
+    workers, ncpu, aff = host_cores()
+    if args.cpu_sample > 0:
+        cols = sample_columns(m.nblk, args.cpu_sample)
+    else:  # about 2 minutes of oracle work over all steps, at most 15 s per step
+        cols, _np, _tp = oracle_sample(m, min(15.0, 120.0 / max(1, args.steps)), workers)
     for _ in range(args.warmup):
-        run_oracle_sample(m, cols[: max(1, len(cols) // 4)], workers)
+        run_oracle_sample(m, cols[: max(1, len(cols) // 8)], workers)
     times = []
     for _ in range(args.steps):
         _d, t = run_oracle_sample(m, cols, workers)
@@ -143,9 +178,11 @@ def reference_arm(args, m, desc):
         "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "sampled_block_columns": len(cols)},
-        "cpu_baseline": {"value": per_build, "unit": "s/build", "cores": workers, "kind": "oracle",
+        "cpu_baseline": {"value": per_build, "unit": "s/build", "cores": workers, "cpu_count": ncpu,
+                         "affinity": aff, "kind": "oracle",
                          "sample": f"{len(cols)} of {m.nblk} block columns per step (numpy eigh per "
-                                   f"submatrix in a {workers}-process pool), scaled to a full build"},
+                                   f"submatrix in a {workers}-process pool, one per core this job may "
+                                   f"use), scaled to a full build"},
         "e2e": {"value": per_build, "unit": "s/build", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -189,10 +226,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="water1024_b23_rc8")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="water20736_b6_rc9")
     ap.add_argument("--prec", choices=["mixed", "fp64", "fp32"], default="mixed")
-    ap.add_argument("--cpu-sample", type=int, default=64, help="block columns in the oracle sample")
-    ap.add_argument("--fp64-sample", type=int, default=32, help="block columns timed on the FP64 path")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="block columns in the oracle sample (0: as many as about 15 s of oracle work)")
+    ap.add_argument("--fp64-sample", type=int, default=0,
+                    help="block columns timed on the FP64 path (0: the whole build)")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the whole-build FP32 path timing")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--adjoint-sample", type=int, default=32,
@@ -264,7 +304,8 @@ def main():
     torch.cuda.synchronize()
 
     # ---- device-resident timed region ----
-    acc = {"kernel_ms": [0.0] * 6, "kernel_launches": [0] * 6, "kernel_work": [0.0] * 6, "kernel_exec": [0.0] * 6,
+    acc = {"kernel_ms": [0.0] * NCLASS, "kernel_launches": [0] * NCLASS, "kernel_work": [0.0] * NCLASS,
+           "kernel_exec": [0.0] * NCLASS,
            "launches": 0, "flops_ns": 0.0, "flops_refine": 0.0}
     barrier()
     torch.cuda.synchronize()
@@ -365,14 +406,14 @@ def main():
 
     # ---- per-kernel-class roofline ----
     kernels = {}
-    for c in range(6):
+    for c in range(NCLASS):
         n = acc["kernel_launches"][c]
         if n == 0:
             continue
         ms = acc["kernel_ms"][c]
         work = acc["kernel_work"][c]
         exec_tf = None
-        if c == 3:
+        if c in HBM_CLASSES:
             achieved = work / (ms / 1e3) / 1e9
             unit, peak, bound, psrc = "GB/s", peaks["hbm_gbs"], "hbm", peak_src
         elif c in (0, 1, 4):
@@ -430,41 +471,66 @@ def main():
         line["kernels"] = kernels
 
     # ---- parity on sampled block columns and the CPU oracle baseline ----
+    want = cols = None
     if not args.no_cpu and world == 1 and not columns:
-        workers = min(16, os.cpu_count() or 1)
-        cols = sample_columns(m.nblk, args.cpu_sample)
+        workers, ncpu, aff = host_cores()
+        if args.cpu_sample > 0:
+            cols = sample_columns(m.nblk, args.cpu_sample)
+        else:  # about 15 s of oracle work
+            cols, _np, _tp = oracle_sample(m, 15.0, workers)
         want, t_cpu = run_oracle_sample(m, cols, workers)
         got = Dh.numpy()
         mask = ~np.isnan(want)
         line["max_abs_err_vs_oracle"] = float(np.max(np.abs(got[mask] - want[mask])))
         line["parity_sample"] = f"{len(cols)} of {m.nblk} block columns"
         line["cpu_baseline"] = {"value": t_cpu * m.nblk / len(cols), "unit": "s/build", "cores": workers,
-                                "kind": "oracle",
+                                "cpu_count": ncpu, "affinity": aff, "kind": "oracle",
                                 "sample": f"{len(cols)} of {m.nblk} block columns (numpy eigh per submatrix, "
-                                          f"{workers}-process pool), time scaled to the full build"}
+                                          f"{workers}-process pool, one per core this job may use), time "
+                                          f"scaled to the full build"}
 
-    # ---- the plain FP64 path on a contiguous chunk of block columns ----
-    if not args.no_fp64 and args.prec == "mixed" and world == 1 and not columns:
-        nc = min(args.fp64_sample, m.nblk)
-        with pkg.Plan.from_bsr(m, prec="fp64", columns=(0, nc), timing=True) as p64:
+    # ---- the plain FP64 and FP32 GPU paths, each over one whole build ----
+    def other_path(prec, ncols):
+        cols_opt = (0, ncols) if ncols else None
+        with pkg.Plan.from_bsr(m, prec=prec, columns=cols_opt, timing=True) as po:
             Dtmp = torch.zeros_like(K)
-            p64.sign(K, m.mu, out=Dtmp)
-            torch.cuda.synchronize()
             f0 = torch.cuda.Event(enable_timing=True)
             f1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
             f0.record(stream)
-            p64.sign(K, m.mu, out=Dtmp)
+            po.sign(K, m.mu, out=Dtmp)
             f1.record(stream)
             torch.cuda.synchronize()
-            t64 = f0.elapsed_time(f1) / 1e3
-            s64 = p64.stats()
-        sub_n3 = float(np.sum(sub["dims"].astype(np.float64) ** 3))
-        chunk_n3 = float(np.sum(sub["dims"][:nc].astype(np.float64) ** 3))
-        est = t64 * sub_n3 / chunk_n3
-        line["fp64_path"] = {"s_per_build_est": est, "sample": f"block columns [0, {nc}) timed, scaled by sum n^3",
-                             "chunk_s": t64, "iters_max": int(s64["iters_max"]),
-                             "tflops": s64["flops_ns"] / t64 / 1e12,
-                             "speedup_mixed_vs_fp64": est / value}
+            t = f0.elapsed_time(f1) / 1e3
+            so = po.stats()
+        out = {"iters_max": int(so["iters_max"]), "tflops": so["flops_ns"] / t / 1e12,
+               "waves": int(so["waves"]), "scale_reduced": int(so["scale_reduced"])}
+        if ncols:
+            sub_n3 = float(np.sum(sub["dims"].astype(np.float64) ** 3))
+            chunk_n3 = float(np.sum(sub["dims"][:ncols].astype(np.float64) ** 3))
+            out.update(s_per_build_est=t * sub_n3 / chunk_n3, chunk_s=t,
+                       measured=f"block columns [0, {ncols}) timed, scaled by sum n^3")
+        else:
+            out.update(s_per_build=t, measured="one whole build (every block column), CUDA events")
+            if want is not None:
+                got = Dtmp.cpu().numpy()
+                mask = ~np.isnan(want)
+                out["max_abs_err_vs_oracle"] = float(np.max(np.abs(got[mask] - want[mask])))
+                out["parity_sample"] = f"{len(cols)} of {m.nblk} block columns"
+        return out
+
+    if not args.no_fp64 and args.prec == "mixed" and world == 1 and not columns:
+        nc = min(args.fp64_sample, m.nblk)
+        f64 = other_path("fp64", nc)
+        t64 = f64.get("s_per_build", f64.get("s_per_build_est"))
+        f64["speedup_mixed_vs_fp64"] = t64 / value
+        line["fp64_path"] = f64
+    if not args.no_fp32 and args.prec == "mixed" and world == 1 and not columns:
+        # FP32 Newton-Schulz without refinement: its error is reported, not held
+        # to the mixed path's 1e-7
+        f32 = other_path("fp32", 0)
+        f32["speedup_mixed_vs_fp32"] = f32["s_per_build"] / value
+        line["fp32_path"] = f32
     # ---- the adjoint (vector-Jacobian product) on a contiguous chunk of block columns ----
     if args.adjoint_sample > 0 and world == 1 and not columns:
         nc = min(args.adjoint_sample, m.nblk)

@@ -73,8 +73,15 @@ typedef struct {
   int max_iter;                /* Newton-Schulz iteration cap; 0 selects 100 */
   int beta_mode;               /* X_0 = a / beta.  0 (default): beta = 1.05 x a 10-step
                                   power-iteration estimate of the spectral radius when that
-                                  is below the bound of mode 1 (any beta > rho / sqrt(3)
-                                  converges; a tighter beta saves iterations);
+                                  is below the bound of mode 1 (a tighter beta saves
+                                  iterations).  The estimate is only a lower bound on rho,
+                                  and an eigenvalue of X_0 beyond sqrt(3) would converge to
+                                  the wrong sign, so the scale is certified from the first
+                                  squaring: rho(X_0)^2 <= ||X_0^2||_inf (largest row
+                                  abs-sum, rounding included) must stay below 2.94 (2.2 for
+                                  the third-order iteration), else X_0 is scaled down to
+                                  meet it, never below 1.7 (1.45) / beta_bound, which is
+                                  safe by itself (submat_stats.scale_reduced counts them);
                                   1: beta = min(max row abs-sum, ||a||_F) >= rho(a) only */
   int symmetrize;              /* 1: return (D + D^T) / 2 on the pattern; 0: column-assembled D */
   size_t workspace_cap_bytes;  /* device workspace cap; 0 = 80 % of free memory at plan time */
@@ -132,20 +139,25 @@ typedef struct {
    *   0 tensor-core GEMM, Newton-Schulz;  1 tensor-core GEMM, correction
    *   (split products and the Lyapunov CG);  2 FP64/FP32 SIMT GEMM;
    *   3 gather (assembly) kernel;  4 tensor-core GEMM, sliced FP64-accurate
-   *   residual products;  5 tensor-core GEMM, adjoint (adjoint_mode 1).
+   *   residual products;  5 tensor-core GEMM, adjoint (adjoint_mode 1);
+   *   6 extraction (scatter) kernel;  7 reserved.
    * kernel_ms: summed launch durations.  kernel_work: algorithmic work of
    * those launches -- flops for the GEMM classes at the standard count (2 n^3
    * per n x n product the method needs, also where the kernels compute only
    * the upper tiles of a symmetric result; a split or sliced product counts
    * once, as the product it represents), bytes moved for the gather (8 per
-   * dense element written plus 8 per K value read).
+   * dense element written plus 8 per K value read) and the scatter (per
+   * extracted entry: the iterate read, 8 or 4 bytes, the mixed path's two
+   * FP32 corrections, and 8 for D written).
    * kernel_exec: MMA flops the tensor cores executed (every slice product,
    * tile padding included); 0 for the other classes. */
-  double  kernel_ms[6];
-  int32_t kernel_launches[6];
-  double  kernel_work[6];
-  double  kernel_exec[6];
+  double  kernel_ms[8];
+  int32_t kernel_launches[8];
+  double  kernel_work[8];
+  double  kernel_exec[8];
   int32_t mu_steps;        /* sign evaluations of the last submat_mu_search (0 otherwise) */
+  int32_t scale_reduced;   /* submatrices whose power-estimate scale the certificate did not
+                              prove safe, so X_0 was scaled down (see beta_mode) */
 } submat_stats;
 
 /* Fill *opt with defaults (FP64, default tolerances, beta_mode 0). */
@@ -202,12 +214,16 @@ submat_status submat_trace(submat_plan* plan, const double* D_vals, double* tr,
 /*
  * Find mu with Tr D(mu) = n_el (canonical adaptation, Section IV-G /
  * Algorithm 1), re-evaluating the submatrix signs at each trial mu.
- * Bisection on a bracket [mu0 - 1.01 b, mu0 + 1.01 b] (b: the largest
- * spectral bound of the submatrices at mu0), oriented by Tr D(mu0) - n_el.
- * (At zero temperature dN/dmu = 1/2 sum_j sum_{c in j} L_sign(a_j, I)_cc is
- * exactly zero for nonsingular a_j -- submat_sign_backward reports it -- so
- * Newton steps never apply.)
- *   n_el       target electron count;  mu0  starting guess
+ * Bisection on a bracket [mu0, mu0 + 1.01 b] or [mu0 - 1.01 b, mu0], on the
+ * side of n_el given by Tr D(mu0), where b = max_j min(max row abs-sum,
+ * ||a_j||_F) is a rigorous bound on the spectra of the submatrices at mu0,
+ * so that N at the far end is 0 or n.  (If the bisection closes in on the far
+ * end, that end is evaluated, and the bracket moves outward should it not
+ * hold n_el.)  At zero temperature dN/dmu = 1/2 sum_j sum_{c in j}
+ * L_sign(a_j, I)_cc is exactly zero for nonsingular a_j --
+ * submat_sign_backward reports it -- so Newton steps never apply.
+ *   n_el       target electron count, 0 <= n_el <= n (else INVALID_ARG)
+ *   mu0        starting guess
  *   tol        stop when |Tr D - n_el| <= tol * n_el
  *   max_steps  cap on sign evaluations (>= 1)
  *   mu_out     host double: final mu
@@ -215,6 +231,10 @@ submat_status submat_trace(submat_plan* plan, const double* D_vals, double* tr,
  * At zero temperature Tr D(mu) is a staircase: if the bracket shrinks below
  * 1e-10 x the spectral bound without meeting tol, the call returns
  * MU_NO_ROOT with mu_out and D at the bracket end nearest n_el.
+ * NOT_CONVERGED: the step cap was reached (mu_out and D at the evaluation
+ * nearest n_el), or the evaluation at mu_out left some submatrix
+ * unconverged (D written, see submat_get_stats); a submatrix that diverged
+ * (its involution residual grew past 1e6) ends the search at once.
  */
 submat_status submat_mu_search(submat_plan* plan, const double* K_vals, double n_el,
                                double mu0, double tol, int max_steps, double* mu_out,
@@ -275,8 +295,11 @@ submat_status submat_get_sub_stats(const submat_plan* plan, int32_t* dims, int32
  *
  *   D = 1/2 (I - sign(K - mu I))  for one dense symmetric n x n matrix K,
  *
- * by the same scaled FP64 Newton-Schulz iteration and kernels as the FP64
- * path, for callers that may not call cudaMalloc or cudaMallocHost: codes
+ * by scaled FP64 Newton-Schulz iteration on the FP64 path's kernels, with
+ * X_0 = (K - mu I) / beta and beta = min(max row abs-sum, ||K - mu I||_F),
+ * the rigorous bound only (no power-estimate tightening, so it may take a
+ * few more iterations than a plan), for callers that may not call
+ * cudaMalloc or cudaMallocHost: codes
  * that reserve the whole device for their own memory pool, allocators that
  * forbid foreign allocations, and time steps in which an allocation's
  * implicit device synchronisation is not acceptable.
@@ -286,9 +309,11 @@ submat_status submat_get_sub_stats(const submat_plan* plan, int32_t* dims, int32
  *   D_dev     device double[n * n], row-major (caller-owned output)
  *   iters_out host int or NULL: Newton-Schulz iterations taken
  * All scratch (6 MiB) is one file-scope device array that every GPU loading
- * the library holds until the process exits.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture on the device.  Every call shares the
+ * the library holds until the process exits.  Every call looks up that
+ * array's device address on the current device (cudaGetSymbolAddress, a
+ * host-side lookup that allocates nothing); the first call on a device also
+ * loads the library's device code there, so make that first call before
+ * any stream capture on the device.  Every call shares the
  * array and it keeps the previous call's contents, so calls whose work
  * overlaps on the GPU (other streams, other host threads) race; serialise
  * them.  The call synchronises `stream`.

@@ -65,9 +65,11 @@ submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, int per_acc
  * Algorithm 1's outer loop) on the electron count of a given set of levels,
  *   N(mu) = sum_i 1/2 (1 - sign(levels[i] - mu))   (sign(0) = 0),
  * i.e. the trace of D for a diagonal K, with the spectral bound
- * max_i |levels[i] - mu0|.
+ * bound_scale * max_i |levels[i] - mu0|.
  *   levels     host double[nlev]
  *   n_el, mu0, tol, max_steps   as in submat_mu_search
+ *   bound_scale  > 0; 1 gives the exact bound, below 1 a bound that
+ *              underestimates the spectrum (the bracket must then grow)
  *   mu_out     host double: the final mu
  *   steps      host int32: evaluations of N
  *   n_out      host double or NULL: N(mu_out)
@@ -75,7 +77,8 @@ submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, int per_acc
  * INVALID_ARG.
  */
 submat_status submat_debug_mu_bisect(const double* levels, int nlev, double n_el, double mu0, double tol,
-                                     int max_steps, double* mu_out, int32_t* steps, double* n_out);
+                                     int max_steps, double bound_scale, double* mu_out, int32_t* steps,
+                                     double* n_out);
 
 #ifdef __cplusplus
 }

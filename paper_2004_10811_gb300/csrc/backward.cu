@@ -182,6 +182,8 @@ submat_status Plan::backward_wave(Wave& wv, const double* K, double mu, const do
   SM_TRY(gather_wave(wv, K, mu, A, st));
   const int passes = dn_part ? 2 : 1;
   for (int pass = 0; pass < passes; ++pass) {
+    // iteration state and beta (the bound) reset for this pass
+    if (pass > 0) SM_CUDA(launch_beta(wv.dev, ns, opt.beta_mode, st));
     // X_0 = a / beta, E_0 = G / beta (or I / beta)
     if (sizeof(T) == 8) SM_CUDA(launch_scale_f64(wv.dev, A, reinterpret_cast<double*>(X[0]), ns.beta, wv.max_ld2, st));
     else SM_CUDA(launch_scale_f32(wv.dev, A, reinterpret_cast<float*>(X[0]), ns.beta, wv.max_ld2, st));
@@ -198,9 +200,8 @@ submat_status Plan::backward_wave(Wave& wv, const double* K, double mu, const do
     }
     k_bwd_seed<T><<<wv.n_gather, dim3(32, 8), 0, st>>>(g, wv.dev, wv.gather_items, Dbar, ns.beta, Ed[0], pass);
     SM_KCHECK();
-    // resets the iteration state (and beta to the bound, which the next pass
-    // scales by again; E_0 above took the final beta)
-    SM_CUDA(launch_beta(wv.dev, ns, opt.beta_mode, st));
+    // the power kernel used rprev for its estimate
+    SM_CUDA(launch_reset_rprev(wv.dev, ns, st));
     int cur = 0, extra = -1;
     for (int k = 0; k < opt.max_iter + 2; ++k) {
       Args a{};
@@ -223,6 +224,11 @@ submat_status Plan::backward_wave(Wave& wv, const double* K, double mu, const do
       T* Ec = Ed[cur];
       // Y = X^2 (symmetric), with the involution residual while still iterating
       SM_CUDA(gemm(wv.sym64, wv.n_sym64, Xc, Xc, nullptr, Y, 1.0, 0.0, 1, extra < 0 ? ns.res2 : nullptr));
+      if (k == 0 && opt.beta_mode == 0) {  // as in the forward paths; E_0 follows X_0
+        const CertSquare sq{sizeof(T) == 8 ? 0 : 1, Y, nullptr, 1.0f, 0.0f};
+        const CertLinear lin{2, {Xc, Ec, nullptr}, {nullptr, nullptr, nullptr}};
+        SM_CUDA(launch_certify(wv.dev, ns, sq, lin, cert_limits(false), max_ld(wv), d_flags + 2, st));
+      }
       if (extra < 0) SM_CUDA(launch_ns_update(wv.dev, ns, tol_eff, sizeof(T) == 8 ? 1e-9 : 1e-4, opt.max_iter, d_flags, st));
       // T1 = X E + E X
       SM_CUDA(gemm(wv.full64, wv.n_full64, Xc, Ec, nullptr, T1, 1.0, 0.0, 0, nullptr));

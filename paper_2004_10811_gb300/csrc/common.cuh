@@ -80,6 +80,8 @@ struct NsStateDev {
   double* beta;     // scale of X_0
   unsigned long long* gersh;  // max row abs-sum (bits of a non-negative double)
   double* fro2;     // ||a||_F^2
+  unsigned long long* cert;   // scale certificate: max row abs-sum of X_0^2 (bits)
+  double* cscale;   // scale certificate: factor applied to X_0 (1 = kept)
 };
 
 // ---- kernel launchers (kernels.cu) ----
@@ -121,6 +123,35 @@ cudaError_t launch_rescale_f64(const WaveDev& w, double* X, const double* rho, d
 cudaError_t launch_reset_rprev(const WaveDev& w, NsStateDev ns, cudaStream_t st);
 cudaError_t launch_rescale_f32(const WaveDev& w, float* X, const double* rho, double* beta,
                                const int* state, int64_t max_ld2, cudaStream_t st);
+
+// ---- scale certificate (certify.cu) ----
+// After the first squaring, ||X_0^2||_inf >= rho(X_0)^2 proves that the power
+// estimate's scale keeps the spectrum of X_0 inside the iteration's basin;
+// where it cannot, X_0 (and everything derived from it) is scaled down.
+// Representation of the squared iterate: 0 FP64 X^2, 1 FP32 X^2, 2 a BF16
+// (hi, lo) pair holding q = diag I + alpha X^2.
+struct CertSquare {
+  int mode;
+  void* hi;        // the square (FP64 / FP32 array, or the pair's hi)
+  void* lo;        // the pair's lo (mode 2)
+  float alpha, diag;
+};
+// Up to three buffers that scale linearly with X_0 (X_0 itself, E_0, E_0^T),
+// in the square's representation (pairs: hi, lo).
+struct CertLinear {
+  int count;
+  void* hi[3];
+  void* lo[3];
+};
+// basin of the iteration: Newton-Schulz (-sqrt 3, sqrt 3), third order
+// (-sqrt(7/3), sqrt(7/3)); the certificate keeps rho(X_0) below these with margin
+struct CertLimits {
+  double gmax;     // certified when the bound on rho(X_0)^2 is <= gmax
+  double fcap;     // X_0 = f a / beta_bound with f <= fcap is safe without it
+};
+CertLimits cert_limits(bool third_order);
+cudaError_t launch_certify(const WaveDev& w, NsStateDev ns, CertSquare sq, CertLinear lin, CertLimits lim,
+                           int max_ld, int* count, cudaStream_t st);
 
 // ---- FP64 GEMM (gemm_f64.cu) ----
 // C = alpha * A * B + beta * C0 on every listed 64x64 tile (s, ti, tj);

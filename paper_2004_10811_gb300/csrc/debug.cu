@@ -184,13 +184,17 @@ extern "C" submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, 
 }
 
 extern "C" submat_status submat_debug_mu_bisect(const double* levels, int nlev, double n_el, double mu0,
-                                                double tol, int max_steps, double* mu_out, int32_t* steps,
-                                                double* n_out) {
+                                                double tol, int max_steps, double bound_scale, double* mu_out,
+                                                int32_t* steps, double* n_out) {
   using namespace submat;
   clear_error();
   if (nlev < 0 || (nlev > 0 && !levels) || !mu_out || !steps || max_steps < 1 || !(tol > 0) ||
-      !std::isfinite(n_el) || !std::isfinite(mu0)) {
+      !std::isfinite(n_el) || !std::isfinite(mu0) || !(bound_scale > 0)) {
     set_error("bad argument to submat_debug_mu_bisect");
+    return SUBMAT_ERR_INVALID_ARG;
+  }
+  if (n_el < 0.0 || n_el > double(nlev)) {  // as submat_mu_search: outside [0, n]
+    set_error("n_el = %.17g outside [0, %d]", n_el, nlev);
     return SUBMAT_ERR_INVALID_ARG;
   }
   auto count = [&](double mu) {
@@ -205,7 +209,7 @@ extern "C" submat_status submat_debug_mu_bisect(const double* levels, int nlev, 
   auto bound = [&]() {
     double b = 0.0;
     for (int i = 0; i < nlev; ++i) b = std::max(b, std::fabs(levels[i] - mu0));
-    return b;
+    return b * bound_scale;
   };
   MuSearchOut r;
   const submat_status s = mu_bisect(eval, bound, n_el, mu0, tol, max_steps, &r);

@@ -27,9 +27,14 @@ submat_status Plan::sign_host(const double* K, double mu, double* D, cudaStream_
 // [lo, hi] with N(lo) <= n_el <= N(hi) and bisects it; a Newton step would use
 // dN/dmu, which the adjoint gives as exactly 0 at T = 0 for nonsingular
 // submatrices (L_sign(a, I) = 0), so bisection is the step that applies.
-// The bracket is [mu0 - 1.01 b, mu0 + 1.01 b] on the side of n_el, b the
-// spectral bound at mu0 (known after the first evaluation).  The last
-// evaluation is made at the returned mu, so that its side effects (D) match.
+// The bracket is [mu0, mu0 + 1.01 b] or [mu0 - 1.01 b, mu0] on the side of
+// n_el, b = bound() the spectral bound at mu0 (known after the first
+// evaluation): with a rigorous bound every eigenvalue of every submatrix lies
+// below mu0 + 1.01 b, so N there is the full count.  The far end is evaluated
+// only if the bisection closes in on it (the target in the last eighth of the
+// bracket); should it not hold n_el (a bound that was too small), the bracket
+// moves outward, twice the span each time.  The last evaluation is made at
+// the returned mu, so that its side effects (D) match.
 submat_status mu_bisect(const std::function<submat_status(double, double*)>& eval,
                         const std::function<double()>& bound, double n_el, double mu0, double tol,
                         int max_steps, MuSearchOut* out) {
@@ -43,20 +48,48 @@ submat_status mu_bisect(const std::function<submat_status(double, double*)>& eva
   r.n_best = n0;
   if (std::fabs(n0 - n_el) <= tol * std::fabs(n_el)) return SUBMAT_OK;
   const double bmax = bound();
-  const double span = 1.01 * bmax + 1e-12;
+  double span = 1.01 * bmax + 1e-12;
+  const bool up = n0 < n_el;
   double lo, hi;
-  if (n0 < n_el) { lo = mu0; hi = mu0 + span; } else { hi = mu0; lo = mu0 - span; }
+  if (up) { lo = mu0; hi = mu0 + span; } else { hi = mu0; lo = mu0 - span; }
+  double far = up ? hi : lo;  // not evaluated
   double best_mu = mu0, best_n = n0;
-  const double width_floor = 1e-10 * std::max(bmax, 1e-300);
+  double width_floor = 1e-10 * std::max(bmax, 1e-300);
+  auto consider = [&](double mu, double nm) {
+    last_mu = mu;
+    // the latest of the evaluations nearest n_el: at a step of the staircase
+    // that is an end of the final bracket
+    if (std::fabs(nm - n_el) <= std::fabs(best_n - n_el)) { best_mu = mu; best_n = nm; }
+  };
+  bool far_ok = false;  // N(far) has been seen on the other side of n_el
   while (r.steps < max_steps && (hi - lo) > width_floor) {
+    // the bisection has closed in on the unevaluated far end (the last eighth
+    // of the bracket): check that it holds n_el, else move the bracket outward
+    if (!far_ok && (up ? far - lo : hi - far) <= 0.125 * span) {
+      double nf = 0;
+      SM_TRY(eval(far, &nf));
+      ++r.steps;
+      consider(far, nf);
+      if (std::fabs(nf - n_el) <= tol * std::fabs(n_el)) {
+        r.mu = far;
+        r.n_best = nf;
+        r.lo = lo; r.hi = hi;
+        return SUBMAT_OK;
+      }
+      if (up ? nf >= n_el : nf <= n_el) {
+        far_ok = true;
+      } else {
+        span *= 2.0;
+        width_floor *= 2.0;  // 1e-10 of the grown bound
+        if (up) { lo = far; hi = far + span; far = hi; } else { hi = far; lo = far - span; far = lo; }
+      }
+      continue;
+    }
     const double mid = 0.5 * (lo + hi);
     double nm = 0;
     SM_TRY(eval(mid, &nm));
     ++r.steps;
-    last_mu = mid;
-    // the latest of the evaluations nearest n_el: at a step of the staircase
-    // that is an end of the final bracket
-    if (std::fabs(nm - n_el) <= std::fabs(best_n - n_el)) { best_mu = mid; best_n = nm; }
+    consider(mid, nm);
     if (std::fabs(nm - n_el) <= tol * std::fabs(n_el)) {
       r.mu = mid;
       r.n_best = nm;
@@ -64,6 +97,7 @@ submat_status mu_bisect(const std::function<submat_status(double, double*)>& eva
       return SUBMAT_OK;
     }
     if (nm < n_el) lo = mid; else hi = mid;
+    if (up ? hi != far : lo != far) far_ok = true;  // a mid value on the far side was seen
   }
   if (last_mu != best_mu) {
     double nb = 0;
@@ -84,23 +118,42 @@ submat_status mu_bisect(const std::function<submat_status(double, double*)>& eva
 
 submat_status Plan::mu_search(const double* K, double n_el, double mu0, double tol, int max_steps,
                               double* mu_out, double* D, cudaStream_t st) {
+  double n_total = 0.0;
+  for (int j = 0; j < nblk; ++j) n_total += bs[j];
+  if (n_el < 0.0 || n_el > n_total) {
+    set_error("n_el = %.17g outside [0, %.17g] (the matrix dimension)", n_el, n_total);
+    return SUBMAT_ERR_INVALID_ARG;
+  }
+  // status of the latest evaluation: a submatrix that did not converge there
+  // leaves D (and the trace) unfinished; one that diverged ends the search
+  submat_status last = SUBMAT_OK;
   auto eval = [&](double mu, double* n) -> submat_status {
-    submat_status s = sign(K, mu, D, st);
-    if (s != SUBMAT_OK && s != SUBMAT_ERR_NOT_CONVERGED) return s;
+    last = sign(K, mu, D, st);
+    if (last != SUBMAT_OK && last != SUBMAT_ERR_NOT_CONVERGED) return last;
+    if (last == SUBMAT_ERR_NOT_CONVERGED && (last_flags & FLAG_DIVERGED)) {
+      set_error("mu search: a submatrix diverged at mu = %.17g", mu);
+      return SUBMAT_ERR_NOT_CONVERGED;
+    }
     SM_TRY(trace(D, n, st));
     return SUBMAT_OK;
   };
-  // spectral bound: every eigenvalue of a_j = K_sub - mu0 I lies in [-beta_j, beta_j]
+  // rigorous spectral bound at mu0: every eigenvalue of a_j = K_sub - mu0 I
+  // lies in [-b_j, b_j], b_j = min(max row abs-sum, ||a_j||_F)
   auto bound = [&]() {
     double bmax = 0;
-    for (double b : res_beta) bmax = std::max(bmax, b);
+    for (int j = col_lo; j < col_hi; ++j) bmax = std::max(bmax, res_bound[j]);
     return bmax;
   };
   MuSearchOut r;
-  const submat_status s = mu_bisect(eval, bound, n_el, mu0, tol, max_steps, &r);
+  submat_status s = mu_bisect(eval, bound, n_el, mu0, tol, max_steps, &r);
   // every evaluation resets the statistics: the step count is set last
   stats.mu_steps = r.steps;
   if (s == SUBMAT_OK || s == SUBMAT_ERR_MU_NO_ROOT || s == SUBMAT_ERR_NOT_CONVERGED) *mu_out = r.mu;
+  if ((s == SUBMAT_OK || s == SUBMAT_ERR_MU_NO_ROOT) && last == SUBMAT_ERR_NOT_CONVERGED) {
+    set_error("mu search ended at mu = %.17g, where %d submatrices did not converge (D written)", r.mu,
+              stats.not_converged);
+    s = SUBMAT_ERR_NOT_CONVERGED;
+  }
   return s;
 }
 

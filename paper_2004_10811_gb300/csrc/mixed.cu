@@ -25,6 +25,7 @@
 #include <cstring>
 #include <vector>
 
+#include "pair.cuh"
 #include "plan.cuh"
 #include "tc_gemm.cuh"
 
@@ -75,39 +76,6 @@ MixedBufs carve(void* ws, int64_t E) {
   b.cr = reinterpret_cast<float*>(take(4));
   b.cw = reinterpret_cast<float*>(take(4));
   return b;
-}
-
-__device__ __forceinline__ void split2f(float v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  hi[i] = h;
-  lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
-}
-
-__device__ __forceinline__ void split2(double v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
-  split2f(d2f_trunc(v), hi, lo, i);
-}
-
-// four consecutive BF16 (hi, lo) pairs <-> four floats (hi + lo)
-__device__ __forceinline__ float4 load_split4(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int64_t i) {
-  const uint2 h = *reinterpret_cast<const uint2*>(hi + i);
-  const uint2 l = *reinterpret_cast<const uint2*>(lo + i);
-  return make_float4(__uint_as_float(h.x << 16) + __uint_as_float(l.x << 16),
-                     __uint_as_float(h.x & 0xFFFF0000u) + __uint_as_float(l.x & 0xFFFF0000u),
-                     __uint_as_float(h.y << 16) + __uint_as_float(l.y << 16),
-                     __uint_as_float(h.y & 0xFFFF0000u) + __uint_as_float(l.y & 0xFFFF0000u));
-}
-
-__device__ __forceinline__ void store_split4(float4 v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
-  const float x[4] = {v.x, v.y, v.z, v.w};
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const __nv_bfloat16 b = __float2bfloat16_rn(x[k]);
-    h[k] = __bfloat16_as_ushort(b);
-    l[k] = __bfloat16_as_ushort(__float2bfloat16_rn(x[k] - __bfloat162float(b)));
-  }
-  *reinterpret_cast<uint2*>(hi + i) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
-  *reinterpret_cast<uint2*>(lo + i) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
 }
 
 #define FOR_SUB_ELEMS(w)                                                                 \
@@ -1115,6 +1083,11 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       SM_CUDA(launch(g1));
       k_mirror_split<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Y[0], b.Y[1], ns.state, ST_DONE);
       SM_KCHECK();
+      if (k == 0 && opt.beta_mode == 0) {  // the power estimate's scale, proven from X_0^2 or reduced
+        const CertSquare sq{2, b.Y[0], b.Y[1], g1.alpha, g1.diag};
+        const CertLinear lin{1, {b.X[0][0], nullptr, nullptr}, {b.X[0][1], nullptr, nullptr}};
+        SM_CUDA(launch_certify(wv.dev, ns, sq, lin, cert_limits(third), max_ld(wv), d_flags + 2, st));
+      }
       SM_CUDA(launch_ns_update(wv.dev, ns, tol_eff, floor_thr, opt.max_iter, d_flags, st));
       int z_hi = MS_YH, z_lo = MS_YL;
       if (third) {  // Z = 3/8 W^2 + 5/6 I into H's buffers
@@ -1439,13 +1412,15 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       k_scale_picked<<<eg, 256, 0, st>>>(wv.dev, ms->pick, b.A, ns.beta, b.S);
       SM_KCHECK();
       // ping-pong between S and T; A serves as the X^2 buffer
-      SM_TRY((ns_simt<double, GemmF64Args>(wv, b.S, b.T, b.A, 1e-14, 1e-9, st, launch_gemm_f64)));
+      SM_TRY((ns_simt<double, GemmF64Args>(wv, b.S, b.T, b.A, 1e-14, 1e-9, st, launch_gemm_f64, false)));
       outS1 = b.T;
     }
     stats.refine_rounds = rounds;
     SM_CUDA(cudaEventRecord(ev[3], st));
     // ---- extract (Section III-A step 3); ns.par picks S or, for fallbacks, S/T ----
-    SM_CUDA(launch_scatter_f64(g, wv.dev, ns, outS0, outS1, D, d_trpart, nb_max, st, b.Fc, b.cx, ms->pick));
+    SM_TRY(scatter_timed(wv, 24.0, [&] {
+      return launch_scatter_f64(g, wv.dev, ns, outS0, outS1, D, d_trpart, nb_max, st, b.Fc, b.cx, ms->pick);
+    }, st));
     SM_TRY(collect_wave(wv, st));
     float t01 = 0, t12 = 0, t23 = 0;
     SM_CUDA(cudaEventElapsedTime(&t01, ev[0], ev[1]));
@@ -1698,6 +1673,11 @@ submat_status Plan::backward_wave_tc(size_t wi, const double* K, double mu, cons
       SM_CUDA(launch(g1));
       k_mirror_split<<<pg, dim3(8, 32), 0, st>>>(wv.dev, P[AS_ZH], P[AS_ZL], nullptr, 0);
       SM_KCHECK();
+      if (k == 0 && opt.beta_mode == 0) {  // as in the forward path; E_0 and E_0^T follow X_0
+        const CertSquare sq{2, P[AS_ZH], P[AS_ZL], g1.alpha, g1.diag};
+        const CertLinear lin{3, {P[AS_X0H], P[AS_E0H], P[AS_TH]}, {P[AS_X0L], P[AS_E0L], P[AS_TL]}};
+        SM_CUDA(launch_certify(wv.dev, ns, sq, lin, cert_limits(false), max_ld(wv), d_flags + 2, st));
+      }
       if (extra < 0) SM_CUDA(launch_ns_update(wv.dev, ns, tol_eff, floor_thr, opt.max_iter, d_flags, st));
       // U = X E (B: E^T)
       TcGemmParams gu = prm(wv.full256, wv.n_full256, xs, AS_TH, 0);

@@ -14,7 +14,6 @@
 
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include "common.cuh"
 #include "submat.h"
@@ -43,28 +42,18 @@ constexpr size_t NA_SMALL_DOUBLES = (sizeof(NaSmall) + sizeof(double) - 1) / siz
 // X0 | X1 | Y | small state.  6 MiB for n <= 512.
 __device__ __align__(256) double g_noalloc_scratch[3 * NA_ELEMS + NA_SMALL_DOUBLES];
 
-// Device address of g_noalloc_scratch per device, found once (see setup()).
-double* g_scratch_addr[64];
-std::mutex g_scratch_mu;
-
+// Device address of g_noalloc_scratch on the current device, looked up on
+// every call: the lookup is on the host and allocates nothing, and a cached
+// address would go stale if the caller reset the device (the module, and
+// with it the array, is then loaded again elsewhere).
 submat_status setup(double** out) {
-  int dev = 0;
-  SM_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) {
-    set_error("device index %d out of range for the scratch table", dev);
-    return SUBMAT_ERR_UNSUPPORTED;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    set_error("cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+    return SUBMAT_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error("cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
-      return SUBMAT_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<double*>(p);
   return SUBMAT_OK;
 }
 

@@ -405,6 +405,7 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
   res_iters.assign(nblk, 0);
   res_resid.assign(nblk, 0.0);
   res_beta.assign(nblk, 0.0);
+  res_bound.assign(nblk, 0.0);
   res_notconv.assign(nblk, 0);
   SM_CUDA(cudaStreamSynchronize(st));
   return SUBMAT_OK;
@@ -422,6 +423,8 @@ submat_status Plan::grow_ns_state(int count) {
   SM_TRY(alloc(&ns.beta, count, "ns beta"));
   SM_TRY(alloc(&ns.gersh, count, "ns gersh"));
   SM_TRY(alloc(&ns.fro2, count, "ns fro"));
+  SM_TRY(alloc(&ns.cert, count, "ns certificate"));
+  SM_TRY(alloc(&ns.cscale, count, "ns certificate"));
   max_wave = std::max(max_wave, count);
   return SUBMAT_OK;
 }
@@ -436,10 +439,14 @@ int max_ld(const Wave& wv) {
   return int(m);
 }
 
+// d_flags[0] is the status word; d_flags[2] counts the submatrices whose
+// scale the certificate reduced (since the last reset of the flags).
 submat_status Plan::read_flags(cudaStream_t st, int* out) {
-  SM_CUDA(cudaMemcpyAsync(h_pinned, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaMemcpyAsync(h_pinned, d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   SM_CUDA(cudaStreamSynchronize(st));
   *out = reinterpret_cast<int*>(h_pinned)[0];
+  last_flags = *out;
+  stats.scale_reduced = reinterpret_cast<int*>(h_pinned)[2];
   return SUBMAT_OK;
 }
 
@@ -466,11 +473,14 @@ submat_status Plan::gather_wave(Wave& wv, const double* K, double mu, double* A,
 
 submat_status Plan::collect_wave(const Wave& wv, cudaStream_t st) {
   std::vector<int> it(wv.count), nc(wv.count);
-  std::vector<double> rp(wv.count), be(wv.count);
+  std::vector<double> rp(wv.count), be(wv.count), fr(wv.count);
+  std::vector<unsigned long long> gs(wv.count);
   SM_CUDA(cudaMemcpyAsync(it.data(), ns.iters, sizeof(int) * wv.count, cudaMemcpyDeviceToHost, st));
   SM_CUDA(cudaMemcpyAsync(nc.data(), ns.notconv, sizeof(int) * wv.count, cudaMemcpyDeviceToHost, st));
   SM_CUDA(cudaMemcpyAsync(rp.data(), ns.rprev, sizeof(double) * wv.count, cudaMemcpyDeviceToHost, st));
   SM_CUDA(cudaMemcpyAsync(be.data(), ns.beta, sizeof(double) * wv.count, cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaMemcpyAsync(gs.data(), ns.gersh, sizeof(unsigned long long) * wv.count, cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaMemcpyAsync(fr.data(), ns.fro2, sizeof(double) * wv.count, cudaMemcpyDeviceToHost, st));
   SM_CUDA(cudaStreamSynchronize(st));
   for (int s = 0; s < wv.count; ++s) {
     const int j = wv.first + s;
@@ -478,6 +488,10 @@ submat_status Plan::collect_wave(const Wave& wv, cudaStream_t st) {
     res_notconv[j] = nc[s];
     res_resid[j] = rp[s] > 1e299 ? 0.0 : rp[s];
     res_beta[j] = be[s];
+    double gersh = 0.0;
+    std::memcpy(&gersh, &gs[s], sizeof(double));
+    // the bound beta of the gather's FP32 sums, with their margin
+    res_bound[j] = std::min(gersh, std::sqrt(fr[s])) * (1.0 + 1e-4);
   }
   return SUBMAT_OK;
 }
@@ -487,7 +501,7 @@ submat_status Plan::collect_wave(const Wave& wv, cudaStream_t st) {
 // ns.par[s] names the buffer that holds sign(a_s).
 template <typename T, typename Args>
 submat_status Plan::ns_simt(const Wave& wv, T* buf0, T* buf1, T* Y, double tol, double floor_thr,
-                            cudaStream_t st, cudaError_t (*gemm)(const Args&, cudaStream_t)) {
+                            cudaStream_t st, cudaError_t (*gemm)(const Args&, cudaStream_t), bool certify) {
   T* bufs[2] = {buf0, buf1};
   int cur = 0;
   for (int k = 0; k < opt.max_iter; ++k) {
@@ -500,6 +514,11 @@ submat_status Plan::ns_simt(const Wave& wv, T* buf0, T* buf1, T* Y, double tol, 
     SM_TRY(timer.start(KC_SIMT, st, &tk1));
     SM_CUDA(gemm(a1, st));
     SM_TRY(timer.stop(tk1, st));
+    if (k == 0 && certify) {  // the power estimate's scale, proven from X_0^2 or reduced
+      const CertSquare sq{sizeof(T) == 8 ? 0 : 1, Y, nullptr, 1.0f, 0.0f};
+      const CertLinear lin{1, {bufs[cur], nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+      SM_CUDA(launch_certify(wv.dev, ns, sq, lin, cert_limits(false), max_ld(wv), d_flags + 2, st));
+    }
     SM_CUDA(launch_ns_update(wv.dev, ns, tol, floor_thr, opt.max_iter, d_flags, st));
     Args a2 = a1;
     a2.B = Y; a2.C0 = bufs[cur]; a2.C = bufs[cur ^ 1];
@@ -531,9 +550,11 @@ submat_status Plan::sign_fp64(const double* K, double mu, double* D, cudaStream_
       SM_CUDA(launch_reset_rprev(wv.dev, ns, st));
     }
     SM_CUDA(cudaEventRecord(ev[1], st));
-    SM_TRY((ns_simt<double, GemmF64Args>(wv, B0, B1, Y, tol_eff, 1e-9, st, launch_gemm_f64)));
+    SM_TRY((ns_simt<double, GemmF64Args>(wv, B0, B1, Y, tol_eff, 1e-9, st, launch_gemm_f64,
+                                         opt.beta_mode == 0)));
     SM_CUDA(cudaEventRecord(ev[2], st));
-    SM_CUDA(launch_scatter_f64(g, wv.dev, ns, B0, B1, D, d_trpart, nb_max, st));
+    SM_TRY(scatter_timed(wv, 16.0, [&] { return launch_scatter_f64(g, wv.dev, ns, B0, B1, D, d_trpart, nb_max, st); },
+                         st));
     SM_CUDA(cudaEventRecord(ev[3], st));
     SM_TRY(collect_wave(wv, st));
     SM_TRY(add_phase_times());
@@ -556,13 +577,27 @@ submat_status Plan::sign_fp32(const double* K, double mu, double* D, cudaStream_
       SM_CUDA(launch_reset_rprev(wv.dev, ns, st));
     }
     SM_CUDA(cudaEventRecord(ev[1], st));
-    SM_TRY((ns_simt<float, GemmF32Args>(wv, B0, B1, Y, tol_eff, 1e-4, st, launch_gemm_f32)));
+    SM_TRY((ns_simt<float, GemmF32Args>(wv, B0, B1, Y, tol_eff, 1e-4, st, launch_gemm_f32,
+                                        opt.beta_mode == 0)));
     SM_CUDA(cudaEventRecord(ev[2], st));
-    SM_CUDA(launch_scatter_f32(g, wv.dev, ns, B0, B1, D, d_trpart, nb_max, st));
+    SM_TRY(scatter_timed(wv, 12.0, [&] { return launch_scatter_f32(g, wv.dev, ns, B0, B1, D, d_trpart, nb_max, st); },
+                         st));
     SM_CUDA(cudaEventRecord(ev[3], st));
     SM_TRY(collect_wave(wv, st));
     SM_TRY(add_phase_times());
   }
+  return SUBMAT_OK;
+}
+
+submat_status Plan::scatter_timed(const Wave& wv, double bytes_per_entry,
+                                  const std::function<cudaError_t()>& launch, cudaStream_t st) {
+  size_t tk;
+  SM_TRY(timer.start(KC_SCATTER, st, &tk));
+  SM_CUDA(launch());
+  SM_TRY(timer.stop(tk, st));
+  if (timer.on)
+    for (int s = 0; s < wv.count; ++s)
+      stats.kernel_work[KC_SCATTER] += bytes_per_entry * double(wv.host_n[s]) * bs[wv.first + s];
   return SUBMAT_OK;
 }
 

@@ -97,7 +97,10 @@ struct KernelTimer {
   submat_status collect(double* ms, int32_t* count);  // after a stream sync
 };
 
-enum KernelClass { KC_TC_NS = 0, KC_TC_REF = 1, KC_SIMT = 2, KC_GATHER = 3, KC_TC_HP = 4, KC_TC_ADJ = 5 };
+enum KernelClass {
+  KC_TC_NS = 0, KC_TC_REF = 1, KC_SIMT = 2, KC_GATHER = 3, KC_TC_HP = 4, KC_TC_ADJ = 5, KC_SCATTER = 6,
+  KC_COUNT = 8
+};
 
 int max_ld(const Wave& wv);
 
@@ -146,7 +149,8 @@ struct Plan {
 
   // results of the last evaluation (per global block column)
   std::vector<int> res_iters, res_notconv;
-  std::vector<double> res_resid, res_beta;
+  std::vector<double> res_resid, res_beta, res_bound;  // res_bound: min(max row abs-sum, ||a||_F)
+  int last_flags = 0;              // status word of the last read_flags
   submat_stats stats{};
   KernelTimer timer;
   long long launches_at_start = 0;
@@ -173,6 +177,10 @@ struct Plan {
   submat_status gather_wave(Wave& wv, const double* K, double mu, double* A, cudaStream_t st);
   submat_status collect_wave(const Wave& wv, cudaStream_t st);
   submat_status add_phase_times();
+  // the extraction of one wave, timed as class KC_SCATTER (bytes_per_entry:
+  // what one extracted entry reads and writes)
+  submat_status scatter_timed(const Wave& wv, double bytes_per_entry, const std::function<cudaError_t()>& launch,
+                              cudaStream_t st);
   void reset_stats();
   void finish_stats(bool adjoint = false);
   submat_status sign_fp64(const double* K, double mu, double* D, cudaStream_t st);
@@ -187,7 +195,7 @@ struct Plan {
   submat_status grow_ns_state(int count);
   template <typename T, typename Args>
   submat_status ns_simt(const Wave& wv, T* buf0, T* buf1, T* Y, double tol, double floor_thr,
-                        cudaStream_t st, cudaError_t (*gemm)(const Args&, cudaStream_t));
+                        cudaStream_t st, cudaError_t (*gemm)(const Args&, cudaStream_t), bool certify);
 };
 
 template <typename T>

@@ -63,8 +63,8 @@ class Stats(C.Structure):
         ("flops_ns", C.c_double), ("flops_refine", C.c_double), ("max_resid", C.c_double),
         ("ms_gather", C.c_double), ("ms_ns", C.c_double), ("ms_refine", C.c_double),
         ("ms_scatter", C.c_double), ("workspace_bytes", C.c_size_t), ("launches", C.c_int64),
-        ("kernel_ms", C.c_double * 6), ("kernel_launches", C.c_int32 * 6), ("kernel_work", C.c_double * 6),
-        ("kernel_exec", C.c_double * 6), ("mu_steps", C.c_int32),
+        ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_int32 * 8), ("kernel_work", C.c_double * 8),
+        ("kernel_exec", C.c_double * 8), ("mu_steps", C.c_int32), ("scale_reduced", C.c_int32),
     ]
 
     def as_dict(self):
@@ -108,7 +108,8 @@ def load(path: str = LIB_PATH):
     lib.submat_debug_slice_plan.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int,
                                             C.POINTER(C.c_int32)]
     lib.submat_debug_mu_bisect.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
-                                           C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+                                           C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_double)]
     lib.submat_last_error.argtypes = []
     lib.submat_last_error.restype = C.c_char_p
     for name in ("submat_plan_create", "submat_plan_destroy", "submat_sign", "submat_sign_host",
@@ -341,15 +342,17 @@ def debug_slice_plan(nx, ny, sym_pairs, per_acc):
     return out[:n.value]
 
 
-def debug_mu_bisect(levels, n_el, mu0, tol=1e-9, max_steps=60):
+def debug_mu_bisect(levels, n_el, mu0, tol=1e-9, max_steps=60, bound_scale=1.0):
     """Host-only test hook (include/submat_debug.h): the mu search's bisection on
-    the electron count of the given levels.  Returns (mu, steps, N(mu), status)."""
+    the electron count of the given levels, with the spectral bound scaled by
+    ``bound_scale``.  Returns (mu, steps, N(mu), status)."""
     lib = load()
     lv = np.ascontiguousarray(levels, dtype=np.float64)
     mu, n = C.c_double(), C.c_double()
     steps = C.c_int32()
     st = lib.submat_debug_mu_bisect(lv.ctypes.data_as(C.c_void_p), len(lv), float(n_el), float(mu0),
-                                    float(tol), int(max_steps), C.byref(mu), C.byref(steps), C.byref(n))
+                                    float(tol), int(max_steps), float(bound_scale), C.byref(mu),
+                                    C.byref(steps), C.byref(n))
     _check(st, allow=(6, 7))
     return mu.value, steps.value, n.value, STATUS[st]
 

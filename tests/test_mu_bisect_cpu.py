@@ -69,3 +69,29 @@ def test_bad_arguments_rejected(sm):
     with pytest.raises(sm.SubmatError) as ei:
         sm.debug_mu_bisect([0.0, 1.0], 1.0, 0.5, tol=0.0)
     assert ei.value.name == "INVALID_ARG"
+
+
+@pytest.mark.parametrize("scale", [0.5, 0.1, 0.01])
+def test_underestimated_bound_grows_the_bracket(sm, scale):
+    """A spectral bound below the true one starts the bracket short of the
+    target; the far end is then evaluated and the bracket moves outward until
+    it holds n_el, so the search still lands on the right plateau or step."""
+    lv = gapped_levels(4)
+    mu, steps, n, status = sm.debug_mu_bisect(lv, 40.0, -0.95, tol=1e-9, bound_scale=scale)
+    assert status == "OK"
+    assert n == 40.0 == count(lv, mu)
+    assert lv[39] < mu < lv[40]
+    mu, steps, n, status = sm.debug_mu_bisect(lv, 40.5, -0.95, tol=1e-12, max_steps=80,
+                                              bound_scale=scale)
+    assert status == "MU_NO_ROOT"
+    assert abs(mu - lv[40]) <= 2e-10 * np.max(np.abs(lv + 0.95))
+    assert n in (40.0, 41.0)
+
+
+def test_unreachable_target_is_rejected(sm):
+    """A target outside [0, n] can never be met: rejected before any evaluation."""
+    lv = gapped_levels(5)
+    for target in (100.5, -0.5):
+        with pytest.raises(sm.SubmatError) as ei:
+            sm.debug_mu_bisect(lv, target, 0.0, tol=1e-9)
+        assert ei.value.name == "INVALID_ARG"

@@ -62,6 +62,29 @@ def test_noalloc_matches_plan_path_on_two_calls(sm):
         assert 5 < iters < 60
 
 
+def test_noalloc_allocates_no_device_memory(sm):
+    """After a first call (which loads the library's device code and with it
+    the fixed scratch array), further calls on other sizes leave the device's
+    free memory and torch's allocator untouched."""
+    import torch
+    a1, a2 = dense_case(300, 3), dense_case(97, 4)
+    K1 = torch.from_numpy(a1).cuda()
+    K2 = torch.from_numpy(a2).cuda()
+    D1 = torch.empty_like(K1)
+    D2 = torch.empty_like(K2)
+    sm.dense_sign_noalloc(K1, 0.0, out=D1)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(2):
+        sm.dense_sign_noalloc(K2, 0.1, out=D2)
+        sm.dense_sign_noalloc(K1, -0.1, out=D1)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
 def test_noalloc_rejects_oversize(sm):
     import torch
     K = torch.zeros(513, 513, dtype=torch.float64, device="cuda")
