@@ -7,6 +7,10 @@ It shares no code with the CUDA path: it is plain NumPy/LAPACK in float64,
 following the paper step by step (Section III-A, Eqs. eigendecompsym and
 signevext, Algorithm 1).
 
+Finite temperature (``oracle.fermi``): the Fermi function in place of
+signum (Section IV-F, last paragraph), with its electron count, dN/dmu, a
+bracketed Newton search for mu and the Daleckii-Krein gradient.
+
 Parity unpinned: results that depend on eigenvalues of a submatrix lying
 within about 1e-8 of the chemical potential (the answer there is
 ill-conditioned, sensitivity ~ rounding / |lambda|); see the pins in
@@ -28,4 +32,15 @@ from .submatrix import (  # noqa: F401
     band_energy_grad,
     sign_backward,
     dense_sign,
+)
+from .fermi import (  # noqa: F401
+    fermi,
+    fermi_deriv,
+    fermi_by_eigh,
+    density_matrix_T,
+    n_elec_T,
+    dn_dmu_T,
+    mu_search_newton_T,
+    frechet_fermi,
+    fermi_backward,
 )
