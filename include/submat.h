@@ -114,6 +114,17 @@ typedef struct {
                                   precision (FP32 for mixed plans); 1 BF16x3 tensor cores, mixed
                                   plans only (UNSUPPORTED otherwise) -- about 15x faster, with
                                   about 10x the error of mode 0 (BF16x3 carries ~16 bits) */
+  double kT;                   /* electronic temperature (Section IV-F, last paragraph: the
+                                  Fermi function in place of signum), in the units of K;
+                                  0 (default) is zero temperature.  With kT > 0 every call
+                                  that evaluates D returns D = f(K - mu I),
+                                  f(x) = 1 / (1 + exp(x / kT)) = (1 - tanh(x / 2kT)) / 2, per
+                                  submatrix by a Chebyshev series of tanh (truncation below
+                                  1e-13 for FP64 plans, 1e-8 for FP32) on the SIMT GEMM in the
+                                  plan's precision; mixed plans return UNSUPPORTED.  The
+                                  series degree grows like (spectral scale) / kT: a degree
+                                  above 8191 returns UNSUPPORTED.  submat_mu_search then takes
+                                  Newton steps on the smooth Tr D(mu) (submat_stats.dn_dmu) */
 } submat_options;
 
 /* Aggregate statistics of the last submat_sign / submat_mu_search call. */
@@ -158,6 +169,13 @@ typedef struct {
   int32_t mu_steps;        /* sign evaluations of the last submat_mu_search (0 otherwise) */
   int32_t scale_reduced;   /* submatrices whose power-estimate scale the certificate did not
                               prove safe, so X_0 was scaled down (see beta_mode) */
+  int32_t poly_degree;     /* finite temperature: the largest Chebyshev degree of the last
+                              evaluation (iters_* then count its matrix products) */
+  double  poly_trunc;      /* ... and its truncation bound, sum of |c_k| beyond the degree */
+  double  dn_dmu;          /* finite temperature: dN/dmu = sum_j sum_{c in block j}
+                              [f(a_j) (1 - f(a_j))]_cc / kT at the last evaluation's mu,
+                              over the evaluated block columns (-L_f(a_j, I) summed; the
+                              adjoint's quantity); 0 at zero temperature */
 } submat_stats;
 
 /* Fill *opt with defaults (FP64, default tolerances, beta_mode 0). */

@@ -80,6 +80,23 @@ submat_status submat_debug_mu_bisect(const double* levels, int nlev, double n_el
                                      int max_steps, double bound_scale, double* mu_out, int32_t* steps,
                                      double* n_out);
 
+/*
+ * Host-only (no GPU needed): the finite-temperature polynomial (Section IV-F,
+ * last paragraph; the Fermi function (1 - tanh(x / 2kT)) / 2).  The
+ * Chebyshev series of tanh(c x) on [-1, 1], cut at the smallest odd degree m
+ * whose coefficient tail sum_{k > m} |c_k| is <= tol, in the baby-step /
+ * giant-step form the GPU evaluates:
+ *   p(x) = sum_{j < blocks} R_j(x) T_j(T_16(x)),
+ *   R_j(x) = sum_{q < 8} r_out[8 j + q] T_{2q+1}(x).
+ *   c          the scale sigma / (2 kT) (> 0)
+ *   tol        truncation tolerance (> 0)
+ *   max_degree largest accepted degree (1 .. 8191); above it UNSUPPORTED
+ *   r_out      host double[8 * blocks] or NULL (cap: its length)
+ *   degree, blocks, trunc   host outputs: m, the giant-step count, the tail sum
+ */
+submat_status submat_debug_fermi_poly(double c, double tol, int max_degree, double* r_out, int cap,
+                                      int32_t* degree, int32_t* blocks, double* trunc);
+
 #ifdef __cplusplus
 }
 #endif

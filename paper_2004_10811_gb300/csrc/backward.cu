@@ -272,6 +272,7 @@ submat_status Plan::backward_wave(Wave& wv, const double* K, double mu, const do
 
 submat_status Plan::backward(const double* K, double mu, const double* Dbar, double* Kbar,
                              double* dN_dmu, cudaStream_t st) {
+  if (opt.kT > 0.0) return backward_fermi(K, mu, Dbar, Kbar, dN_dmu, st);
   reset_stats();
   SM_CUDA(cudaMemsetAsync(d_flags, 0, 4 * sizeof(int), st));
   SM_CUDA(launch_check_finite(Dbar, nvals, d_flags, st));

@@ -183,6 +183,15 @@ CertLimits cert_limits(bool third_order) {
   return third_order ? CertLimits{2.2, 1.45} : CertLimits{2.94, 1.7};
 }
 
+cudaError_t launch_cert_rowsum(const WaveDev& w, NsStateDev ns, CertSquare sq, int max_ld, cudaStream_t st) {
+  if (w.nsub <= 0) return cudaSuccess;
+  int bx = (max_ld + 7) / 8;
+  if (bx > 32) bx = 32;
+  k_cert_rowsum<<<dim3(unsigned(bx), unsigned(w.nsub)), 256, 0, st>>>(w, sq, ns.state, ns.cert);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_certify(const WaveDev& w, NsStateDev ns, CertSquare sq, CertLinear lin, CertLimits lim,
                            int max_ld, int* count, cudaStream_t st) {
   if (w.nsub <= 0) return cudaSuccess;

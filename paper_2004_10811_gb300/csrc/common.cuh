@@ -106,6 +106,11 @@ cudaError_t launch_scatter_f64(const PatternDev& g, const WaveDev& w, NsStateDev
 cudaError_t launch_scatter_f32(const PatternDev& g, const WaveDev& w, NsStateDev ns,
                                const float* buf0, const float* buf1, double* D,
                                double* trpart, int nb_max, cudaStream_t st);
+// the same from one buffer S (finite temperature: S = p(X), the polynomial
+// for tanh), with sqpart[j] = sum over the block's columns c of (D_j^2)_cc
+template <typename T>
+cudaError_t launch_scatter_sq(const PatternDev& g, const WaveDev& w, NsStateDev ns, const T* S, double* D,
+                              double* trpart, double* sqpart, int nb_max, cudaStream_t st);
 cudaError_t launch_trace(const PatternDev& g, int nblk, const double* D, double* part,
                          double* out, cudaStream_t st);
 cudaError_t launch_symmetrize_impl(const PatternDev& g, int64_t nnzb, const double* Din,
@@ -150,6 +155,9 @@ struct CertLimits {
   double fcap;     // X_0 = f a / beta_bound with f <= fcap is safe without it
 };
 CertLimits cert_limits(bool third_order);
+// the row-sum pass alone: ns.cert[s] = bits of the largest row abs-sum of X^2
+// (ns.cert must be zero beforehand; submatrices not ACTIVE are skipped)
+cudaError_t launch_cert_rowsum(const WaveDev& w, NsStateDev ns, CertSquare sq, int max_ld, cudaStream_t st);
 cudaError_t launch_certify(const WaveDev& w, NsStateDev ns, CertSquare sq, CertLinear lin, CertLimits lim,
                            int max_ld, int* count, cudaStream_t st);
 

@@ -218,3 +218,28 @@ extern "C" submat_status submat_debug_mu_bisect(const double* levels, int nlev, 
   if (n_out) *n_out = count(r.mu);
   return s;
 }
+
+extern "C" submat_status submat_debug_fermi_poly(double c, double tol, int max_degree, double* r_out, int cap,
+                                                 int32_t* degree, int32_t* blocks, double* trunc) {
+  using namespace submat;
+  clear_error();
+  if (!degree || !blocks || !trunc || cap < 0 || max_degree < 1 || max_degree > kFermiMaxDegree ||
+      !(tol > 0)) {
+    set_error("bad argument to submat_debug_fermi_poly");
+    return SUBMAT_ERR_INVALID_ARG;
+  }
+  FermiPoly P;
+  SM_TRY(fermi_poly(c, tol, max_degree, &P));
+  *degree = P.m;
+  *blocks = P.blocks;
+  *trunc = P.trunc;
+  const int n = int(P.r.size());
+  if (r_out) {
+    if (cap < n) {
+      set_error("submat_debug_fermi_poly: %d coefficients, room for %d", n, cap);
+      return SUBMAT_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n; ++i) r_out[i] = P.r[i];
+  }
+  return SUBMAT_OK;
+}

@@ -116,6 +116,71 @@ submat_status mu_bisect(const std::function<submat_status(double, double*)>& eva
   return SUBMAT_ERR_NOT_CONVERGED;
 }
 
+// Finite temperature: N(mu) = Tr f(K - mu I) is smooth and strictly
+// increasing, and every evaluation also returns dN/dmu (the adjoint's
+// -sum L_f(a_j, I)_cc, from the same build), so the search takes Newton steps
+// inside a bracket and bisects when a step would leave it or does not halve
+// the error fast enough (the safeguard of rtsafe).  The bracket is
+// [mu0, mu0 + s] or [mu0 - s, mu0] on the side of n_el, s = 1.01 b + 40 kT with
+// b the rigorous spectral bound at mu0: beyond every eigenvalue by 40 kT the
+// Fermi tails are below e^-40.
+submat_status Plan::mu_newton(const double* K, double n_el, double mu0, double tol, int max_steps,
+                              double* mu_out, double* D, cudaStream_t st) {
+  int steps = 0;
+  submat_status last = SUBMAT_OK;
+  auto eval = [&](double mu, double* n, double* dn) -> submat_status {
+    last = sign(K, mu, D, st);
+    if (last != SUBMAT_OK) return last;
+    SM_TRY(trace(D, n, st));
+    *dn = stats.dn_dmu;
+    ++steps;
+    return SUBMAT_OK;
+  };
+  auto done = [&](double nv) { return std::fabs(nv - n_el) <= tol * std::fabs(n_el); };
+  double mu = mu0, n = 0, dn = 0;
+  submat_status s = eval(mu, &n, &dn);
+  double best_mu = mu, best_n = n;
+  if (s == SUBMAT_OK && !done(n)) {
+    double bmax = 0;
+    for (int j = col_lo; j < col_hi; ++j) bmax = std::max(bmax, res_bound[j]);
+    const double span = 1.01 * bmax + 40.0 * opt.kT;
+    double lo = n < n_el ? mu0 : mu0 - span, hi = n < n_el ? mu0 + span : mu0;
+    double dx_old = hi - lo, dx = dx_old;
+    s = SUBMAT_ERR_NOT_CONVERGED;
+    while (steps < max_steps) {
+      const double f = n - n_el;
+      // Newton from mu, unless it leaves (lo, hi) or the error shrinks too slowly
+      const bool out = !((mu - hi) * dn - f < 0.0 && (mu - lo) * dn - f > 0.0);
+      if (!(dn > 0.0) || out || std::fabs(2.0 * f) > std::fabs(dx_old * dn)) {
+        dx_old = dx;
+        dx = 0.5 * (hi - lo);
+        mu = lo + dx;
+      } else {
+        dx_old = dx;
+        dx = f / dn;
+        mu -= dx;
+      }
+      SM_TRY(eval(mu, &n, &dn));
+      if (std::fabs(n - n_el) <= std::fabs(best_n - n_el)) { best_mu = mu; best_n = n; }
+      if (done(n)) { s = SUBMAT_OK; break; }
+      if (n < n_el) lo = mu; else hi = mu;
+      if (hi - lo <= 1e-15 * std::max(std::fabs(mu), bmax)) break;  // at the rounding floor
+    }
+    if (s != SUBMAT_OK) {
+      if (mu != best_mu) {
+        double nb = 0, db = 0;
+        SM_TRY(eval(best_mu, &nb, &db));
+      }
+      mu = best_mu;
+      set_error("mu search (finite temperature) used %d evaluations without meeting tol (N = %.17g "
+                "at mu = %.17g)", steps, best_n, best_mu);
+    }
+  }
+  stats.mu_steps = steps;
+  if (s == SUBMAT_OK || s == SUBMAT_ERR_NOT_CONVERGED) *mu_out = mu;
+  return s;
+}
+
 submat_status Plan::mu_search(const double* K, double n_el, double mu0, double tol, int max_steps,
                               double* mu_out, double* D, cudaStream_t st) {
   double n_total = 0.0;
@@ -124,6 +189,7 @@ submat_status Plan::mu_search(const double* K, double n_el, double mu0, double t
     set_error("n_el = %.17g outside [0, %.17g] (the matrix dimension)", n_el, n_total);
     return SUBMAT_ERR_INVALID_ARG;
   }
+  if (opt.kT > 0.0) return mu_newton(K, n_el, mu0, tol, max_steps, mu_out, D, st);
   // status of the latest evaluation: a submatrix that did not converge there
   // leaves D (and the trace) unfinished; one that diverged ends the search
   submat_status last = SUBMAT_OK;

@@ -206,9 +206,10 @@ __global__ void __launch_bounds__(256) k_scatter(PatternDev g, WaveDev w, NsStat
                                                  double* __restrict__ D, double* trpart,
                                                  const float* __restrict__ corr_a,
                                                  const float* __restrict__ corr_b,
-                                                 const int* __restrict__ fallback) {
+                                                 const int* __restrict__ fallback,
+                                                 double* __restrict__ sqpart) {
   extern __shared__ int sm[];
-  __shared__ double red[8];
+  __shared__ double red[8], red2[8];
   const int s = blockIdx.x;
   const int j = w.sub[s];
   const int64_t rp0 = g.row_ptr[j];
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(256) k_scatter(PatternDev g, WaveDev w, NsStat
   const float* cb = corr_b ? corr_b + w.off[s] : nullptr;
   const int koff = g.koff[j];
   const int bj = g.bs[j];
-  double tr = 0.0;
+  double tr = 0.0, sq = 0.0;
   const int64_t total = int64_t(bj) * n;
   for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
     const int c = int(e / n);
@@ -245,14 +246,21 @@ __global__ void __launch_bounds__(256) k_scatter(PatternDev g, WaveDev w, NsStat
     const double v = (diag ? 0.5 : 0.0) - 0.5 * sv;
     D[g.valptr[p] + int64_t(r) * bj + c] = v;
     if (diag) tr += v;
+    if (sqpart) sq = fma(v, v, sq);
   }
   tr = warp_sum(tr);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tr;
+  if (sqpart) {
+    sq = warp_sum(sq);
+    if ((threadIdx.x & 31) == 0) red2[threadIdx.x >> 5] = sq;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double acc = 0.0;
-    for (int q = 0; q < int(blockDim.x >> 5); ++q) acc += red[q];
+    double acc = 0.0, acc2 = 0.0;
+    for (int q = 0; q < int(blockDim.x >> 5); ++q) { acc += red[q]; acc2 += red2[q]; }
     trpart[j] = acc;
+    // sum over the block's columns c of (D^2)_cc = sum_k D_kc^2 (D_j symmetric)
+    if (sqpart) sqpart[j] = acc2;
   }
 }
 
@@ -511,14 +519,15 @@ template <typename T>
 static cudaError_t scatter_impl(const PatternDev& g, const WaveDev& w, NsStateDev ns,
                                 const T* buf0, const T* buf1, double* D, double* trpart,
                                 int nb_max, cudaStream_t st, const float* corr_a = nullptr,
-                                const float* corr_b = nullptr, const int* fallback = nullptr) {
+                                const float* corr_b = nullptr, const int* fallback = nullptr,
+                                double* sqpart = nullptr) {
   const size_t smem = size_t(nb_max + 1) * sizeof(int);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_scatter<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
   }
-  k_scatter<T><<<w.nsub, 256, smem, st>>>(g, w, ns, buf0, buf1, D, trpart, corr_a, corr_b, fallback);
+  k_scatter<T><<<w.nsub, 256, smem, st>>>(g, w, ns, buf0, buf1, D, trpart, corr_a, corr_b, fallback, sqpart);
   count_launch();
   return cudaGetLastError();
 }
@@ -535,6 +544,16 @@ cudaError_t launch_scatter_f32(const PatternDev& g, const WaveDev& w, NsStateDev
                                double* trpart, int nb_max, cudaStream_t st) {
   return scatter_impl<float>(g, w, ns, buf0, buf1, D, trpart, nb_max, st);
 }
+
+template <typename T>
+cudaError_t launch_scatter_sq(const PatternDev& g, const WaveDev& w, NsStateDev ns, const T* S, double* D,
+                              double* trpart, double* sqpart, int nb_max, cudaStream_t st) {
+  return scatter_impl<T>(g, w, ns, S, S, D, trpart, nb_max, st, nullptr, nullptr, nullptr, sqpart);
+}
+template cudaError_t launch_scatter_sq<double>(const PatternDev&, const WaveDev&, NsStateDev, const double*,
+                                               double*, double*, double*, int, cudaStream_t);
+template cudaError_t launch_scatter_sq<float>(const PatternDev&, const WaveDev&, NsStateDev, const float*,
+                                              double*, double*, double*, int, cudaStream_t);
 
 cudaError_t launch_trace(const PatternDev& g, int nblk, const double* D, double* part,
                          double* out, cudaStream_t st) {

@@ -58,7 +58,8 @@ Plan::~Plan() {
 }
 
 // bytes of workspace per dense element for each precision
-static size_t bytes_per_elem(int prec) {
+static size_t bytes_per_elem(int prec, double kT) {
+  if (kT > 0.0) return fermi_bytes_per_elem(prec);
   switch (prec) {
     case SUBMAT_FP64: return 3 * 8;                 // X ping-pong + X^2
     case SUBMAT_FP32: return 8 + 3 * 4;             // A (FP64) + X ping-pong + X^2
@@ -352,7 +353,7 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
     g = PatternDev{d_bs, d_rp, d_col, d_vp, d_loc, d_tp, d_ns, d_ko, d_dp};
   }
   // waves
-  const size_t bpe = bytes_per_elem(opt.prec);
+  const size_t bpe = bytes_per_elem(opt.prec, opt.kT);
   size_t cap = opt.workspace_cap_bytes;
   if (cap == 0) {
     size_t fre = 0, tot = 0;
@@ -382,6 +383,7 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
   SM_TRY(alloc(&d_flags, 4, "flags"));
   SM_TRY(alloc(&d_active, 1, "active count"));
   SM_TRY(alloc(&d_trpart, size_t(nblk), "trace partials"));
+  if (opt.kT > 0.0) SM_TRY(alloc(&d_sqpart, size_t(nblk), "sum-of-squares partials"));
   SM_TRY(alloc(&d_scalar, 8, "scalars"));
   SM_CUDA(cudaMallocHost(&h_pinned, 64));
   for (auto& e : ev) SM_CUDA(cudaEventCreate(&e));
@@ -644,7 +646,8 @@ void Plan::finish_stats(bool adjoint) {
     imax = std::max(imax, res_iters[j]);
     nc += res_notconv[j];
     const double n3 = double(nsub[j]) * nsub[j] * nsub[j];
-    flops += adjoint ? 12.0 * n3 * (res_iters[j] + 2) : (opt.iteration == 1 ? 6.0 : 4.0) * n3 * res_iters[j];
+    if (opt.kT > 0.0 && !adjoint) flops += 2.0 * n3 * res_iters[j];  // res_iters: products
+    else flops += adjoint ? 12.0 * n3 * (res_iters[j] + 2) : (opt.iteration == 1 ? 6.0 : 4.0) * n3 * res_iters[j];
     rmax = std::max(rmax, res_resid[j]);
   }
   stats.iters_min = imin == INT32_MAX ? 0 : imin;
@@ -657,6 +660,8 @@ void Plan::finish_stats(bool adjoint) {
     timer.collect(stats.kernel_ms, stats.kernel_launches);
     if (adjoint) {  // every adjoint product runs on one GEMM kind
       stats.kernel_work[opt.adjoint_mode == 1 ? KC_TC_ADJ : KC_SIMT] += flops;
+    } else if (opt.kT > 0.0) {
+      stats.kernel_work[KC_SIMT] += flops;
     } else if (opt.prec != SUBMAT_MIXED_BF16_REFINE) {
       // two products per iteration, 2 n^3 flops each at the standard count
       for (int j = col_lo; j < col_hi; ++j) {
@@ -711,7 +716,12 @@ submat_status Plan::sign(const double* K, double mu, double* D, cudaStream_t st)
     if (!d_symtmp) SM_TRY(alloc(&d_symtmp, size_t(nvals), "symmetrize buffer"));
     Dout = d_symtmp;
   }
-  switch (opt.prec) {
+  fermi_degree = 0;
+  fermi_trunc = fermi_flops = 0.0;
+  if (opt.kT > 0.0) {
+    if (opt.prec == SUBMAT_FP64) SM_TRY(sign_fermi<double>(K, mu, Dout, st));
+    else SM_TRY(sign_fermi<float>(K, mu, Dout, st));
+  } else switch (opt.prec) {
     case SUBMAT_FP64: SM_TRY(sign_fp64(K, mu, Dout, st)); break;
     case SUBMAT_FP32: SM_TRY(sign_fp32(K, mu, Dout, st)); break;
     case SUBMAT_MIXED_BF16_REFINE: SM_TRY(sign_mixed(K, mu, Dout, st)); break;
@@ -720,6 +730,11 @@ submat_status Plan::sign(const double* K, double mu, double* D, cudaStream_t st)
   if (opt.symmetrize) SM_CUDA(launch_symmetrize_impl(g, nnzb, d_symtmp, D, d_rowof, st));
   SM_CUDA(cudaStreamSynchronize(st));
   finish_stats();
+  if (opt.kT > 0.0) {
+    stats.poly_degree = fermi_degree;
+    stats.poly_trunc = fermi_trunc;
+    SM_TRY(fermi_dn_dmu(st, &stats.dn_dmu));
+  }
   int fl = 0;
   SM_TRY(read_flags(st, &fl));
   if (fl & FLAG_TIMEOUT) { set_error("a bounded device wait timed out"); return SUBMAT_ERR_TIMEOUT; }
@@ -815,6 +830,14 @@ submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int
     if (o.col_begin < 0 || o.col_end < 0 || o.col_end > nblk || (o.col_end > 0 && o.col_begin >= o.col_end)) {
       submat::set_error("bad column range [%d, %d) for %d block columns", o.col_begin, o.col_end, nblk);
       return SUBMAT_ERR_INVALID_ARG;
+    }
+    if (!(o.kT >= 0.0) || !std::isfinite(o.kT)) {
+      submat::set_error("kT must be finite and >= 0");
+      return SUBMAT_ERR_INVALID_ARG;
+    }
+    if (o.kT > 0.0 && o.prec == SUBMAT_MIXED_BF16_REFINE) {
+      submat::set_error("finite temperature runs on the FP64 and FP32 paths only");
+      return SUBMAT_ERR_UNSUPPORTED;
     }
     if (o.max_iter == 0) o.max_iter = 100;
     if (o.refine_rounds == 0) o.refine_rounds = 1;

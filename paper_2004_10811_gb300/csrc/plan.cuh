@@ -46,6 +46,20 @@ submat_status mu_bisect(const std::function<submat_status(double, double*)>& eva
                         int max_steps, MuSearchOut* out);
 
 
+// Finite temperature (fermi.cu): the Chebyshev series of tanh(c x) on
+// [-1, 1] cut at odd degree m, folded for 16 baby steps: p = sum_j R_j T_j(Y),
+// Y = T_16, R_j = sum_{q < 8} r[j * 8 + q] T_{2q+1}.
+constexpr int kFermiBaby = 16;
+constexpr int kFermiBuffers = kFermiBaby / 2 + 3;  // odd T_k, T_2 / Y, two Clenshaw buffers
+constexpr int kFermiMaxDegree = 8191;
+struct FermiPoly {
+  int m = 0, blocks = 0;
+  double trunc = 0.0;  // sum of |c_k| beyond m: bounds the truncation error on [-1, 1]
+  std::vector<double> r;
+};
+submat_status fermi_poly(double c, double tol, int max_degree, FermiPoly* out);
+size_t fermi_bytes_per_elem(int prec);
+
 struct Wave {
   int first = 0;           // first global block column of the wave
   int count = 0;           // submatrices in the wave
@@ -146,6 +160,11 @@ struct Plan {
   int64_t bws_elems = 0;
   double* d_dnpart = nullptr;
   double dn_acc = 0.0;
+  // finite temperature: per block column sum of squares of the extracted
+  // columns, and the last evaluation's polynomial
+  double* d_sqpart = nullptr;
+  int fermi_degree = 0;
+  double fermi_trunc = 0.0, fermi_flops = 0.0;
 
   // results of the last evaluation (per global block column)
   std::vector<int> res_iters, res_notconv;
@@ -186,6 +205,13 @@ struct Plan {
   submat_status sign_fp64(const double* K, double mu, double* D, cudaStream_t st);
   submat_status sign_fp32(const double* K, double mu, double* D, cudaStream_t st);
   submat_status sign_mixed(const double* K, double mu, double* D, cudaStream_t st);
+  template <typename T>
+  submat_status sign_fermi(const double* K, double mu, double* D, cudaStream_t st);
+  submat_status fermi_dn_dmu(cudaStream_t st, double* out);
+  submat_status backward_fermi(const double* K, double mu, const double* Dbar, double* Kbar, double* dN_dmu,
+                               cudaStream_t st);
+  submat_status mu_newton(const double* K, double n_el, double mu0, double tol, int max_steps,
+                          double* mu_out, double* D, cudaStream_t st);
   submat_status build_waves(size_t bpe, size_t cap, std::vector<Wave>& out, cudaStream_t st);
   template <typename T>
   submat_status backward_wave(Wave& wv, const double* K, double mu, const double* Dbar, double* Kbar,

@@ -29,7 +29,7 @@ EXPORTS = (
     "submat_sign_host", "submat_trace", "submat_mu_search", "submat_sign_backward",
     "submat_plan_value_count", "submat_get_stats", "submat_get_sub_stats", "submat_last_error",
     "submat_debug_tc_gemm", "submat_dense_sign_noalloc", "submat_autotune", "submat_debug_slice_plan",
-    "submat_debug_mu_bisect",
+    "submat_debug_mu_bisect", "submat_debug_fermi_poly",
 )
 
 
@@ -50,7 +50,7 @@ class Options(C.Structure):
         ("symmetrize", C.c_int), ("workspace_cap_bytes", C.c_size_t),
         ("refine_rounds", C.c_int), ("timing", C.c_int), ("col_begin", C.c_int), ("col_end", C.c_int),
         ("hp_mode", C.c_int), ("tile_n_ns", C.c_int), ("tile_n_corr", C.c_int), ("tile_n_hp", C.c_int),
-        ("iteration", C.c_int), ("adjoint_mode", C.c_int),
+        ("iteration", C.c_int), ("adjoint_mode", C.c_int), ("kT", C.c_double),
     ]
 
 
@@ -65,6 +65,7 @@ class Stats(C.Structure):
         ("ms_scatter", C.c_double), ("workspace_bytes", C.c_size_t), ("launches", C.c_int64),
         ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_int32 * 8), ("kernel_work", C.c_double * 8),
         ("kernel_exec", C.c_double * 8), ("mu_steps", C.c_int32), ("scale_reduced", C.c_int32),
+        ("poly_degree", C.c_int32), ("poly_trunc", C.c_double), ("dn_dmu", C.c_double),
     ]
 
     def as_dict(self):
@@ -110,12 +111,14 @@ def load(path: str = LIB_PATH):
     lib.submat_debug_mu_bisect.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
                                            C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int32),
                                            C.POINTER(C.c_double)]
+    lib.submat_debug_fermi_poly.argtypes = [C.c_double, C.c_double, C.c_int, vp, C.c_int,
+                                            C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)]
     lib.submat_last_error.argtypes = []
     lib.submat_last_error.restype = C.c_char_p
     for name in ("submat_plan_create", "submat_plan_destroy", "submat_sign", "submat_sign_host",
                  "submat_trace", "submat_mu_search", "submat_sign_backward", "submat_get_stats",
                  "submat_get_sub_stats", "submat_debug_tc_gemm", "submat_dense_sign_noalloc",
-                 "submat_debug_slice_plan", "submat_debug_mu_bisect"):
+                 "submat_debug_slice_plan", "submat_debug_mu_bisect", "submat_debug_fermi_poly"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -158,7 +161,7 @@ class Plan:
     def __init__(self, block_sizes, row_ptr, col_idx, prec="fp64", tol=0.0, max_iter=0,
                  beta_mode=0, symmetrize=False, workspace_cap_bytes=0, refine_rounds=0,
                  timing=False, columns=None, hp_mode=0, tile_n_ns=0, tile_n_corr=0, tile_n_hp=0,
-                 iteration=0, adjoint_mode=0, stream=None):
+                 iteration=0, adjoint_mode=0, kT=0.0, stream=None):
         lib = load()
         self._lib = lib
         self.block_sizes = np.ascontiguousarray(block_sizes, dtype=np.int32)
@@ -180,6 +183,7 @@ class Plan:
         opt.tile_n_hp = int(tile_n_hp)
         opt.iteration = int(iteration)
         opt.adjoint_mode = int(adjoint_mode)
+        opt.kT = float(kT)
         if columns is not None:
             opt.col_begin, opt.col_end = int(columns[0]), int(columns[1])
         self.options = opt
@@ -373,3 +377,17 @@ def dense_sign_noalloc(K, mu, out=None, stream=None):
     _check(lib.submat_dense_sign_noalloc(n, _devptr(K, "K"), float(mu), _devptr(out, "D"),
                                          C.byref(it), _stream(stream)))
     return out, it.value
+
+
+def debug_fermi_poly(c, tol=1e-13, max_degree=8191):
+    """Host-only test hook (include/submat_debug.h): the finite-temperature
+    polynomial for tanh(c x) on [-1, 1].  Returns (r [blocks, 8], degree,
+    truncation bound): p(x) = sum_j (sum_q r[j, q] T_{2q+1}(x)) T_j(T_16(x))."""
+    lib = load()
+    m, blocks, trunc = C.c_int32(), C.c_int32(), C.c_double()
+    _check(lib.submat_debug_fermi_poly(float(c), float(tol), int(max_degree), None, 0, C.byref(m),
+                                       C.byref(blocks), C.byref(trunc)))
+    r = np.zeros(8 * blocks.value, dtype=np.float64)
+    _check(lib.submat_debug_fermi_poly(float(c), float(tol), int(max_degree), r.ctypes.data_as(C.c_void_p),
+                                       len(r), C.byref(m), C.byref(blocks), C.byref(trunc)))
+    return r.reshape(blocks.value, 8), m.value, trunc.value
