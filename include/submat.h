@@ -124,7 +124,8 @@ typedef struct {
                                   plan's precision; mixed plans return UNSUPPORTED.  The
                                   series degree grows like (spectral scale) / kT: a degree
                                   above 8191 returns UNSUPPORTED.  submat_mu_search then takes
-                                  Newton steps on the smooth Tr D(mu) (submat_stats.dn_dmu) */
+                                  Newton steps on the smooth Tr D(mu) (submat_stats.dn_dmu),
+                                  and submat_sign_backward differentiates the same series */
 } submat_options;
 
 /* Aggregate statistics of the last submat_sign / submat_mu_search call. */
@@ -272,6 +273,12 @@ submat_status submat_mu_search(submat_plan* plan, const double* K_vals, double n
  * plans), or with options.adjoint_mode = 1 as BF16x3 split products on the
  * tensor cores, E's transpose kept beside it for the products that read E as
  * their right operand.
+ * Finite temperature (options.kT > 0, D = f(K - mu I) with the Fermi
+ * function): abar_j = L_f(a_j, G_j), from the Chebyshev evaluation of D run
+ * on dual numbers (every matrix M with a derivative part M',
+ * (AB)' = A'B + AB', seeded with G_j / sigma), three products for every one
+ * of the forward; dN/dmu = sum_j sum_{c in block j} [f(a_j)(1 - f(a_j))]_cc / kT
+ * from the same pass.
  */
 submat_status submat_sign_backward(submat_plan* plan, const double* K_vals, double mu,
                                    const double* Dbar_vals, double* Kbar_vals,

@@ -138,27 +138,50 @@ struct GemmFor<float> {
 
 }  // namespace
 
+template <typename T>
+cudaError_t launch_bwd_seed(const PatternDev& g, const Wave& wv, const double* Dbar, const double* beta, T* E,
+                            int identity, cudaStream_t st) {
+  k_bwd_seed<T><<<wv.n_gather, dim3(32, 8), 0, st>>>(g, wv.dev, wv.gather_items, Dbar, beta, E, identity);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_bwd_seed<double>(const PatternDev&, const Wave&, const double*, const double*,
+                                             double*, int, cudaStream_t);
+template cudaError_t launch_bwd_seed<float>(const PatternDev&, const Wave&, const double*, const double*,
+                                            float*, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_bwd_scatter_add(const PatternDev& g, const Wave& wv, int nb_max, const T* E, double* Kbar,
+                                   cudaStream_t st) {
+  const size_t smem = size_t(3 * nb_max + 1) * sizeof(int);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_bwd_scatter_add<T>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  k_bwd_scatter_add<T><<<wv.n_gather, 256, smem, st>>>(g, wv.dev, wv.gather_items, E, Kbar);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_bwd_scatter_add<double>(const PatternDev&, const Wave&, int, const double*, double*,
+                                                    cudaStream_t);
+template cudaError_t launch_bwd_scatter_add<float>(const PatternDev&, const Wave&, int, const float*, double*,
+                                                   cudaStream_t);
+
 cudaError_t launch_bwd_seed_f32(const PatternDev& g, const Wave& wv, const double* Dbar, const double* beta,
                                 float* E, int identity, cudaStream_t st) {
-  k_bwd_seed<float><<<wv.n_gather, dim3(32, 8), 0, st>>>(g, wv.dev, wv.gather_items, Dbar, beta, E, identity);
-  return cudaGetLastError();
+  return launch_bwd_seed<float>(g, wv, Dbar, beta, E, identity, st);
 }
 
 cudaError_t launch_bwd_scatter_add_f32(const PatternDev& g, const Wave& wv, int nb_max, const float* E,
                                        double* Kbar, cudaStream_t st) {
-  const size_t smem = size_t(3 * nb_max + 1) * sizeof(int);
-  if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(k_bwd_scatter_add<float>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-  }
-  k_bwd_scatter_add<float><<<wv.n_gather, 256, smem, st>>>(g, wv.dev, wv.gather_items, E, Kbar);
-  return cudaGetLastError();
+  return launch_bwd_scatter_add<float>(g, wv, nb_max, E, Kbar, st);
 }
 
 cudaError_t launch_bwd_dn_f32(const PatternDev& g, const Wave& wv, const float* E, double* part,
                               cudaStream_t st) {
   k_bwd_dn<float><<<(wv.count + 255) / 256, 256, 0, st>>>(g, wv.dev, E, part);
+  count_launch();
   return cudaGetLastError();
 }
 

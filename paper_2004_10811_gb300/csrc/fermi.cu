@@ -140,10 +140,25 @@ __global__ void k_fermi_rescale(WaveDev w, T* __restrict__ X, T* __restrict__ T2
        e += int64_t(gridDim.x) * blockDim.x) {
     const int row = int(e / ld), col = int(e - int64_t(row) * ld);
     X[base + e] *= rt;
+    if (!T2) continue;
     T v = r2 * T2[base + e];
     if (row == col && row < n) v += dshift;
     T2[base + e] = v;
   }
+}
+
+// M <- r_s^2 M (the derivative part of the rescaled square)
+template <typename T>
+__global__ void k_fermi_scale_sq(WaveDev w, T* __restrict__ M, const double* __restrict__ ratio) {
+  const int s = blockIdx.y;
+  const double r = ratio[s];
+  if (r == 1.0) return;
+  const int ld = w.ld[s];
+  const int64_t total = int64_t(ld) * ld, base = w.off[s];
+  const T r2 = T(r * r);
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x)
+    M[base + e] *= r2;
 }
 
 // W = sum_i r_i T_{2i+1} - B (B may be null): the giant-step coefficient R_j
@@ -196,127 +211,172 @@ size_t fermi_bytes_per_elem(int prec) {
   return 8 + size_t(kFermiBuffers) * (prec == SUBMAT_FP64 ? 8 : 4);
 }
 
+// The adjoint runs the same buffers twice: values and derivative parts.
+size_t fermi_dual_bytes_per_elem(int prec) {
+  return 8 + size_t(2 * kFermiBuffers) * (prec == SUBMAT_FP64 ? 8 : 4);
+}
+
+// One wave.  Forward: D = (I - p(X)) / 2 on the extracted columns, with the
+// trace and sum-of-squares partials for dN/dmu.  With Dbar (the adjoint):
+// every matrix M of the evaluation carries a derivative part M' (dual
+// numbers), (A B)' = A' B + A B', seeded with X' = G_j / sigma, G_j holding
+// Dbar's block column j in the columns of block j; then p' = L_p(X, X') and
+// L_f(a_j, G_j) = -1/2 p' is added into every stored block of Kbar that a_j
+// came from (L_f(a, .) is self-adjoint in the Frobenius product for
+// symmetric a).  The value part is evaluated exactly as in the forward path.
 template <typename T>
-submat_status Plan::sign_fermi(const double* K, double mu, double* D, cudaStream_t st) {
+submat_status Plan::fermi_wave(Wave& wv, const double* K, double mu, double* D, const double* Dbar, double* Kbar,
+                               void* w, int64_t E, cudaStream_t st) {
   using G = FermiGemm<T>;
   using Args = typename G::Args;
   constexpr int S = kFermiBaby;
-  const int64_t E = ws_elems;
-  double* A = static_cast<double*>(ws);
+  const bool dual = Dbar != nullptr;
+  double* A = static_cast<double*>(w);
   T* base = reinterpret_cast<T*>(A + E);
   T* odd = base;                  // T_1 = X, T_3, ..., T_15 at odd + q E
   T* T2 = base + (S / 2) * E;     // T_2, later Y = T_16
   T* bb[2] = {T2 + E, T2 + 2 * E};    // Clenshaw b_{j+1}, b_{j+2}
+  // derivative parts, the same layout kFermiBuffers buffers further on
+  const int64_t dofs = int64_t(kFermiBuffers) * E;
+  auto dp = [&](const T* v) -> T* { return v ? const_cast<T*>(v) + dofs : nullptr; };
   const bool f64 = sizeof(T) == 8;
   // truncation tolerance of the series: below the products' own rounding
   const double tol_poly = f64 ? 1e-13 : 1e-8;
-  double fl_total = 0.0;
-  for (auto& wv : waves) {
-    SM_CUDA(cudaEventRecord(ev[0], st));
-    SM_TRY(gather_wave(wv, K, mu, A, st));
-    SM_CUDA(G::scale(wv.dev, A, odd, ns.beta, wv.max_ld2, st));
-    SM_CUDA(cudaEventRecord(ev[1], st));
-    int products = 0;
-    auto gemm = [&](const T* Aop, const T* Bop, const T* C0, T* C, double alpha, double beta,
-                    double diag) -> submat_status {
-      Args a{};
-      a.w = wv.dev; a.items = wv.sym64; a.nitems = wv.n_sym64;
-      a.A = Aop; a.B = Bop; a.C0 = C0; a.C = C;
-      a.alpha = alpha; a.beta = beta; a.diag = diag; a.sym = 1;
-      a.res2 = nullptr; a.state = nullptr; a.skip_state = -1;
-      size_t tk;
-      SM_TRY(timer.start(KC_SIMT, st, &tk));
-      SM_CUDA(G::run(a, st));
-      SM_TRY(timer.stop(tk, st));
-      ++products;
-      return SUBMAT_OK;
-    };
-    // T_2 = 2 X^2 - I at X = a / beta_bound, and from it the tight scale
-    SM_TRY(gemm(odd, odd, nullptr, T2, 2.0, 0.0, -1.0));
-    const CertSquare sq{f64 ? 0 : 1, T2, nullptr, 2.0f, -1.0f};
-    SM_CUDA(cudaMemsetAsync(ns.cert, 0, sizeof(unsigned long long) * wv.count, st));
-    SM_CUDA(launch_cert_rowsum(wv.dev, ns, sq, max_ld(wv), st));
-    std::vector<unsigned long long> cert(wv.count), gersh(wv.count);
-    std::vector<double> fro2(wv.count), beta(wv.count), ratio(wv.count, 1.0);
-    SM_CUDA(cudaMemcpyAsync(cert.data(), ns.cert, 8 * wv.count, cudaMemcpyDeviceToHost, st));
-    SM_CUDA(cudaMemcpyAsync(gersh.data(), ns.gersh, 8 * wv.count, cudaMemcpyDeviceToHost, st));
-    SM_CUDA(cudaMemcpyAsync(fro2.data(), ns.fro2, 8 * wv.count, cudaMemcpyDeviceToHost, st));
-    SM_CUDA(cudaMemcpyAsync(beta.data(), ns.beta, 8 * wv.count, cudaMemcpyDeviceToHost, st));
-    SM_CUDA(cudaStreamSynchronize(st));
-    double sigma = 0.0;
-    std::vector<double> bound(wv.count, 0.0);
-    const double eps0 = f64 ? 0x1p-50 : 0x1p-22, eps_ld = f64 ? 0x1p-52 : 0x1p-23;
-    for (int s = 0; s < wv.count; ++s) {
-      double cv = 0.0, gv = 0.0;
-      std::memcpy(&cv, &cert[s], 8);
-      std::memcpy(&gv, &gersh[s], 8);
-      const double bnd = std::min(gv, std::sqrt(fro2[s])) * (1.0 + 1e-4);
-      if (!(bnd > 0.0)) continue;  // a zero submatrix: f(0) = 1/2 whatever the scale
-      const int ld = wv.host_ld[s];
-      const double gx = gv / bnd;
-      const double Gs = cv * (1.0 + ld * 0x1p-24) + (eps0 + eps_ld * ld) * gx * gx;
-      bound[s] = beta[s] * std::min(1.0, std::sqrt(Gs));
-      sigma = std::max(sigma, bound[s]);
+  SM_CUDA(cudaEventRecord(ev[0], st));
+  SM_TRY(gather_wave(wv, K, mu, A, st));
+  SM_CUDA(G::scale(wv.dev, A, odd, ns.beta, wv.max_ld2, st));
+  if (dual) SM_CUDA(launch_bwd_seed<T>(g, wv, Dbar, ns.beta, dp(odd), 0, st));  // X' = G / beta
+  SM_CUDA(cudaEventRecord(ev[1], st));
+  int products = 0;
+  auto gemm1 = [&](const Args& a) -> submat_status {
+    size_t tk;
+    SM_TRY(timer.start(KC_SIMT, st, &tk));
+    SM_CUDA(G::run(a, st));
+    SM_TRY(timer.stop(tk, st));
+    return SUBMAT_OK;
+  };
+  // C = alpha A B + beta C0 + diag I (symmetric: A, B commute), and with
+  // dual numbers C' = alpha (A' B + A B') + beta C0' (full tiles)
+  auto gemm = [&](const T* Aop, const T* Bop, const T* C0, T* C, double alpha, double beta,
+                  double diag) -> submat_status {
+    Args a{};
+    a.w = wv.dev; a.items = wv.sym64; a.nitems = wv.n_sym64;
+    a.A = Aop; a.B = Bop; a.C0 = C0; a.C = C;
+    a.alpha = alpha; a.beta = beta; a.diag = diag; a.sym = 1;
+    a.res2 = nullptr; a.state = nullptr; a.skip_state = -1;
+    if (dual) {  // derivative first: it reads the values of A, B (and C0 may alias C)
+      Args d = a;
+      d.items = wv.full64; d.nitems = wv.n_full64; d.sym = 0; d.diag = 0.0;
+      d.A = dp(Aop); d.B = Bop; d.C0 = dp(C0); d.C = dp(C);
+      SM_TRY(gemm1(d));
+      d.A = Aop; d.B = dp(Bop); d.C0 = dp(C); d.beta = 1.0;
+      SM_TRY(gemm1(d));
     }
-    sigma *= 1.0 + 1e-6;
-    if (!(sigma > 0.0)) sigma = 1.0;
-    for (int s = 0; s < wv.count; ++s)
-      if (bound[s] > 0.0) ratio[s] = beta[s] / sigma;
-    SM_CUDA(cudaMemcpyAsync(ns.cscale, ratio.data(), 8 * wv.count, cudaMemcpyHostToDevice, st));
-    k_fermi_rescale<T><<<fermi_grid(wv), 256, 0, st>>>(wv.dev, odd, T2, ns.cscale);
+    SM_TRY(gemm1(a));
+    ++products;
+    return SUBMAT_OK;
+  };
+  // T_2 = 2 X^2 - I at X = a / beta_bound, and from it the tight scale
+  SM_TRY(gemm(odd, odd, nullptr, T2, 2.0, 0.0, -1.0));
+  const CertSquare sq{f64 ? 0 : 1, T2, nullptr, 2.0f, -1.0f};
+  SM_CUDA(cudaMemsetAsync(ns.cert, 0, sizeof(unsigned long long) * wv.count, st));
+  SM_CUDA(launch_cert_rowsum(wv.dev, ns, sq, max_ld(wv), st));
+  std::vector<unsigned long long> cert(wv.count), gersh(wv.count);
+  std::vector<double> fro2(wv.count), beta(wv.count), ratio(wv.count, 1.0);
+  SM_CUDA(cudaMemcpyAsync(cert.data(), ns.cert, 8 * wv.count, cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaMemcpyAsync(gersh.data(), ns.gersh, 8 * wv.count, cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaMemcpyAsync(fro2.data(), ns.fro2, 8 * wv.count, cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaMemcpyAsync(beta.data(), ns.beta, 8 * wv.count, cudaMemcpyDeviceToHost, st));
+  SM_CUDA(cudaStreamSynchronize(st));
+  double sigma = 0.0;
+  std::vector<double> bound(wv.count, 0.0);
+  const double eps0 = f64 ? 0x1p-50 : 0x1p-22, eps_ld = f64 ? 0x1p-52 : 0x1p-23;
+  for (int s = 0; s < wv.count; ++s) {
+    double cv = 0.0, gv = 0.0;
+    std::memcpy(&cv, &cert[s], 8);
+    std::memcpy(&gv, &gersh[s], 8);
+    const double bnd = std::min(gv, std::sqrt(fro2[s])) * (1.0 + 1e-4);
+    if (!(bnd > 0.0)) continue;  // a zero submatrix: f(0) = 1/2 whatever the scale
+    const int ld = wv.host_ld[s];
+    const double gx = gv / bnd;
+    const double Gs = cv * (1.0 + ld * 0x1p-24) + (eps0 + eps_ld * ld) * gx * gx;
+    bound[s] = beta[s] * std::min(1.0, std::sqrt(Gs));
+    sigma = std::max(sigma, bound[s]);
+  }
+  sigma *= 1.0 + 1e-6;
+  if (!(sigma > 0.0)) sigma = 1.0;
+  for (int s = 0; s < wv.count; ++s)
+    if (bound[s] > 0.0) ratio[s] = beta[s] / sigma;
+  SM_CUDA(cudaMemcpyAsync(ns.cscale, ratio.data(), 8 * wv.count, cudaMemcpyHostToDevice, st));
+  k_fermi_rescale<T><<<fermi_grid(wv), 256, 0, st>>>(wv.dev, odd, T2, ns.cscale);
+  SM_KCHECK();
+  if (dual) {  // X' and T_2' = 2 (X' X + X X') follow the scale linearly / quadratically
+    k_fermi_rescale<T><<<fermi_grid(wv), 256, 0, st>>>(wv.dev, dp(odd), nullptr, ns.cscale);
     SM_KCHECK();
-    FermiPoly P;
-    SM_TRY(fermi_poly(sigma / (2.0 * opt.kT), tol_poly, kFermiMaxDegree, &P));
-    fermi_degree = std::max(fermi_degree, P.m);
-    fermi_trunc = std::max(fermi_trunc, P.trunc);
-    // baby steps: T_3 = 2 T_2 X - X, T_{k+2} = 2 T_2 T_k - T_{k-2}
-    for (int q = 1; q < S / 2; ++q)
-      SM_TRY(gemm(T2, odd + int64_t(q - 1) * E, q >= 2 ? odd + int64_t(q - 2) * E : odd, odd + int64_t(q) * E,
-                  2.0, -1.0, 0.0));
-    // Y = T_16 = 2 T_9 T_7 - T_2, in T_2's buffer
-    SM_TRY(gemm(odd + 4 * E, odd + 3 * E, T2, T2, 2.0, -1.0, 0.0));
-    const T* Y = T2;
-    // giant steps: Clenshaw in Y with the coefficients R_j
-    auto comb = [&](int j, const T* B, T* W) -> submat_status {
-      CombArgs ca;
-      for (int q = 0; q < S / 2; ++q) ca.r[q] = P.r[size_t(j) * (S / 2) + q];
-      k_cheb_comb<T><<<fermi_grid(wv), 256, 0, st>>>(wv.dev, odd, E, ca, B, W);
+    k_fermi_scale_sq<T><<<fermi_grid(wv), 256, 0, st>>>(wv.dev, dp(T2), ns.cscale);
+    SM_KCHECK();
+  }
+  FermiPoly P;
+  SM_TRY(fermi_poly(sigma / (2.0 * opt.kT), tol_poly, kFermiMaxDegree, &P));
+  fermi_degree = std::max(fermi_degree, P.m);
+  fermi_trunc = std::max(fermi_trunc, P.trunc);
+  // baby steps: T_3 = 2 T_2 X - X, T_{k+2} = 2 T_2 T_k - T_{k-2}
+  for (int q = 1; q < S / 2; ++q)
+    SM_TRY(gemm(T2, odd + int64_t(q - 1) * E, q >= 2 ? odd + int64_t(q - 2) * E : odd, odd + int64_t(q) * E,
+                2.0, -1.0, 0.0));
+  // Y = T_16 = 2 T_9 T_7 - T_2, in T_2's buffer
+  SM_TRY(gemm(odd + 4 * E, odd + 3 * E, T2, T2, 2.0, -1.0, 0.0));
+  const T* Y = T2;
+  // giant steps: Clenshaw in Y with the coefficients R_j
+  auto comb = [&](int j, const T* B, T* W) -> submat_status {
+    CombArgs ca;
+    for (int q = 0; q < S / 2; ++q) ca.r[q] = P.r[size_t(j) * (S / 2) + q];
+    k_cheb_comb<T><<<fermi_grid(wv), 256, 0, st>>>(wv.dev, odd, E, ca, B, W);
+    SM_KCHECK();
+    if (dual) {
+      k_cheb_comb<T><<<fermi_grid(wv), 256, 0, st>>>(wv.dev, dp(odd), E, ca, dp(B), dp(W));
       SM_KCHECK();
-      return SUBMAT_OK;
-    };
-    T* out = nullptr;
-    if (P.blocks == 1) {
-      SM_TRY(comb(0, nullptr, bb[0]));
-      out = bb[0];
-    } else {
-      T* b1 = bb[0];     // b_{j+1}
-      T* b2 = nullptr;   // b_{j+2} (b_G = 0 at the start)
-      SM_TRY(comb(P.blocks - 1, nullptr, b1));
-      for (int j = P.blocks - 2; j >= 0; --j) {
-        // W = R_j - b_{j+2} (in place over b_{j+2}), then W += c Y b_{j+1}
-        T* W = b2 ? b2 : bb[1];
-        SM_TRY(comb(j, b2, W));
-        SM_TRY(gemm(Y, b1, W, W, j == 0 ? 1.0 : 2.0, 1.0, 0.0));
-        if (j == 0) { out = W; break; }
-        b2 = b1;
-        b1 = W;
-      }
     }
-    SM_CUDA(cudaEventRecord(ev[2], st));
-    // D = (I - p(X)) / 2 on the extracted columns, Tr and sum of squares
-    SM_TRY(scatter_timed(wv, f64 ? 16.0 : 12.0, [&] {
-      return launch_scatter_sq<T>(g, wv.dev, ns, out, D, d_trpart, d_sqpart, nb_max, st);
-    }, st));
-    SM_CUDA(cudaEventRecord(ev[3], st));
-    SM_TRY(collect_wave(wv, st));
-    SM_TRY(add_phase_times());
-    for (int s = 0; s < wv.count; ++s) {
-      res_iters[wv.first + s] = products;  // products of the evaluation, for the statistics
-      const double n = wv.host_n[s];
-      fl_total += 2.0 * n * n * n * products;
+    return SUBMAT_OK;
+  };
+  T* out = nullptr;
+  if (P.blocks == 1) {
+    SM_TRY(comb(0, nullptr, bb[0]));
+    out = bb[0];
+  } else {
+    T* b1 = bb[0];     // b_{j+1}
+    T* b2 = nullptr;   // b_{j+2} (b_G = 0 at the start)
+    SM_TRY(comb(P.blocks - 1, nullptr, b1));
+    for (int j = P.blocks - 2; j >= 0; --j) {
+      // W = R_j - b_{j+2} (in place over b_{j+2}), then W += c Y b_{j+1}
+      T* W = b2 ? b2 : bb[1];
+      SM_TRY(comb(j, b2, W));
+      SM_TRY(gemm(Y, b1, W, W, j == 0 ? 1.0 : 2.0, 1.0, 0.0));
+      if (j == 0) { out = W; break; }
+      b2 = b1;
+      b1 = W;
     }
   }
-  fermi_flops = fl_total;
+  SM_CUDA(cudaEventRecord(ev[2], st));
+  // D = (I - p(X)) / 2 on the extracted columns, Tr and sum of squares
+  SM_TRY(scatter_timed(wv, f64 ? 16.0 : 12.0, [&] {
+    return launch_scatter_sq<T>(g, wv.dev, ns, out, D, d_trpart, d_sqpart, nb_max, st);
+  }, st));
+  if (dual) SM_CUDA(launch_bwd_scatter_add<T>(g, wv, nb_max, dp(out), Kbar, st));
+  SM_CUDA(cudaEventRecord(ev[3], st));
+  SM_TRY(collect_wave(wv, st));
+  SM_TRY(add_phase_times());
+  for (int s = 0; s < wv.count; ++s) {
+    res_iters[wv.first + s] = products;  // products of the evaluation, for the statistics
+    const double n = wv.host_n[s];
+    fermi_flops += 2.0 * n * n * n * products * (dual ? 3.0 : 1.0);
+  }
+  return SUBMAT_OK;
+}
+
+template <typename T>
+submat_status Plan::sign_fermi(const double* K, double mu, double* D, cudaStream_t st) {
+  for (auto& wv : waves) SM_TRY(fermi_wave<T>(wv, K, mu, D, nullptr, nullptr, ws, ws_elems, st));
   return SUBMAT_OK;
 }
 
@@ -336,14 +396,57 @@ submat_status Plan::fermi_dn_dmu(cudaStream_t st, double* out) {
   return SUBMAT_OK;
 }
 
-// The adjoint at finite temperature: the gradient of K -> D is not built
-// yet; dN/dmu alone comes from a forward evaluation (the adjoint's
-// L_f(a_j, I) is f'(a_j), a function of a_j itself).
+// The adjoint at finite temperature (vector-Jacobian product of K -> D):
+// fermi_wave on dual numbers, on the adjoint's own waves and workspace.
+// dN/dmu = sum_j sum_{c in block j} [f'(a_j)]_cc comes from the value part
+// of the same pass (f' = f (1 - f) / kT is a function of a_j itself).
 submat_status Plan::backward_fermi(const double* K, double mu, const double* Dbar, double* Kbar,
                                    double* dN_dmu, cudaStream_t st) {
-  (void)K; (void)mu; (void)Dbar; (void)Kbar; (void)dN_dmu; (void)st;
-  set_error("submat_sign_backward: the finite-temperature gradient is not available");
-  return SUBMAT_ERR_UNSUPPORTED;
+  reset_stats();
+  fermi_degree = 0;
+  fermi_trunc = fermi_flops = 0.0;
+  SM_CUDA(cudaMemsetAsync(d_flags, 0, 4 * sizeof(int), st));
+  SM_CUDA(launch_check_finite(Dbar, nvals, d_flags, st));
+  int fl = 0;
+  SM_TRY(read_flags(st, &fl));
+  if (fl & FLAG_NONFINITE) {
+    set_error("Dbar holds a NaN or Inf value");
+    return SUBMAT_ERR_NONFINITE;
+  }
+  const size_t bpe = fermi_dual_bytes_per_elem(opt.prec);
+  if (bwaves.empty()) {
+    size_t fre = 0, tot = 0;
+    SM_CUDA(cudaMemGetInfo(&fre, &tot));
+    size_t cap = opt.workspace_cap_bytes ? opt.workspace_cap_bytes : size_t(double(fre) * 0.8);
+    SM_TRY(build_waves(bpe, cap, bwaves, st));
+    int64_t mx = 0;
+    for (auto& wv : bwaves) {
+      mx = std::max(mx, wv.elems);
+      max_bwave = std::max(max_bwave, wv.count);
+    }
+    SM_TRY(grow_ns_state(max_bwave));
+    bws_elems = mx;
+    SM_TRY(dev_alloc(&bws, size_t(mx) * bpe, "adjoint workspace"));
+    owned.push_back(bws);
+  }
+  SM_CUDA(cudaMemsetAsync(Kbar, 0, sizeof(double) * size_t(nvals), st));
+  for (auto& wv : bwaves) {
+    if (opt.prec == SUBMAT_FP64) SM_TRY(fermi_wave<double>(wv, K, mu, nullptr, Dbar, Kbar, bws, bws_elems, st));
+    else SM_TRY(fermi_wave<float>(wv, K, mu, nullptr, Dbar, Kbar, bws, bws_elems, st));
+  }
+  SM_CUDA(cudaStreamSynchronize(st));
+  finish_stats(true);
+  stats.flops_ns = fermi_flops;
+  stats.poly_degree = fermi_degree;
+  stats.poly_trunc = fermi_trunc;
+  SM_TRY(fermi_dn_dmu(st, &stats.dn_dmu));
+  if (dN_dmu) *dN_dmu = stats.dn_dmu;
+  SM_TRY(read_flags(st, &fl));
+  if (fl & FLAG_NONFINITE) {
+    set_error("K holds a NaN or Inf value");
+    return SUBMAT_ERR_NONFINITE;
+  }
+  return SUBMAT_OK;
 }
 
 }  // namespace submat

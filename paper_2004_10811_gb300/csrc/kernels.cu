@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256) k_scatter(PatternDev g, WaveDev w, NsStat
     if (correct) sv -= f2d_exact(ca[si] + cb[si]);
     const bool diag = (col == koff + c);
     const double v = (diag ? 0.5 : 0.0) - 0.5 * sv;
-    D[g.valptr[p] + int64_t(r) * bj + c] = v;
+    if (D) D[g.valptr[p] + int64_t(r) * bj + c] = v;  // null: trace and squares only
     if (diag) tr += v;
     if (sqpart) sq = fma(v, v, sq);
   }

@@ -646,7 +646,7 @@ void Plan::finish_stats(bool adjoint) {
     imax = std::max(imax, res_iters[j]);
     nc += res_notconv[j];
     const double n3 = double(nsub[j]) * nsub[j] * nsub[j];
-    if (opt.kT > 0.0 && !adjoint) flops += 2.0 * n3 * res_iters[j];  // res_iters: products
+    if (opt.kT > 0.0) flops += (adjoint ? 6.0 : 2.0) * n3 * res_iters[j];  // res_iters: products
     else flops += adjoint ? 12.0 * n3 * (res_iters[j] + 2) : (opt.iteration == 1 ? 6.0 : 4.0) * n3 * res_iters[j];
     rmax = std::max(rmax, res_resid[j]);
   }
@@ -659,7 +659,7 @@ void Plan::finish_stats(bool adjoint) {
   if (timer.on) {
     timer.collect(stats.kernel_ms, stats.kernel_launches);
     if (adjoint) {  // every adjoint product runs on one GEMM kind
-      stats.kernel_work[opt.adjoint_mode == 1 ? KC_TC_ADJ : KC_SIMT] += flops;
+      stats.kernel_work[opt.adjoint_mode == 1 && opt.kT == 0.0 ? KC_TC_ADJ : KC_SIMT] += flops;
     } else if (opt.kT > 0.0) {
       stats.kernel_work[KC_SIMT] += flops;
     } else if (opt.prec != SUBMAT_MIXED_BF16_REFINE) {

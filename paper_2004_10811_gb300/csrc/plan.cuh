@@ -98,6 +98,12 @@ cudaError_t launch_bwd_scatter_add_f32(const PatternDev& g, const Wave& wv, int 
                                        double* Kbar, cudaStream_t st);
 cudaError_t launch_bwd_dn_f32(const PatternDev& g, const Wave& wv, const float* E, double* part,
                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_bwd_seed(const PatternDev& g, const Wave& wv, const double* Dbar, const double* beta, T* E,
+                            int identity, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bwd_scatter_add(const PatternDev& g, const Wave& wv, int nb_max, const T* E, double* Kbar,
+                                   cudaStream_t st);
 
 // Event pairs around kernel launches, grouped in classes (submat_stats kernel_*).
 struct KernelTimer {
@@ -207,6 +213,12 @@ struct Plan {
   submat_status sign_mixed(const double* K, double mu, double* D, cudaStream_t st);
   template <typename T>
   submat_status sign_fermi(const double* K, double mu, double* D, cudaStream_t st);
+  // one wave of the finite-temperature evaluation on workspace `w` of E
+  // elements per buffer; with Dbar set, the polynomial runs on dual numbers
+  // and -1/2 of its derivative part (L_f(a_j, G_j)) is added into Kbar
+  template <typename T>
+  submat_status fermi_wave(Wave& wv, const double* K, double mu, double* D, const double* Dbar, double* Kbar,
+                           void* w, int64_t E, cudaStream_t st);
   submat_status fermi_dn_dmu(cudaStream_t st, double* out);
   submat_status backward_fermi(const double* K, double mu, const double* Dbar, double* Kbar, double* dN_dmu,
                                cudaStream_t st);

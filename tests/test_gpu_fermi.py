@@ -23,6 +23,20 @@ def pkg():
     return p
 
 
+def transpose_index(m):
+    """perm such that vals[perm] lays out K_(c,r)^T in block (r, c)'s slots."""
+    vp = m.val_ptr
+    rows = np.repeat(np.arange(m.nblk), np.diff(m.row_ptr))
+    pos = {(int(rows[p]), int(m.col_idx[p])): p for p in range(m.nnzb)}
+    perm = np.empty(m.vals.shape[0], dtype=np.int64)
+    for (r, c), p in pos.items():
+        q = pos[(c, r)]
+        br, bc = m.block_sizes[r], m.block_sizes[c]
+        idx = np.arange(br * bc)
+        perm[vp[p] + idx] = vp[q] + (idx % bc) * br + idx // bc
+    return perm
+
+
 def run(pkg, m, mu, kT, **kw):
     import torch
     K = torch.from_numpy(m.vals).cuda()
@@ -169,14 +183,59 @@ def test_full_size_column_ranges(pkg, cfg):
     assert float(np.max(np.abs(got[mask] - want[mask]))) <= TOL["fp64"]
 
 
-def test_adjoint_not_available_and_mixed_refused(pkg):
-    import torch
+def test_mixed_plan_refused(pkg):
     m = small_case(n_mol=12, block=3, r_c=5.5, seed=9)
-    K = torch.from_numpy(m.vals).cuda()
-    with pkg.Plan.from_bsr(m, prec="fp64", kT=0.1) as plan:
-        with pytest.raises(pkg.SubmatError) as ei:
-            plan.sign_backward(K, 0.0, torch.ones_like(K))
-        assert ei.value.name == "UNSUPPORTED"
     with pytest.raises(pkg.SubmatError) as ei:
         pkg.Plan.from_bsr(m, prec="mixed", kT=0.1)
     assert ei.value.name == "UNSUPPORTED"
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
+@pytest.mark.parametrize("kT,mu", [(0.05, 0.02), (0.2, -0.1)])
+def test_adjoint_matches_daleckii_krein(pkg, prec, tol, kT, mu):
+    """Kbar from the polynomial on dual numbers against the oracle's
+    Daleckii-Krein gradient with the Fermi function's divided differences;
+    dN/dmu from the same pass against the oracle's."""
+    import torch
+    m = small_case(n_mol=20, block=4, r_c=5.5, seed=101)
+    rng = np.random.default_rng(1)
+    dbar = rng.standard_normal(m.vals.shape)
+    want, dn_want = oracle.fermi_backward(m, dbar, mu, kT)
+    with pkg.Plan.from_bsr(m, prec=prec, kT=kT) as plan:
+        kbar, dn = plan.sign_backward(torch.from_numpy(m.vals).cuda(), mu, torch.from_numpy(dbar).cuda(),
+                                      want_dn_dmu=True)
+    got = kbar.cpu().numpy()
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+    eps = 1e-12 if prec == "fp64" else 2e-6
+    assert abs(dn - dn_want) <= 1e-8 * dn_want + eps * m.n / kT
+
+
+def test_band_energy_gradient_matches_central_differences(pkg):
+    """E = Tr(D K) at finite temperature through the autograd wrapper (the
+    library's adjoint for the implicit part) against central differences of
+    the GPU forward map, moving K_pq and K_qp together."""
+    import torch
+    m = small_case(n_mol=12, block=3, r_c=5.5, seed=33)
+    kT, mu, h = 0.1, 0.0, 1e-5
+    perm = torch.from_numpy(transpose_index(m)).cuda()
+    with pkg.Plan.from_bsr(m, prec="fp64", kT=kT) as plan:
+        K = torch.from_numpy(m.vals.copy()).cuda().requires_grad_(True)
+        sign_fn = pkg.make_autograd_sign(plan)
+        E = (sign_fn(K, mu) * K[perm]).sum()
+        E.backward()
+        grad = K.grad.cpu().numpy()
+        rng = np.random.default_rng(4)
+        tp = transpose_index(m)
+        for p in rng.choice(m.vals.shape[0], 12, replace=False):
+            q = int(tp[p])
+            vals = []
+            for d in (h, -h):
+                v = m.vals.copy()
+                v[p] += d
+                if q != p:
+                    v[q] += d
+                Kd = torch.from_numpy(v).cuda()
+                vals.append(float((plan.sign(Kd, mu) * Kd[perm]).sum()))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = grad[p] + (grad[q] if q != p else 0.0)
+            assert abs(an - fd) <= 1e-6 * max(1.0, abs(fd)), (p, an, fd)
