@@ -158,6 +158,16 @@ __device__ __forceinline__ uint32_t pack_split(float o) {
   return uint32_t(__bfloat16_as_ushort(h)) | (uint32_t(__bfloat16_as_ushort(l)) << 16);
 }
 
+// two values as (hi, lo) BF16 pairs: hi = rn(v), lo = rn(v - hi), two
+// values per conversion instruction; bit-identical to pack_split
+__device__ __forceinline__ void pack_split2(float a, float b, uint32_t* hw, uint32_t* lw) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  *hw = *reinterpret_cast<const uint32_t*>(&h);
+  *lw = *reinterpret_cast<const uint32_t*>(&l);
+}
+
 // one 32-byte store (a full L2 sector); the address is 32-byte aligned
 __device__ __forceinline__ void st_v8(void* d, const uint32_t* w) {
   asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(d), "r"(w[0]), "r"(w[1]),
@@ -174,11 +184,7 @@ __device__ __forceinline__ void store_row(const TcGemmParams& p, int64_t idx, co
   } else {
     uint32_t hw[16], lw[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const uint32_t a = pack_split(o[2 * q]), b = pack_split(o[2 * q + 1]);
-      hw[q] = (a & 0xFFFFu) | (b << 16);
-      lw[q] = (a >> 16) | (b & 0xFFFF0000u);
-    }
+    for (int q = 0; q < 16; ++q) pack_split2(o[2 * q], o[2 * q + 1], &hw[q], &lw[q]);
     st_v8(p.out_hi + idx, hw);
     st_v8(p.out_hi + idx + 16, hw + 8);
     if (p.out_lo) {
@@ -241,7 +247,10 @@ __device__ __forceinline__ void load_c0(const TcGemmParams& p, int64_t idx, floa
   }
 }
 
-template <int BN>
+// LEAN: the launch has one accumulator, a BF16-pair or FP32 output, no
+// mirror and double-buffered TMEM (the host checks), and the epilogue drains
+// it 32 columns at a time; the general epilogue is not compiled in.
+template <int BN, bool LEAN>
 __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGemmParams p) {
   constexpr int TILE_B = BN * BK * 2;  // one BN x 64 BF16 operand tile (B side)
   constexpr int HALVES = BN / 128;
@@ -412,6 +421,71 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       const int rg = item.y * BM + r;
       double part = 0.0;
       const uint32_t tbase = tmem_base + (uint32_t(quarter * 32) << 16) + uint32_t(ab * p.nacc * BN);
+      // Lean path for the common launches (one accumulator, BF16-pair or FP32
+      // output, no mirror, double-buffered TMEM): 32 columns at a time, so
+      // only one chunk is live in registers, and the diagonal handled only
+      // on diagonal sub-tiles.  TMEM is released after its last read.
+      if constexpr (LEAN) {
+        for (int h = 0; h < HALVES; ++h) {
+          const int sub_tj = item.z * HALVES + h;
+          const bool last_h = h == HALVES - 1;
+          if (p.sym && sub_tj < item.y) {  // below the diagonal: not written
+            if (last_h) {
+              tc_fence_before();
+              if (!p.test_skip_arrive) mbar_arrive(&tempty[ab]);
+            }
+            continue;
+          }
+          const bool dtile = item.y == sub_tj;  // the diagonal crosses this sub-tile
+          const bool diag_sym = p.sym && dtile;
+          const double res_weight = (p.sym && !diag_sym) ? 2.0 : 1.0;
+          const uint32_t tb = tbase + uint32_t(h * 128);
+#pragma unroll 1
+          for (int c = 0; c < 4; ++c) {
+            float a[32];
+            tmem_ld32(tb + uint32_t(c * 32), a);
+            tmem_wait_ld();
+            if (last_h && c == 3) {
+              tc_fence_before();
+              if (!p.test_skip_arrive) mbar_arrive(&tempty[ab]);
+            }
+            const int cg0 = sub_tj * 128 + c * 32;
+            if (rg >= ld || cg0 >= ld) continue;
+            const int64_t idx = base + int64_t(rg) * ld + cg0;
+            const bool has_c0 = (p.c0_f32 || p.c0_hi) && p.beta != 0.0f && !p.dot_c0;
+            float c0[32];
+            if (has_c0 || p.dot_c0) load_c0(p, idx, c0);
+            float o[32];
+            float pr = 0.0f, pd = 0.0f;
+            if (!dtile) {
+#pragma unroll
+              for (int q = 0; q < 32; ++q) {
+                float v = p.alpha * a[q];
+                if (has_c0) v = fmaf(p.beta, c0[q], v);
+                o[q] = v;
+                pr = fmaf(a[q], a[q], pr);
+                if (p.dot_c0) pd = fmaf(v, c0[q], pd);
+              }
+            } else {
+              const int dq = (rg < n) ? rg - cg0 : -1;  // diagonal position in this segment
+#pragma unroll
+              for (int q = 0; q < 32; ++q) {
+                float v = p.alpha * a[q];
+                if (has_c0) v = fmaf(p.beta, c0[q], v);
+                if (q == dq) v += p.diag;
+                o[q] = v;
+                const float e = a[q] - ((q == dq) ? 1.0f : 0.0f);
+                pr = fmaf(e, e, pr);
+                if (p.dot_c0) pd = fmaf(v, c0[q], pd);
+              }
+            }
+            if (p.res2) part += res_weight * double(pr);
+            if (p.dot_c0) part += 2.0 * double(pd);
+            if (diag_sym) store_range(p, idx, o, r - c * 32, 32);
+            else store_row(p, idx, o);
+          }
+        }
+      } else {
       for (int h = 0; h < HALVES; ++h) {
       float acc[128];
       const uint32_t tb = tbase + uint32_t(h * 128);
@@ -552,6 +626,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
         }
       }
       }  // halves
+      }  // general epilogue
       if (p.res2 || p.dot_c0) {
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o2);
@@ -594,16 +669,20 @@ cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st) {
     return cudaErrorInvalidValue;
   const int smem = tc_smem_bytes(p.na, p.nb, p.nstage, bn);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  // the lean epilogue: one accumulator, double-buffered in TMEM, BF16-pair or
+  // FP32 output without a mirror
+  const bool lean = p.tmem_cols >= 2 * bn && p.nacc == 1 && !p.out_i64 && !(p.sym && !p.upper_only) &&
+                    (p.out_f32 || p.out_hi);
+  auto run = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 192, smem, st>>>(p);
+    return cudaSuccess;
+  };
   cudaError_t e;
-  if (bn == 256) {
-    e = cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k_tc_gemm<256><<<grid, 192, smem, st>>>(p);
-  } else {
-    e = cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k_tc_gemm<128><<<grid, 192, smem, st>>>(p);
-  }
+  if (bn == 256) e = lean ? run(k_tc_gemm<256, true>) : run(k_tc_gemm<256, false>);
+  else e = lean ? run(k_tc_gemm<128, true>) : run(k_tc_gemm<128, false>);
+  if (e != cudaSuccess) return e;
   count_launch();
   return cudaGetLastError();
 }
