@@ -84,10 +84,27 @@ struct NsStateDev {
   double* cscale;   // scale certificate: factor applied to X_0 (1 = kept)
 };
 
+// geometry bounds for the gather / scatter kernels: the largest number of
+// blocks in a submatrix, leading dimension and block size
+struct ScatterGeom {
+  int nb_max, ld_max, bs_max;
+};
+
 // ---- kernel launchers (kernels.cu) ----
 cudaError_t launch_gather(const PatternDev& g, const WaveDev& w, const int2* items, int nitems,
-                          int nb_max, int ld_max, const double* K, double mu, double* A, NsStateDev ns,
-                          int* flags, cudaStream_t st);
+                          int nb_max, int ld_max, int bs_max, const double* K, double mu, double* A,
+                          NsStateDev ns, int* flags, cudaStream_t st);
+// (gather.cu) the row-wise gather and the staged scatter
+bool gather_rows_fits(int nb_max, int ld_max, int bs_max);
+cudaError_t launch_gather_rows(const PatternDev& g, const WaveDev& w, int nb_max, int ld_max, const double* K,
+                               double mu, double* A, NsStateDev ns, int* flags, cudaStream_t st);
+size_t scatter_staged_smem(int nb_max, int ld_max, int bs_max);
+template <typename T>
+cudaError_t launch_scatter_staged(const PatternDev& g, const WaveDev& w, NsStateDev ns, const T* buf0,
+                                  const T* buf1, double* D, double* trpart, int nb_max, int ld_max, int bs_max,
+                                  cudaStream_t st, const float* corr_a, const float* corr_b, const int* fallback,
+                                  double* sqpart);
+
 cudaError_t launch_beta(const WaveDev& w, NsStateDev ns, int beta_mode, cudaStream_t st);
 cudaError_t launch_scale_f64(const WaveDev& w, const double* A, double* X, const double* beta,
                              int64_t max_ld2, cudaStream_t st);
@@ -101,16 +118,16 @@ cudaError_t launch_ns_post(const WaveDev& w, NsStateDev ns, int par_new, int* d_
 // S become S - (corr_a + corr_b), except in submatrices with fallback[s] set
 cudaError_t launch_scatter_f64(const PatternDev& g, const WaveDev& w, NsStateDev ns,
                                const double* buf0, const double* buf1, double* D,
-                               double* trpart, int nb_max, cudaStream_t st, const float* corr_a = nullptr,
+                               double* trpart, ScatterGeom geo, cudaStream_t st, const float* corr_a = nullptr,
                                const float* corr_b = nullptr, const int* fallback = nullptr);
 cudaError_t launch_scatter_f32(const PatternDev& g, const WaveDev& w, NsStateDev ns,
                                const float* buf0, const float* buf1, double* D,
-                               double* trpart, int nb_max, cudaStream_t st);
+                               double* trpart, ScatterGeom geo, cudaStream_t st);
 // the same from one buffer S (finite temperature: S = p(X), the polynomial
 // for tanh), with sqpart[j] = sum over the block's columns c of (D_j^2)_cc
 template <typename T>
 cudaError_t launch_scatter_sq(const PatternDev& g, const WaveDev& w, NsStateDev ns, const T* S, double* D,
-                              double* trpart, double* sqpart, int nb_max, cudaStream_t st);
+                              double* trpart, double* sqpart, ScatterGeom geo, cudaStream_t st);
 cudaError_t launch_trace(const PatternDev& g, int nblk, const double* D, double* part,
                          double* out, cudaStream_t st);
 cudaError_t launch_symmetrize_impl(const PatternDev& g, int64_t nnzb, const double* Din,

@@ -360,7 +360,7 @@ submat_status Plan::fermi_wave(Wave& wv, const double* K, double mu, double* D, 
   SM_CUDA(cudaEventRecord(ev[2], st));
   // D = (I - p(X)) / 2 on the extracted columns, Tr and sum of squares
   SM_TRY(scatter_timed(wv, f64 ? 16.0 : 12.0, [&] {
-    return launch_scatter_sq<T>(g, wv.dev, ns, out, D, d_trpart, d_sqpart, nb_max, st);
+    return launch_scatter_sq<T>(g, wv.dev, ns, out, D, d_trpart, d_sqpart, geom(wv), st);
   }, st));
   if (dual) SM_CUDA(launch_bwd_scatter_add<T>(g, wv, nb_max, dp(out), Kbar, st));
   SM_CUDA(cudaEventRecord(ev[3], st));

@@ -467,9 +467,11 @@ void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t launch_gather(const PatternDev& g, const WaveDev& w, const int2* items, int nitems,
-                          int nb_max, int ld_max, const double* K, double mu, double* A, NsStateDev ns,
-                          int* flags, cudaStream_t st) {
+                          int nb_max, int ld_max, int bs_max, const double* K, double mu, double* A,
+                          NsStateDev ns, int* flags, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
+  if (gather_rows_fits(nb_max, ld_max, bs_max))
+    return launch_gather_rows(g, w, nb_max, ld_max, K, mu, A, ns, flags, st);
   const size_t smem = size_t(ld_max) * (sizeof(long long) + sizeof(int)) + size_t(3 * nb_max + 1) * sizeof(int);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -518,9 +520,15 @@ cudaError_t launch_ns_post(const WaveDev& w, NsStateDev ns, int par_new, int* d_
 template <typename T>
 static cudaError_t scatter_impl(const PatternDev& g, const WaveDev& w, NsStateDev ns,
                                 const T* buf0, const T* buf1, double* D, double* trpart,
-                                int nb_max, cudaStream_t st, const float* corr_a = nullptr,
+                                ScatterGeom geo, cudaStream_t st, const float* corr_a = nullptr,
                                 const float* corr_b = nullptr, const int* fallback = nullptr,
                                 double* sqpart = nullptr) {
+  // shared-memory staging of the extracted rows (coalesced reads of S and
+  // whole-block writes of D), unless a block is too large to stage
+  if (scatter_staged_smem(geo.nb_max, geo.ld_max, geo.bs_max) <= 200 * 1024)
+    return launch_scatter_staged<T>(g, w, ns, buf0, buf1, D, trpart, geo.nb_max, geo.ld_max, geo.bs_max, st,
+                                    corr_a, corr_b, fallback, sqpart);
+  const int nb_max = geo.nb_max;
   const size_t smem = size_t(nb_max + 1) * sizeof(int);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_scatter<T>,
@@ -534,26 +542,26 @@ static cudaError_t scatter_impl(const PatternDev& g, const WaveDev& w, NsStateDe
 
 cudaError_t launch_scatter_f64(const PatternDev& g, const WaveDev& w, NsStateDev ns,
                                const double* buf0, const double* buf1, double* D,
-                               double* trpart, int nb_max, cudaStream_t st, const float* corr_a,
+                               double* trpart, ScatterGeom geo, cudaStream_t st, const float* corr_a,
                                const float* corr_b, const int* fallback) {
-  return scatter_impl<double>(g, w, ns, buf0, buf1, D, trpart, nb_max, st, corr_a, corr_b, fallback);
+  return scatter_impl<double>(g, w, ns, buf0, buf1, D, trpart, geo, st, corr_a, corr_b, fallback);
 }
 
 cudaError_t launch_scatter_f32(const PatternDev& g, const WaveDev& w, NsStateDev ns,
                                const float* buf0, const float* buf1, double* D,
-                               double* trpart, int nb_max, cudaStream_t st) {
-  return scatter_impl<float>(g, w, ns, buf0, buf1, D, trpart, nb_max, st);
+                               double* trpart, ScatterGeom geo, cudaStream_t st) {
+  return scatter_impl<float>(g, w, ns, buf0, buf1, D, trpart, geo, st);
 }
 
 template <typename T>
 cudaError_t launch_scatter_sq(const PatternDev& g, const WaveDev& w, NsStateDev ns, const T* S, double* D,
-                              double* trpart, double* sqpart, int nb_max, cudaStream_t st) {
-  return scatter_impl<T>(g, w, ns, S, S, D, trpart, nb_max, st, nullptr, nullptr, nullptr, sqpart);
+                              double* trpart, double* sqpart, ScatterGeom geo, cudaStream_t st) {
+  return scatter_impl<T>(g, w, ns, S, S, D, trpart, geo, st, nullptr, nullptr, nullptr, sqpart);
 }
 template cudaError_t launch_scatter_sq<double>(const PatternDev&, const WaveDev&, NsStateDev, const double*,
-                                               double*, double*, double*, int, cudaStream_t);
+                                               double*, double*, double*, ScatterGeom, cudaStream_t);
 template cudaError_t launch_scatter_sq<float>(const PatternDev&, const WaveDev&, NsStateDev, const float*,
-                                              double*, double*, double*, int, cudaStream_t);
+                                              double*, double*, double*, ScatterGeom, cudaStream_t);
 
 cudaError_t launch_trace(const PatternDev& g, int nblk, const double* D, double* part,
                          double* out, cudaStream_t st) {

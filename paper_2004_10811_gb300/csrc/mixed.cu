@@ -1419,7 +1419,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     SM_CUDA(cudaEventRecord(ev[3], st));
     // ---- extract (Section III-A step 3); ns.par picks S or, for fallbacks, S/T ----
     SM_TRY(scatter_timed(wv, 24.0, [&] {
-      return launch_scatter_f64(g, wv.dev, ns, outS0, outS1, D, d_trpart, nb_max, st, b.Fc, b.cx, ms->pick);
+      return launch_scatter_f64(g, wv.dev, ns, outS0, outS1, D, d_trpart, geom(wv), st, b.Fc, b.cx, ms->pick);
     }, st));
     SM_TRY(collect_wave(wv, st));
     float t01 = 0, t12 = 0, t23 = 0;

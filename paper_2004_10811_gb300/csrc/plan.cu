@@ -313,6 +313,7 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
   nb_max = 0;
   n_max = 0;
   n_min = INT32_MAX;
+  bs_max = *std::max_element(bs.begin(), bs.end());
   sum_n2 = sum_n3 = 0.0;
   for (int j = 0; j < nblk; ++j) {
     int64_t acc = 0;
@@ -457,7 +458,8 @@ submat_status Plan::gather_wave(Wave& wv, const double* K, double mu, double* A,
   SM_CUDA(cudaMemsetAsync(ns.fro2, 0, sizeof(double) * wv.count, st));
   size_t tk;
   SM_TRY(timer.start(KC_GATHER, st, &tk));
-  SM_CUDA(launch_gather(g, wv.dev, wv.gather_items, wv.n_gather, nb_max, max_ld(wv), K, mu, A, ns, d_flags, st));
+  SM_CUDA(launch_gather(g, wv.dev, wv.gather_items, wv.n_gather, nb_max, max_ld(wv), bs_max, K, mu, A, ns, d_flags,
+                        st));
   SM_TRY(timer.stop(tk, st));
   if (timer.on)
     for (int s = 0; s < wv.count; ++s)
@@ -555,7 +557,7 @@ submat_status Plan::sign_fp64(const double* K, double mu, double* D, cudaStream_
     SM_TRY((ns_simt<double, GemmF64Args>(wv, B0, B1, Y, tol_eff, 1e-9, st, launch_gemm_f64,
                                          opt.beta_mode == 0)));
     SM_CUDA(cudaEventRecord(ev[2], st));
-    SM_TRY(scatter_timed(wv, 16.0, [&] { return launch_scatter_f64(g, wv.dev, ns, B0, B1, D, d_trpart, nb_max, st); },
+    SM_TRY(scatter_timed(wv, 16.0, [&] { return launch_scatter_f64(g, wv.dev, ns, B0, B1, D, d_trpart, geom(wv), st); },
                          st));
     SM_CUDA(cudaEventRecord(ev[3], st));
     SM_TRY(collect_wave(wv, st));
@@ -582,7 +584,7 @@ submat_status Plan::sign_fp32(const double* K, double mu, double* D, cudaStream_
     SM_TRY((ns_simt<float, GemmF32Args>(wv, B0, B1, Y, tol_eff, 1e-4, st, launch_gemm_f32,
                                         opt.beta_mode == 0)));
     SM_CUDA(cudaEventRecord(ev[2], st));
-    SM_TRY(scatter_timed(wv, 12.0, [&] { return launch_scatter_f32(g, wv.dev, ns, B0, B1, D, d_trpart, nb_max, st); },
+    SM_TRY(scatter_timed(wv, 12.0, [&] { return launch_scatter_f32(g, wv.dev, ns, B0, B1, D, d_trpart, geom(wv), st); },
                          st));
     SM_CUDA(cudaEventRecord(ev[3], st));
     SM_TRY(collect_wave(wv, st));

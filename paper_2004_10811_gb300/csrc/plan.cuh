@@ -134,7 +134,8 @@ struct Plan {
   double tol_eff = 1e-14;
   std::vector<int32_t> bs, col, locoff, tpos, nsub, koff, diagpos;
   std::vector<int64_t> row_ptr, valptr, rowof;
-  int nb_max = 0, n_max = 0, n_min = 0;
+  int nb_max = 0, n_max = 0, n_min = 0, bs_max = 1;
+  ScatterGeom geom(const Wave& wv) const { return ScatterGeom{nb_max, max_ld(wv), bs_max}; }
   int col_lo = 0, col_hi = 0;      // evaluated block columns
   double sum_n2 = 0, sum_n3 = 0;
 
