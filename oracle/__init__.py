@@ -11,6 +11,9 @@ Finite temperature (``oracle.fermi``): the Fermi function in place of
 signum (Section IV-F, last paragraph), with its electron count, dN/dmu, a
 bracketed Newton search for mu and the Daleckii-Krein gradient.
 
+Groups of block columns sharing one submatrix (``oracle.grouped``, Section
+IV-C): ``density_matrix_grouped``.
+
 Parity unpinned: results that depend on eigenvalues of a submatrix lying
 within about 1e-8 of the chemical potential (the answer there is
 ill-conditioned, sensitivity ~ rounding / |lambda|); see the pins in
@@ -44,3 +47,4 @@ from .fermi import (  # noqa: F401
     frechet_fermi,
     fermi_backward,
 )
+from .grouped import density_matrix_grouped  # noqa: F401
