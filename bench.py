@@ -233,6 +233,9 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=0,
                     help="block columns timed on the FP64 path (0: the whole build)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the whole-build FP32 path timing")
+    ap.add_argument("--group-size", type=int, default=2,
+                    help="block columns per submatrix for the grouped key (periodic k-means on the molecule "
+                         "centres, Section IV-C); 0 skips it")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--adjoint-sample", type=int, default=32,
@@ -302,6 +305,7 @@ def main():
     for _ in range(args.warmup):
         plan.sign(K, m.mu, out=D)
     torch.cuda.synchronize()
+    plan_tiles = (plan.options.tile_n_ns, plan.options.tile_n_corr, plan.options.tile_n_hp)
 
     # ---- device-resident timed region ----
     acc = {"kernel_ms": [0.0] * NCLASS, "kernel_launches": [0] * NCLASS, "kernel_work": [0.0] * NCLASS,
@@ -531,6 +535,44 @@ def main():
         f32 = other_path("fp32", 0)
         f32["speedup_mixed_vs_fp32"] = f32["s_per_build"] / value
         line["fp32_path"] = f32
+    # ---- submatrices shared by k-means groups of block columns (Section IV-C) ----
+    if args.group_size > 1 and args.prec == "mixed" and world == 1 and not columns:
+        from paper_2004_10811_gb300 import grouping
+        t0 = time.perf_counter()
+        groups = grouping.periodic_kmeans(m.coords, m.box, max(1, m.nblk // args.group_size), seed=1)
+        t_km = time.perf_counter() - t0
+        single_dims = sub["dims"]
+        gdims, _gl = grouping.group_dims(m.block_sizes, m.row_ptr, m.col_idx, groups)
+        with pkg.Plan.from_bsr(m, prec="mixed", groups=groups, timing=True, tile_n_ns=plan_tiles[0],
+                               tile_n_corr=plan_tiles[1], tile_n_hp=plan_tiles[2]) as pg:
+            Dg = torch.empty_like(K)
+            pg.sign(K, m.mu, out=Dg)
+            torch.cuda.synchronize()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            reps = 2
+            g0.record(stream)
+            for _ in range(reps):
+                pg.sign(K, m.mu, out=Dg)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            tg = g0.elapsed_time(g1) / 1e3 / reps
+            sg = pg.stats()
+        gline = {"group_size": args.group_size, "submatrices": int(groups.max()) + 1,
+                 "sub_dim_min": int(gdims.min()), "sub_dim_max": int(gdims.max()),
+                 "s_per_build": tg, "speedup_vs_single_columns": value / tg,
+                 "estimated_speedup_sum_n3": grouping.estimated_speedup(single_dims, gdims),
+                 "kmeans_s": round(t_km, 2), "iters_max": int(sg["iters_max"]),
+                 "fp64_fallback_submatrices": int(sg["refine_fallback"])}
+        if not args.no_cpu:
+            import oracle
+            sample = np.linspace(0, groups.max(), 16).astype(int)
+            wantg = oracle.density_matrix_grouped(m, m.mu, groups, only=sample)
+            mk = ~np.isnan(wantg)
+            gline["max_abs_err_vs_grouped_oracle"] = float(np.max(np.abs(Dg.cpu().numpy()[mk] - wantg[mk])))
+            gline["parity_sample"] = f"{len(sample)} of {int(groups.max()) + 1} groups"
+        line["grouped"] = gline
+
     # ---- the adjoint (vector-Jacobian product) on a contiguous chunk of block columns ----
     if args.adjoint_sample > 0 and world == 1 and not columns:
         nc = min(args.adjoint_sample, m.nblk)

@@ -200,6 +200,27 @@ submat_status submat_plan_create(int nblk, const int32_t* block_sizes,
                                  const submat_options* opt, void* stream,
                                  submat_plan** out);
 
+/*
+ * A plan whose submatrices are shared by groups of block columns (Section
+ * IV-C, "Generating Submatrices From Multiple Block Columns"): the block
+ * columns j with groups[j] = q share one submatrix over N(q), the ascending
+ * union of their row sets N(j), so a_q = K[N(q), N(q)] - mu I, and every
+ * member j takes the columns of block j of 1/2 (I - sign(a_q)) into block
+ * column j of D (rows N(j): D keeps K's pattern).  Larger submatrices change
+ * the method's truncation (they see more of K) and, by the paper's cost model
+ * sum_q n_q^3 (Eq. estimatedspeedup), can cost fewer operations when the
+ * members are close in space.
+ *   groups  host int32[nblk], group ids 0 .. ngroups - 1, every id used;
+ *           copied.  paper_2004_10811_gb300.grouping finds groups by
+ *           periodic k-means on the molecule centres.
+ * Other arguments and errors as submat_plan_create.  Column ranges
+ * (col_begin / col_end) and submat_sign_backward are UNSUPPORTED for
+ * grouped plans.  Statistics per block column report its group's submatrix.
+ */
+submat_status submat_plan_create_grouped(int nblk, const int32_t* block_sizes, const int64_t* row_ptr,
+                                         const int32_t* col_idx, const int32_t* groups,
+                                         const submat_options* opt, void* stream, submat_plan** out);
+
 /* Release the plan and all device memory it owns.  NULL is allowed. */
 submat_status submat_plan_destroy(submat_plan* plan);
 

@@ -24,15 +24,16 @@ def group_rows(m, members, structure=None):
     return np.unique(np.concatenate([structure[int(j)] for j in members]))
 
 
-def density_matrix_grouped(m, mu, groups):
+def density_matrix_grouped(m, mu, groups, only=None):
     """D in K's block pattern with one submatrix per group; ``groups[j]`` is
-    the group of block column j."""
+    the group of block column j.  ``only`` restricts the evaluation to some
+    groups (the block columns of the others are NaN)."""
     groups = np.asarray(groups)
     structure = column_structure(m)
     lookup = _block_lookup(m)
     bs = m.block_sizes
     out = np.full(m.vals.shape, np.nan)
-    for g in np.unique(groups):
+    for g in (np.unique(groups) if only is None else np.asarray(only)):
         members = np.flatnonzero(groups == g)
         rows = group_rows(m, members, structure)
         loc = np.zeros(len(rows) + 1, dtype=np.int64)

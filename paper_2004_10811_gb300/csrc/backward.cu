@@ -295,6 +295,10 @@ submat_status Plan::backward_wave(Wave& wv, const double* K, double mu, const do
 
 submat_status Plan::backward(const double* K, double mu, const double* Dbar, double* Kbar,
                              double* dN_dmu, cudaStream_t st) {
+  if (grouped) {
+    set_error("submat_sign_backward: not available for grouped plans");
+    return SUBMAT_ERR_UNSUPPORTED;
+  }
   if (opt.kT > 0.0) return backward_fermi(K, mu, Dbar, Kbar, dN_dmu, st);
   reset_stats();
   SM_CUDA(cudaMemsetAsync(d_flags, 0, 4 * sizeof(int), st));

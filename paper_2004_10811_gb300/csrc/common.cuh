@@ -58,6 +58,20 @@ struct PatternDev {
   const int32_t* nsub;     // [nblk] submatrix dimension n_j
   const int32_t* koff;     // [nblk] local offset of block j inside submatrix j
   const int32_t* diagpos;  // [nblk] CSR position of block (j, j)
+  // Submatrices (index q = WaveDev::sub[s]): one per block column, or one
+  // per group of block columns (Section IV-C) over the union of their rows.
+  // Without groups sp / srows / sloc are row_ptr / col / locoff.
+  const int64_t* sp;       // [nq + 1] block rows of submatrix q: srows[sp[q] .. sp[q+1])
+  const int32_t* srows;    //   ascending block rows N(q)
+  const int32_t* sloc;     //   their local offsets inside submatrix q
+  // groups only (null otherwise): the member block columns of submatrix q,
+  // mcol[mp[q] .. mp[q+1]), block j's local offset mkoff[], and for every
+  // stored block p = (i, j) the local offset dloc[p] of block row i in the
+  // submatrix of j's group
+  const int32_t* mp;
+  const int32_t* mcol;
+  const int32_t* mkoff;
+  const int32_t* dloc;
 };
 
 // One wave: a set of submatrices whose dense buffers fit the workspace together.
@@ -85,9 +99,12 @@ struct NsStateDev {
 };
 
 // geometry bounds for the gather / scatter kernels: the largest number of
-// blocks in a submatrix, leading dimension and block size
+// blocks in a submatrix, leading dimension and block size; for grouped
+// submatrices (members_max > 0) the largest member count and block-column
+// length nbj_max, and the member-wise scatter is used
 struct ScatterGeom {
   int nb_max, ld_max, bs_max;
+  int members_max = 0, nbj_max = 0;
 };
 
 // ---- kernel launchers (kernels.cu) ----
@@ -99,6 +116,11 @@ bool gather_rows_fits(int nb_max, int ld_max, int bs_max);
 cudaError_t launch_gather_rows(const PatternDev& g, const WaveDev& w, int nb_max, int ld_max, const double* K,
                                double mu, double* A, NsStateDev ns, int* flags, cudaStream_t st);
 size_t scatter_staged_smem(int nb_max, int ld_max, int bs_max);
+template <typename T>
+cudaError_t launch_scatter_members(const PatternDev& g, const WaveDev& w, NsStateDev ns, const T* buf0,
+                                   const T* buf1, double* D, double* trpart, int nbj_max, int members_max,
+                                   cudaStream_t st, const float* corr_a, const float* corr_b, const int* fallback,
+                                   double* sqpart);
 template <typename T>
 cudaError_t launch_scatter_staged(const PatternDev& g, const WaveDev& w, NsStateDev ns, const T* buf0,
                                   const T* buf1, double* D, double* trpart, int nb_max, int ld_max, int bs_max,

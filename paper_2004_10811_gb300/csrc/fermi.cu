@@ -391,7 +391,10 @@ submat_status Plan::fermi_dn_dmu(cudaStream_t st, double* out) {
   SM_CUDA(cudaMemcpyAsync(sq.data(), d_sqpart, 8 * size_t(nblk), cudaMemcpyDeviceToHost, st));
   SM_CUDA(cudaStreamSynchronize(st));
   double acc = 0.0;
-  for (int j = col_lo; j < col_hi; ++j) acc += tr[j] - sq[j];
+  // block columns evaluated: all of them for grouped plans (col_lo / col_hi
+  // count submatrices there), else the column range
+  const int j0 = grouped ? 0 : col_lo, j1 = grouped ? nblk : col_hi;
+  for (int j = j0; j < j1; ++j) acc += tr[j] - sq[j];
   *out = acc / opt.kT;
   return SUBMAT_OK;
 }

@@ -53,14 +53,14 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_rows(PatternDev g, Wa
   __shared__ float red_max[kGatherThreads / 32];
   __shared__ double red_fro[kGatherThreads / 32];
   const int s = blockIdx.y;
-  const int j = w.sub[s];
-  const int64_t rp0 = g.row_ptr[j];
-  const int nb = int(g.row_ptr[j + 1] - rp0);
+  const int j = w.sub[s];  // the submatrix (a block column, or a group of them)
+  const int64_t rp0 = g.sp[j];
+  const int nb = int(g.sp[j + 1] - rp0);
   const int n = w.n[s], ld = w.ld[s];
   double* Aj = A + w.off[s];
   for (int u = threadIdx.x; u < nb; u += blockDim.x) {
-    nbr[u] = g.col[rp0 + u];
-    loc[u] = g.locoff[rp0 + u];
+    nbr[u] = g.srows[rp0 + u];
+    loc[u] = g.sloc[rp0 + u];
   }
   if (threadIdx.x == 0) loc[nb] = n;
   __syncthreads();
@@ -220,7 +220,103 @@ __global__ void __launch_bounds__(256) k_scatter_staged(PatternDev g, WaveDev w,
   }
 }
 
+// Grouped submatrices (Section IV-C): block column j of D from the rows
+// mkoff .. mkoff + b_j - 1 of its group's S (by symmetry, the columns of
+// block j), one CTA per (member, submatrix).  Block (N(j)[u], j) of D takes
+// the rows dloc[p] .. of the submatrix, p its CSR position; entries are walked
+// in D's order (row-major blocks), reading b_j-long row runs of S.
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter_members(PatternDev g, WaveDev w, NsStateDev ns,
+                                                         const T* __restrict__ buf0, const T* __restrict__ buf1,
+                                                         double* __restrict__ D, double* trpart,
+                                                         const float* __restrict__ corr_a,
+                                                         const float* __restrict__ corr_b,
+                                                         const int* __restrict__ fallback, double* sqpart) {
+  extern __shared__ int smi[];
+  __shared__ double red[8], red2[8];
+  const int s = blockIdx.y;
+  const int q = w.sub[s];
+  const int m0 = g.mp[q];
+  if (int(blockIdx.x) >= g.mp[q + 1] - m0) return;
+  const int j = g.mcol[m0 + blockIdx.x];
+  const int kq = g.mkoff[m0 + blockIdx.x];
+  const int bj = g.bs[j];
+  const int ld = w.ld[s];
+  const int64_t rp0 = g.row_ptr[j];
+  const int nb = int(g.row_ptr[j + 1] - rp0);
+  const int nj = g.nsub[j];
+  int* locj = smi;            // [nb + 1] offsets of N(j)'s blocks in n_j-space
+  int* tp = locj + nb + 1;    // [nb] CSR position of block (N(j)[u], j)
+  int* dl = tp + nb;          // [nb] its row offset inside the submatrix
+  for (int u = threadIdx.x; u < nb; u += blockDim.x) {
+    locj[u] = g.locoff[rp0 + u];
+    tp[u] = g.tpos[rp0 + u];
+    dl[u] = g.dloc[tp[u]];
+  }
+  if (threadIdx.x == 0) locj[nb] = nj;
+  __syncthreads();
+  const T* S = (ns.par[s] ? buf1 : buf0) + w.off[s];
+  const bool correct = corr_a && !fallback[s];
+  const float* ca = corr_a ? corr_a + w.off[s] : nullptr;
+  const float* cb = corr_b ? corr_b + w.off[s] : nullptr;
+  double tr = 0.0, sq = 0.0;
+  for (int e = threadIdx.x; e < nj * bj; e += blockDim.x) {
+    const int x = e / bj, c = e - x * bj;
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (locj[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    const int r = x - locj[lo];
+    const int row = dl[lo] + r;
+    const int64_t si = int64_t(row) * ld + kq + c;
+    double sv = double(S[si]);
+    if (correct) sv -= f2d_exact(ca[si] + cb[si]);
+    const bool diag = row == kq + c;
+    const double v = (diag ? 0.5 : 0.0) - 0.5 * sv;
+    if (D) D[g.valptr[tp[lo]] + int64_t(r) * bj + c] = v;
+    if (diag) tr += v;
+    if (sqpart) sq = fma(v, v, sq);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = tr; red2[threadIdx.x >> 5] = sq; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0, acc2 = 0.0;
+    for (int k = 0; k < int(blockDim.x >> 5); ++k) { acc += red[k]; acc2 += red2[k]; }
+    trpart[j] = acc;
+    if (sqpart) sqpart[j] = acc2;
+  }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_scatter_members(const PatternDev& g, const WaveDev& w, NsStateDev ns, const T* buf0,
+                                   const T* buf1, double* D, double* trpart, int nbj_max, int members_max,
+                                   cudaStream_t st, const float* corr_a, const float* corr_b, const int* fallback,
+                                   double* sqpart) {
+  if (w.nsub <= 0) return cudaSuccess;
+  const size_t smem = size_t(3 * nbj_max + 1) * sizeof(int);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_scatter_members<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  k_scatter_members<T><<<dim3(unsigned(members_max), unsigned(w.nsub)), 256, smem, st>>>(
+      g, w, ns, buf0, buf1, D, trpart, corr_a, corr_b, fallback, sqpart);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_scatter_members<double>(const PatternDev&, const WaveDev&, NsStateDev, const double*,
+                                                    const double*, double*, double*, int, int, cudaStream_t,
+                                                    const float*, const float*, const int*, double*);
+template cudaError_t launch_scatter_members<float>(const PatternDev&, const WaveDev&, NsStateDev, const float*,
+                                                   const float*, double*, double*, int, int, cudaStream_t,
+                                                   const float*, const float*, const int*, double*);
 
 // Gather through k_gather_rows when its tables fit in shared memory (block
 // sizes below 512, as every workload here); the caller falls back otherwise.

@@ -37,18 +37,18 @@ __global__ void __launch_bounds__(256) k_gather(PatternDev g, WaveDev w, const i
   int* sm = colstride + ld_max;
   const int2 it = items[blockIdx.x];
   const int s = it.x, t = it.y;
-  const int j = w.sub[s];
-  const int64_t rp0 = g.row_ptr[j];
-  const int nb = int(g.row_ptr[j + 1] - rp0);
+  const int j = w.sub[s];  // the submatrix (a block column, or a group of them)
+  const int64_t rp0 = g.sp[j];
+  const int nb = int(g.sp[j + 1] - rp0);
   int* nbr = sm;            // N(j)
   int* blk = sm + nb;       // CSR position of block (i1, N(j)[u]) or -1
   int* loc = sm + 2 * nb;   // local offsets, loc[nb] = n
   const int n = w.n[s];
   const int ld = w.ld[s];
   for (int u = threadIdx.x; u < nb; u += blockDim.x) {
-    nbr[u] = g.col[rp0 + u];
+    nbr[u] = g.srows[rp0 + u];
     blk[u] = -1;
-    loc[u] = g.locoff[rp0 + u];
+    loc[u] = g.sloc[rp0 + u];
   }
   if (threadIdx.x == 0) loc[nb] = n;
   __syncthreads();
@@ -523,6 +523,9 @@ static cudaError_t scatter_impl(const PatternDev& g, const WaveDev& w, NsStateDe
                                 ScatterGeom geo, cudaStream_t st, const float* corr_a = nullptr,
                                 const float* corr_b = nullptr, const int* fallback = nullptr,
                                 double* sqpart = nullptr) {
+  if (geo.members_max > 0)  // groups of block columns per submatrix
+    return launch_scatter_members<T>(g, w, ns, buf0, buf1, D, trpart, geo.nbj_max, geo.members_max, st, corr_a,
+                                     corr_b, fallback, sqpart);
   // shared-memory staging of the extracted rows (coalesced reads of S and
   // whole-block writes of D), unless a block is too large to stage
   if (scatter_staged_smem(geo.nb_max, geo.ld_max, geo.bs_max) <= 200 * 1024)

@@ -156,8 +156,8 @@ static int64_t find_block(const std::vector<int64_t>& rp, const std::vector<int3
 // Split the evaluated block columns into waves whose dense buffers (bpe bytes
 // per element) fit `cap`, and build each wave's maps and work lists.
 submat_status Plan::build_waves(size_t bpe, size_t cap, std::vector<Wave>& waves, cudaStream_t st) {
-  std::vector<int64_t> ld_of(nblk);
-  for (int j = 0; j < nblk; ++j) ld_of[j] = (nsub[j] + 63) / 64 * 64;
+  std::vector<int64_t> ld_of(nq);
+  for (int j = 0; j < nq; ++j) ld_of[j] = (qn[j] + 63) / 64 * 64;
   waves.clear();
   {
     int first = col_lo;
@@ -168,7 +168,7 @@ submat_status Plan::build_waves(size_t bpe, size_t cap, std::vector<Wave>& waves
         const int64_t e = ld_of[first + cnt] * ld_of[first + cnt];
         if (cnt > 0 && size_t(elems + e) * bpe > cap) break;
         if (cnt == 0 && size_t(e) * bpe > cap) {
-          set_error("one submatrix (dim %d) needs %zu bytes > workspace cap %zu", nsub[first],
+          set_error("one submatrix (dim %d) needs %zu bytes > workspace cap %zu", qn[first],
                     size_t(e) * bpe, cap);
           return SUBMAT_ERR_OOM;
         }
@@ -217,10 +217,10 @@ submat_status Plan::build_waves(size_t bpe, size_t cap, std::vector<Wave>& waves
       const int j = wv.first + s;
       sub[s] = j;
       ld[s] = int32_t(ld_of[j]);
-      nn[s] = nsub[j];
+      nn[s] = qn[j];
       off[s] = wv.bucket_base[bucket_of[s]] + int64_t(slot_of[s]) * ld_of[j] * ld_of[j];
       wv.max_ld2 = std::max(wv.max_ld2, ld_of[j] * ld_of[j]);
-      const int nbj = int(row_ptr[j + 1] - row_ptr[j]);
+      const int nbj = int(grouped ? qsp[j + 1] - qsp[j] : row_ptr[j + 1] - row_ptr[j]);
       for (int t = 0; t < nbj; ++t) gitems.push_back(make_int2(s, t));
       const int T = int(ld_of[j] / 64);
       for (int a = 0; a < T; ++a)
@@ -274,8 +274,71 @@ submat_status Plan::build_waves(size_t bpe, size_t cap, std::vector<Wave>& waves
   return SUBMAT_OK;
 }
 
+// Submatrices shared by groups of block columns (Section IV-C): submatrix q
+// of a group G spans N(G), the ascending union of its members' row sets.
+submat_status Plan::build_groups(const int32_t* groups) {
+  int ng = 0;
+  for (int j = 0; j < nblk; ++j) {
+    if (groups[j] < 0 || groups[j] >= nblk) {
+      set_error("groups[%d] = %d outside [0, %d)", j, groups[j], nblk);
+      return SUBMAT_ERR_INVALID_ARG;
+    }
+    ng = std::max(ng, groups[j] + 1);
+  }
+  std::vector<std::vector<int>> mem(ng);
+  for (int j = 0; j < nblk; ++j) mem[groups[j]].push_back(j);
+  for (int q = 0; q < ng; ++q)
+    if (mem[q].empty()) {
+      set_error("group %d has no block column (group ids must be 0 .. ngroups - 1, all used)", q);
+      return SUBMAT_ERR_INVALID_ARG;
+    }
+  nq = ng;
+  grouped = true;
+  qn.assign(nq, 0);
+  qext.assign(nq, 0);
+  qsp.assign(nq + 1, 0);
+  qrows.clear();
+  qloc.clear();
+  qof.assign(nblk, 0);
+  qmp.assign(nq + 1, 0);
+  qmcol.clear();
+  qmkoff.clear();
+  dloc.assign(nnzb, 0);
+  qm_max = 1;
+  for (int q = 0; q < nq; ++q) {
+    std::vector<int32_t> rows;
+    for (int j : mem[q]) rows.insert(rows.end(), col.begin() + row_ptr[j], col.begin() + row_ptr[j + 1]);
+    std::sort(rows.begin(), rows.end());
+    rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+    std::vector<int32_t> lo(rows.size());
+    int64_t acc = 0;
+    for (size_t t = 0; t < rows.size(); ++t) { lo[t] = int32_t(acc); acc += bs[rows[t]]; }
+    if (acc > 32768) {
+      set_error("group %d spans a submatrix of dimension %lld > 32768", q, (long long)acc);
+      return SUBMAT_ERR_UNSUPPORTED;
+    }
+    auto local = [&](int i) {
+      return lo[size_t(std::lower_bound(rows.begin(), rows.end(), i) - rows.begin())];
+    };
+    qn[q] = int32_t(acc);
+    for (int j : mem[q]) {
+      qof[j] = q;
+      qmcol.push_back(j);
+      qmkoff.push_back(local(j));
+      qext[q] += bs[j];
+      for (int64_t t = row_ptr[j]; t < row_ptr[j + 1]; ++t) dloc[tpos[t]] = local(col[t]);
+    }
+    qm_max = std::max<int>(qm_max, int(mem[q].size()));
+    qrows.insert(qrows.end(), rows.begin(), rows.end());
+    qloc.insert(qloc.end(), lo.begin(), lo.end());
+    qsp[q + 1] = int64_t(qrows.size());
+    qmp[q + 1] = int32_t(qmcol.size());
+  }
+  return SUBMAT_OK;
+}
+
 submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, const int32_t* ci_,
-                          const submat_options* o, cudaStream_t st) {
+                          const submat_options* o, cudaStream_t st, const int32_t* groups) {
   nblk = nblk_;
   opt = *o;
   bs.assign(bs_, bs_ + nblk);
@@ -328,10 +391,32 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
     }
     nsub[j] = int32_t(acc);
     nb_max = std::max<int>(nb_max, int(row_ptr[j + 1] - row_ptr[j]));
+    nbj_max = nb_max;
     n_max = std::max<int>(n_max, nsub[j]);
     n_min = std::min<int>(n_min, nsub[j]);
     sum_n2 += double(acc) * acc;
     sum_n3 += double(acc) * acc * acc;
+  }
+  // submatrices: one per block column, or one per group
+  if (groups) {
+    SM_TRY(build_groups(groups));
+    nb_max = n_max = 0;
+    n_min = INT32_MAX;
+    sum_n2 = sum_n3 = 0.0;
+    for (int q = 0; q < nq; ++q) {
+      const double n = qn[q];
+      nb_max = std::max<int>(nb_max, int(qsp[q + 1] - qsp[q]));
+      n_max = std::max<int>(n_max, qn[q]);
+      n_min = std::min<int>(n_min, qn[q]);
+      sum_n2 += n * n;
+      sum_n3 += n * n * n;
+    }
+  } else {
+    nq = nblk;
+    qn = nsub;
+    qext = bs;
+    qof.resize(nblk);
+    for (int j = 0; j < nblk; ++j) qof[j] = j;
   }
   if (nb_max * 3 + 1 > 48 * 1024) {
     set_error("a submatrix spans %d blocks; at most 16383 are supported", nb_max);
@@ -351,7 +436,20 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
     SM_TRY(put(&d_ko, koff, st, "k offsets"));
     SM_TRY(put(&d_dp, diagpos, st, "diagonal positions"));
     SM_TRY(put(&d_rowof, rowof, st, "row of block"));
-    g = PatternDev{d_bs, d_rp, d_col, d_vp, d_loc, d_tp, d_ns, d_ko, d_dp};
+    g = PatternDev{d_bs, d_rp, d_col, d_vp, d_loc, d_tp, d_ns, d_ko, d_dp,
+                   d_rp, d_col, d_loc, nullptr, nullptr, nullptr, nullptr};
+    if (grouped) {
+      int64_t* d_sp; int32_t* d_sr; int32_t* d_sl; int32_t* d_mp; int32_t* d_mc; int32_t* d_mk; int32_t* d_dl;
+      SM_TRY(put(&d_sp, qsp, st, "submatrix rows"));
+      SM_TRY(put(&d_sr, qrows, st, "submatrix rows"));
+      SM_TRY(put(&d_sl, qloc, st, "submatrix offsets"));
+      SM_TRY(put(&d_mp, qmp, st, "group members"));
+      SM_TRY(put(&d_mc, qmcol, st, "group members"));
+      SM_TRY(put(&d_mk, qmkoff, st, "group member offsets"));
+      SM_TRY(put(&d_dl, dloc, st, "group block offsets"));
+      g.sp = d_sp; g.srows = d_sr; g.sloc = d_sl;
+      g.mp = d_mp; g.mcol = d_mc; g.mkoff = d_mk; g.dloc = d_dl;
+    }
   }
   // waves
   const size_t bpe = bytes_per_elem(opt.prec, opt.kT);
@@ -361,8 +459,9 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
     SM_CUDA(cudaMemGetInfo(&fre, &tot));
     cap = size_t(double(fre) * 0.8);
   }
+  // the evaluated submatrices (a column range without groups)
   col_lo = opt.col_end > opt.col_begin ? opt.col_begin : 0;
-  col_hi = opt.col_end > opt.col_begin ? opt.col_end : nblk;
+  col_hi = opt.col_end > opt.col_begin ? opt.col_end : nq;
   SM_TRY(build_waves(bpe, cap, waves, st));
   int64_t max_elems = 0;
   max_wave = 0;
@@ -390,26 +489,28 @@ submat_status Plan::build(int nblk_, const int32_t* bs_, const int64_t* rp_, con
   for (auto& e : ev) SM_CUDA(cudaEventCreate(&e));
   timer.on = opt.timing != 0;
   if (timer.on) {
-    // K values each submatrix reads: the stored blocks inside N(j) x N(j)
-    gather_bytes.assign(nblk, 0.0);
-    for (int j = 0; j < nblk; ++j) {
+    // K values each submatrix reads: the stored blocks inside N(q) x N(q)
+    const std::vector<int64_t>& sp = grouped ? qsp : row_ptr;
+    const std::vector<int32_t>& sr = grouped ? qrows : col;
+    gather_bytes.assign(nq, 0.0);
+    for (int j = 0; j < nq; ++j) {
       double acc = 0.0;
-      for (int64_t t = row_ptr[j]; t < row_ptr[j + 1]; ++t) {
-        const int i = col[t];
-        int64_t a = row_ptr[j], e = row_ptr[j + 1];
+      for (int64_t t = sp[j]; t < sp[j + 1]; ++t) {
+        const int i = sr[t];
+        int64_t a = sp[j], e = sp[j + 1];
         for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
-          while (a < e && col[a] < col[q]) ++a;
-          if (a < e && col[a] == col[q]) acc += double(bs[i]) * bs[col[q]];
+          while (a < e && sr[a] < col[q]) ++a;
+          if (a < e && sr[a] == col[q]) acc += double(bs[i]) * bs[col[q]];
         }
       }
       gather_bytes[j] = 8.0 * acc;
     }
   }
-  res_iters.assign(nblk, 0);
-  res_resid.assign(nblk, 0.0);
-  res_beta.assign(nblk, 0.0);
-  res_bound.assign(nblk, 0.0);
-  res_notconv.assign(nblk, 0);
+  res_iters.assign(nq, 0);
+  res_resid.assign(nq, 0.0);
+  res_beta.assign(nq, 0.0);
+  res_bound.assign(nq, 0.0);
+  res_notconv.assign(nq, 0);
   SM_CUDA(cudaStreamSynchronize(st));
   return SUBMAT_OK;
 }
@@ -601,7 +702,7 @@ submat_status Plan::scatter_timed(const Wave& wv, double bytes_per_entry,
   SM_TRY(timer.stop(tk, st));
   if (timer.on)
     for (int s = 0; s < wv.count; ++s)
-      stats.kernel_work[KC_SCATTER] += bytes_per_entry * double(wv.host_n[s]) * bs[wv.first + s];
+      stats.kernel_work[KC_SCATTER] += bytes_per_entry * double(wv.host_n[s]) * qext[wv.first + s];
   return SUBMAT_OK;
 }
 
@@ -623,9 +724,9 @@ void Plan::reset_stats() {
   int nmin = INT32_MAX, nmax = 0;
   double s2 = 0.0, s3 = 0.0;
   for (int j = col_lo; j < col_hi; ++j) {
-    const double n = nsub[j];
-    nmin = std::min(nmin, nsub[j]);
-    nmax = std::max(nmax, nsub[j]);
+    const double n = qn[j];
+    nmin = std::min(nmin, qn[j]);
+    nmax = std::max(nmax, qn[j]);
     s2 += n * n;
     s3 += n * n * n;
   }
@@ -647,7 +748,7 @@ void Plan::finish_stats(bool adjoint) {
     imin = std::min(imin, res_iters[j]);
     imax = std::max(imax, res_iters[j]);
     nc += res_notconv[j];
-    const double n3 = double(nsub[j]) * nsub[j] * nsub[j];
+    const double n3 = double(qn[j]) * qn[j] * qn[j];
     if (opt.kT > 0.0) flops += (adjoint ? 6.0 : 2.0) * n3 * res_iters[j];  // res_iters: products
     else flops += adjoint ? 12.0 * n3 * (res_iters[j] + 2) : (opt.iteration == 1 ? 6.0 : 4.0) * n3 * res_iters[j];
     rmax = std::max(rmax, res_resid[j]);
@@ -667,7 +768,7 @@ void Plan::finish_stats(bool adjoint) {
     } else if (opt.prec != SUBMAT_MIXED_BF16_REFINE) {
       // two products per iteration, 2 n^3 flops each at the standard count
       for (int j = col_lo; j < col_hi; ++j) {
-        const double n = nsub[j];
+        const double n = qn[j];
         stats.kernel_work[KC_SIMT] += 4.0 * n * n * n * res_iters[j];
       }
     }
@@ -788,9 +889,9 @@ void submat_options_default(submat_options* opt) {
   opt->prec = SUBMAT_FP64;
 }
 
-submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int64_t* row_ptr,
-                                 const int32_t* col_idx, const submat_options* opt, void* stream,
-                                 submat_plan** out) {
+static submat_status plan_create_impl(int nblk, const int32_t* block_sizes, const int64_t* row_ptr,
+                                      const int32_t* col_idx, const int32_t* groups, const submat_options* opt,
+                                      void* stream, submat_plan** out) {
   ABI_GUARD({
     submat::clear_error();
     if (!out) { submat::set_error("out is NULL"); return SUBMAT_ERR_INVALID_ARG; }
@@ -841,17 +942,38 @@ submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int
       submat::set_error("finite temperature runs on the FP64 and FP32 paths only");
       return SUBMAT_ERR_UNSUPPORTED;
     }
+    if (groups && (o.col_end > 0 || o.col_begin > 0)) {
+      submat::set_error("column ranges do not apply to grouped plans");
+      return SUBMAT_ERR_UNSUPPORTED;
+    }
     if (o.max_iter == 0) o.max_iter = 100;
     if (o.refine_rounds == 0) o.refine_rounds = 1;
     submat_status s = submat::validate_pattern_public(nblk, block_sizes, row_ptr, col_idx);
     if (s != SUBMAT_OK) return s;
     std::unique_ptr<submat_plan> p(new submat_plan());
     p->impl.tol_eff = o.tol > 0 ? o.tol : (o.prec == SUBMAT_FP64 ? 1e-14 : (o.prec == SUBMAT_FP32 ? 1e-6 : 2e-5));
-    s = p->impl.build(nblk, block_sizes, row_ptr, col_idx, &o, static_cast<cudaStream_t>(stream));
+    s = p->impl.build(nblk, block_sizes, row_ptr, col_idx, &o, static_cast<cudaStream_t>(stream), groups);
     if (s != SUBMAT_OK) return s;
     *out = p.release();
     return SUBMAT_OK;
   })
+}
+
+submat_status submat_plan_create(int nblk, const int32_t* block_sizes, const int64_t* row_ptr,
+                                 const int32_t* col_idx, const submat_options* opt, void* stream,
+                                 submat_plan** out) {
+  return plan_create_impl(nblk, block_sizes, row_ptr, col_idx, nullptr, opt, stream, out);
+}
+
+submat_status submat_plan_create_grouped(int nblk, const int32_t* block_sizes, const int64_t* row_ptr,
+                                         const int32_t* col_idx, const int32_t* groups,
+                                         const submat_options* opt, void* stream, submat_plan** out) {
+  if (!groups) {
+    submat::set_error("groups is NULL");
+    if (out) *out = nullptr;
+    return SUBMAT_ERR_INVALID_ARG;
+  }
+  return plan_create_impl(nblk, block_sizes, row_ptr, col_idx, groups, opt, stream, out);
 }
 
 submat_status submat_plan_destroy(submat_plan* plan) {
@@ -940,11 +1062,12 @@ submat_status submat_get_sub_stats(const submat_plan* plan, int32_t* dims, int32
                                    double* resid, double* beta) {
   if (!plan) { submat::set_error("plan is NULL"); return SUBMAT_ERR_INVALID_ARG; }
   const Plan& p = plan->impl;
-  for (int j = 0; j < p.nblk; ++j) {
-    if (dims) dims[j] = p.nsub[j];
-    if (iters) iters[j] = p.res_iters[j];
-    if (resid) resid[j] = p.res_resid[j];
-    if (beta) beta[j] = p.res_beta[j];
+  for (int j = 0; j < p.nblk; ++j) {  // block column j reports its submatrix q
+    const int q = p.qof[j];
+    if (dims) dims[j] = p.qn[q];
+    if (iters) iters[j] = p.res_iters[q];
+    if (resid) resid[j] = p.res_resid[q];
+    if (beta) beta[j] = p.res_beta[q];
   }
   return SUBMAT_OK;
 }

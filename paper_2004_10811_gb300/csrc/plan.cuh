@@ -135,7 +135,18 @@ struct Plan {
   std::vector<int32_t> bs, col, locoff, tpos, nsub, koff, diagpos;
   std::vector<int64_t> row_ptr, valptr, rowof;
   int nb_max = 0, n_max = 0, n_min = 0, bs_max = 1;
-  ScatterGeom geom(const Wave& wv) const { return ScatterGeom{nb_max, max_ld(wv), bs_max}; }
+  // submatrices: nq of them (nblk without groups); per submatrix q its
+  // dimension qn[q], extracted width qext[q] (sum of its members' block
+  // sizes), block rows qrows[qsp[q] .. qsp[q+1]) with local offsets qloc;
+  // qof[j] is the submatrix of block column j
+  bool grouped = false;
+  int nq = 0, qm_max = 1;
+  std::vector<int32_t> qn, qext, qrows, qloc, qof, qmp, qmcol, qmkoff, dloc;
+  std::vector<int64_t> qsp;
+  int nbj_max = 0;  // most blocks in one block column (the member scatter's tables)
+  ScatterGeom geom(const Wave& wv) const {
+    return ScatterGeom{nb_max, max_ld(wv), bs_max, grouped ? qm_max : 0, nbj_max};
+  }
   int col_lo = 0, col_hi = 0;      // evaluated block columns
   double sum_n2 = 0, sum_n3 = 0;
 
@@ -188,7 +199,8 @@ struct Plan {
   submat_status put(T** p, const std::vector<T>& v, cudaStream_t st, const char* what);
 
   submat_status build(int nblk, const int32_t* bs, const int64_t* rp, const int32_t* ci,
-                      const submat_options* o, cudaStream_t st);
+                      const submat_options* o, cudaStream_t st, const int32_t* groups = nullptr);
+  submat_status build_groups(const int32_t* groups);
   submat_status sign(const double* K, double mu, double* D, cudaStream_t st);
   submat_status sign_host(const double* K, double mu, double* D, cudaStream_t st);
   submat_status trace(const double* D, double* tr, cudaStream_t st);

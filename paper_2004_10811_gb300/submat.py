@@ -29,7 +29,7 @@ EXPORTS = (
     "submat_sign_host", "submat_trace", "submat_mu_search", "submat_sign_backward",
     "submat_plan_value_count", "submat_get_stats", "submat_get_sub_stats", "submat_last_error",
     "submat_debug_tc_gemm", "submat_dense_sign_noalloc", "submat_autotune", "submat_debug_slice_plan",
-    "submat_debug_mu_bisect", "submat_debug_fermi_poly",
+    "submat_debug_mu_bisect", "submat_debug_fermi_poly", "submat_plan_create_grouped",
 )
 
 
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
     lib.submat_options_default.argtypes = [C.POINTER(Options)]
     lib.submat_options_default.restype = None
     lib.submat_plan_create.argtypes = [C.c_int, i32p, i64p, i32p, C.POINTER(Options), vp, C.POINTER(vp)]
+    lib.submat_plan_create_grouped.argtypes = [C.c_int, i32p, i64p, i32p, i32p, C.POINTER(Options), vp,
+                                               C.POINTER(vp)]
     lib.submat_plan_destroy.argtypes = [vp]
     lib.submat_sign.argtypes = [vp, vp, C.c_double, vp, vp]
     lib.submat_sign_host.argtypes = [vp, dp, C.c_double, dp, vp]
@@ -115,7 +117,7 @@ def load(path: str = LIB_PATH):
                                             C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)]
     lib.submat_last_error.argtypes = []
     lib.submat_last_error.restype = C.c_char_p
-    for name in ("submat_plan_create", "submat_plan_destroy", "submat_sign", "submat_sign_host",
+    for name in ("submat_plan_create", "submat_plan_create_grouped", "submat_plan_destroy", "submat_sign", "submat_sign_host",
                  "submat_trace", "submat_mu_search", "submat_sign_backward", "submat_get_stats",
                  "submat_get_sub_stats", "submat_debug_tc_gemm", "submat_dense_sign_noalloc",
                  "submat_debug_slice_plan", "submat_debug_mu_bisect", "submat_debug_fermi_poly"):
@@ -161,7 +163,7 @@ class Plan:
     def __init__(self, block_sizes, row_ptr, col_idx, prec="fp64", tol=0.0, max_iter=0,
                  beta_mode=0, symmetrize=False, workspace_cap_bytes=0, refine_rounds=0,
                  timing=False, columns=None, hp_mode=0, tile_n_ns=0, tile_n_corr=0, tile_n_hp=0,
-                 iteration=0, adjoint_mode=0, kT=0.0, stream=None):
+                 iteration=0, adjoint_mode=0, kT=0.0, groups=None, stream=None):
         lib = load()
         self._lib = lib
         self.block_sizes = np.ascontiguousarray(block_sizes, dtype=np.int32)
@@ -188,10 +190,16 @@ class Plan:
             opt.col_begin, opt.col_end = int(columns[0]), int(columns[1])
         self.options = opt
         h = C.c_void_p()
-        _check(lib.submat_plan_create(len(self.block_sizes), _ptr(self.block_sizes, C.c_int32),
-                                      _ptr(self.row_ptr, C.c_int64), _ptr(self.col_idx, C.c_int32),
-                                      C.byref(opt), _stream(stream) if stream is not None else C.c_void_p(0),
-                                      C.byref(h)))
+        st = _stream(stream) if stream is not None else C.c_void_p(0)
+        if groups is None:
+            _check(lib.submat_plan_create(len(self.block_sizes), _ptr(self.block_sizes, C.c_int32),
+                                          _ptr(self.row_ptr, C.c_int64), _ptr(self.col_idx, C.c_int32),
+                                          C.byref(opt), st, C.byref(h)))
+        else:
+            self.groups = np.ascontiguousarray(groups, dtype=np.int32)
+            _check(lib.submat_plan_create_grouped(len(self.block_sizes), _ptr(self.block_sizes, C.c_int32),
+                                                  _ptr(self.row_ptr, C.c_int64), _ptr(self.col_idx, C.c_int32),
+                                                  _ptr(self.groups, C.c_int32), C.byref(opt), st, C.byref(h)))
         self._h = h
         self.value_count = int(lib.submat_plan_value_count(h))
 

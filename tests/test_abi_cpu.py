@@ -123,3 +123,27 @@ def test_bad_options_rejected_on_host(lib, opts, status, what):
     st, msg = _create(lib, [2, 2], [0, 2, 4], [0, 1, 0, 1], **opts)
     assert st == status, (st, msg)
     assert what in msg
+
+
+@pytest.mark.parametrize("groups,what", [
+    ([0, 2, 2], "has no block column"),
+    ([0, -1, 1], "outside"),
+    ([0, 3, 1], "outside"),
+])
+def test_bad_groups_rejected_on_host(lib, groups, what):
+    """Grouped plans (Section IV-C): group ids must be 0 .. ngroups - 1, all
+    used; checked on the host before any device allocation."""
+    from paper_2004_10811_gb300.submat import Options
+    bs = np.ascontiguousarray([2, 2, 2], np.int32)
+    rp = np.ascontiguousarray([0, 2, 4, 5], np.int64)
+    ci = np.ascontiguousarray([0, 1, 0, 1, 2], np.int32)
+    gr = np.ascontiguousarray(groups, np.int32)
+    opt = Options()
+    lib.submat_options_default(C.byref(opt))
+    h = C.c_void_p()
+    st = lib.submat_plan_create_grouped(3, bs.ctypes.data_as(C.POINTER(C.c_int32)),
+                                        rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                                        ci.ctypes.data_as(C.POINTER(C.c_int32)),
+                                        gr.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(opt), None, C.byref(h))
+    assert st == 1
+    assert what in lib.submat_last_error().decode()
