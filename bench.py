@@ -366,12 +366,14 @@ def main():
         # started 1.0 above the workload's mu, inside the virtual band, so
         # that the bracket has to be bisected down into the gap
         mu0 = m.mu + 1.0
-        mu_found, _Dm, status = plan.mu_search(K, m.n_el, mu0=mu0, tol=1e-9, max_steps=60, out=D)
+        mu_found, _Dm, status = plan.mu_search(K, m.n_el, mu0=mu0, tol=1e-9, max_steps=120, out=D)
         torch.cuda.synchronize()
         tm = time.perf_counter() - t0
-        steps = int(plan.stats()["mu_steps"])
-        mu_line = {"mu0": mu0, "mu": mu_found, "status": status, "s_total": tm, "steps": steps,
-                   "s_per_step": tm / max(1, steps), "n_el": float(m.n_el)}
+        stm = plan.stats()
+        steps, probes = int(stm["mu_steps"]), int(stm["mu_probes"])
+        mu_line = {"mu0": mu0, "mu": mu_found, "status": status, "s_total": tm, "full_evaluations": steps,
+                   "probes": probes, "builds_equivalent": tm / (t_dev / args.steps),
+                   "n_el": float(m.n_el)}
     plan.close()
 
     if rank != 0:

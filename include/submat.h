@@ -173,6 +173,7 @@ typedef struct {
   int32_t poly_degree;     /* finite temperature: the largest Chebyshev degree of the last
                               evaluation (iters_* then count its matrix products) */
   double  poly_trunc;      /* ... and its truncation bound, sum of |c_k| beyond the degree */
+  int32_t mu_probes;       /* probe evaluations of the last submat_mu_search (mixed plans) */
   double  dn_dmu;          /* finite temperature: dN/dmu = sum_j sum_{c in block j}
                               [f(a_j) (1 - f(a_j))]_cc / kT at the last evaluation's mu,
                               over the evaluated block columns (-L_f(a_j, I) summed; the
@@ -271,6 +272,14 @@ submat_status submat_trace(submat_plan* plan, const double* D_vals, double* tr,
  * At zero temperature Tr D(mu) is a staircase: if the bracket shrinks below
  * 1e-10 x the spectral bound without meeting tol, the call returns
  * MU_NO_ROOT with mu_out and D at the bracket end nearest n_el.
+ * Mixed plans probe each step first: the BF16x3 Newton-Schulz iterate alone
+ * (no correction, no FP64 fallback, at most 40 iterations), whose trace is
+ * within 1/2 sum_q b_q (r_q sqrt(n_q) + 1e-3) of the full result (r_q the
+ * final involution residual, b_q the extracted width); the probe decides the
+ * step when its count lies farther than that (and tol) from n_el.  After the
+ * first inconclusive probe only full evaluations follow, and D and mu_out
+ * always come from a full one.  max_steps counts both kinds
+ * (submat_stats.mu_steps: full, mu_probes: probes).
  * NOT_CONVERGED: the step cap was reached (mu_out and D at the evaluation
  * nearest n_el), or the evaluation at mu_out left some submatrix
  * unconverged (D written, see submat_get_stats); a submatrix that diverged

@@ -70,15 +70,19 @@ submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, int per_acc
  *   n_el, mu0, tol, max_steps   as in submat_mu_search
  *   bound_scale  > 0; 1 gives the exact bound, below 1 a bound that
  *              underestimates the spectrum (the bracket must then grow)
+ *   probe_err  >= 0; with probe_err > 0 a probe returns N off by probe_err
+ *              (alternating sides) with the bound probe_err, as the mixed
+ *              path's probes do with their certified bound
  *   mu_out     host double: the final mu
- *   steps      host int32: evaluations of N
+ *   steps      host int32: full evaluations of N
+ *   probes     host int32 or NULL: probe evaluations
  *   n_out      host double or NULL: N(mu_out)
  * Returns what submat_mu_search returns: OK, MU_NO_ROOT, NOT_CONVERGED, or
  * INVALID_ARG.
  */
 submat_status submat_debug_mu_bisect(const double* levels, int nlev, double n_el, double mu0, double tol,
-                                     int max_steps, double bound_scale, double* mu_out, int32_t* steps,
-                                     double* n_out);
+                                     int max_steps, double bound_scale, double probe_err, double* mu_out,
+                                     int32_t* steps, int32_t* probes, double* n_out);
 
 /*
  * Host-only (no GPU needed): the finite-temperature polynomial (Section IV-F,

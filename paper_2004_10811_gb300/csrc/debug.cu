@@ -184,12 +184,13 @@ extern "C" submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, 
 }
 
 extern "C" submat_status submat_debug_mu_bisect(const double* levels, int nlev, double n_el, double mu0,
-                                                double tol, int max_steps, double bound_scale, double* mu_out,
-                                                int32_t* steps, double* n_out) {
+                                                double tol, int max_steps, double bound_scale, double probe_err,
+                                                double* mu_out, int32_t* steps, int32_t* probes,
+                                                double* n_out) {
   using namespace submat;
   clear_error();
   if (nlev < 0 || (nlev > 0 && !levels) || !mu_out || !steps || max_steps < 1 || !(tol > 0) ||
-      !std::isfinite(n_el) || !std::isfinite(mu0) || !(bound_scale > 0)) {
+      !std::isfinite(n_el) || !std::isfinite(mu0) || !(bound_scale > 0) || !(probe_err >= 0)) {
     set_error("bad argument to submat_debug_mu_bisect");
     return SUBMAT_ERR_INVALID_ARG;
   }
@@ -211,10 +212,20 @@ extern "C" submat_status submat_debug_mu_bisect(const double* levels, int nlev, 
     for (int i = 0; i < nlev; ++i) b = std::max(b, std::fabs(levels[i] - mu0));
     return b * bound_scale;
   };
+  // probe: the count off by up to probe_err (alternating sides), with that bound
+  int calls = 0;
+  MuProbe probe;
+  if (probe_err > 0)
+    probe = [&](double mu, double* n, double* b) -> submat_status {
+      *n = count(mu) + ((calls++ & 1) ? probe_err : -probe_err);
+      *b = probe_err;
+      return SUBMAT_OK;
+    };
   MuSearchOut r;
-  const submat_status s = mu_bisect(eval, bound, n_el, mu0, tol, max_steps, &r);
+  const submat_status s = mu_bisect(eval, bound, n_el, mu0, tol, max_steps, &r, probe);
   *mu_out = r.mu;
   *steps = r.steps;
+  if (probes) *probes = r.probes;
   if (n_out) *n_out = count(r.mu);
   return s;
 }

@@ -37,23 +37,46 @@ submat_status Plan::sign_host(const double* K, double mu, double* D, cudaStream_
 // the returned mu, so that its side effects (D) match.
 submat_status mu_bisect(const std::function<submat_status(double, double*)>& eval,
                         const std::function<double()>& bound, double n_el, double mu0, double tol,
-                        int max_steps, MuSearchOut* out) {
+                        int max_steps, MuSearchOut* out, const MuProbe& probe) {
   MuSearchOut& r = *out;
   r = MuSearchOut{};
+  // a probe is conclusive when N lies on one side of n_el, outside tol,
+  // whatever its error
+  bool probing = bool(probe);
+  bool last_probe = false;  // the latest evaluation was a probe (D not final)
+  auto try_probe = [&](double mu, int* side) -> submat_status {
+    *side = 0;
+    if (!probing) return SUBMAT_OK;
+    double np = 0, b = 0;
+    SM_TRY(probe(mu, &np, &b));
+    ++r.probes;
+    last_probe = true;
+    if (std::fabs(np - n_el) > b + tol * std::fabs(n_el)) *side = np < n_el ? -1 : 1;
+    else probing = false;  // near n_el: full evaluations from here on
+    return SUBMAT_OK;
+  };
   double n0 = 0;
-  SM_TRY(eval(mu0, &n0));
-  ++r.steps;
+  int side0 = 0;
+  SM_TRY(try_probe(mu0, &side0));
   double last_mu = mu0;
-  r.mu = mu0;
-  r.n_best = n0;
-  if (std::fabs(n0 - n_el) <= tol * std::fabs(n_el)) return SUBMAT_OK;
+  if (side0 == 0) {
+    SM_TRY(eval(mu0, &n0));
+    ++r.steps;
+    last_probe = false;
+    r.mu = mu0;
+    r.n_best = n0;
+    if (std::fabs(n0 - n_el) <= tol * std::fabs(n_el)) return SUBMAT_OK;
+  } else {
+    n0 = side0 < 0 ? -HUGE_VAL : HUGE_VAL;  // only its side is known
+    last_mu = HUGE_VAL;
+  }
   const double bmax = bound();
   double span = 1.01 * bmax + 1e-12;
   const bool up = n0 < n_el;
   double lo, hi;
   if (up) { lo = mu0; hi = mu0 + span; } else { hi = mu0; lo = mu0 - span; }
   double far = up ? hi : lo;  // not evaluated
-  double best_mu = mu0, best_n = n0;
+  double best_mu = side0 == 0 ? mu0 : HUGE_VAL, best_n = n0;
   double width_floor = 1e-10 * std::max(bmax, 1e-300);
   auto consider = [&](double mu, double nm) {
     last_mu = mu;
@@ -62,13 +85,14 @@ submat_status mu_bisect(const std::function<submat_status(double, double*)>& eva
     if (std::fabs(nm - n_el) <= std::fabs(best_n - n_el)) { best_mu = mu; best_n = nm; }
   };
   bool far_ok = false;  // N(far) has been seen on the other side of n_el
-  while (r.steps < max_steps && (hi - lo) > width_floor) {
+  while (r.steps + r.probes < max_steps && (hi - lo) > width_floor) {
     // the bisection has closed in on the unevaluated far end (the last eighth
     // of the bracket): check that it holds n_el, else move the bracket outward
     if (!far_ok && (up ? far - lo : hi - far) <= 0.125 * span) {
       double nf = 0;
       SM_TRY(eval(far, &nf));
       ++r.steps;
+      last_probe = false;
       consider(far, nf);
       if (std::fabs(nf - n_el) <= tol * std::fabs(n_el)) {
         r.mu = far;
@@ -86,9 +110,18 @@ submat_status mu_bisect(const std::function<submat_status(double, double*)>& eva
       continue;
     }
     const double mid = 0.5 * (lo + hi);
+    int side = 0;
+    SM_TRY(try_probe(mid, &side));
+    if (side != 0) {  // the probe decides this step
+      ++r.probe_steps;
+      if (side < 0) lo = mid; else hi = mid;
+      if (up ? hi != far : lo != far) far_ok = true;
+      continue;
+    }
     double nm = 0;
     SM_TRY(eval(mid, &nm));
     ++r.steps;
+    last_probe = false;
     consider(mid, nm);
     if (std::fabs(nm - n_el) <= tol * std::fabs(n_el)) {
       r.mu = mid;
@@ -99,7 +132,14 @@ submat_status mu_bisect(const std::function<submat_status(double, double*)>& eva
     if (nm < n_el) lo = mid; else hi = mid;
     if (up ? hi != far : lo != far) far_ok = true;  // a mid value on the far side was seen
   }
-  if (last_mu != best_mu) {
+  if (best_mu == HUGE_VAL || !std::isfinite(best_n)) {  // only probes so far: one full evaluation
+    best_mu = 0.5 * (lo + hi);
+    SM_TRY(eval(best_mu, &best_n));
+    ++r.steps;
+    last_probe = false;
+    last_mu = best_mu;
+  }
+  if (last_mu != best_mu || last_probe) {
     double nb = 0;
     SM_TRY(eval(best_mu, &nb));
     ++r.steps;
@@ -210,10 +250,32 @@ submat_status Plan::mu_search(const double* K, double n_el, double mu0, double t
     for (int j = col_lo; j < col_hi; ++j) bmax = std::max(bmax, res_bound[j]);
     return bmax;
   };
+  // Mixed plans probe first: the BF16x3 iterate without correction or FP64
+  // fallback (a fraction of a build, and none of the slow fallbacks that
+  // evaluations inside a band need).  Its trace error is bounded per block
+  // column c of submatrix q: with X the final iterate, S = sign(a) and
+  // e_l = x_l^2 - 1 in the eigenbasis, |(X - S)_cc| <= sum_l Q_cl^2 |e_l|
+  // <= ||X^2 - I||_F = r_q sqrt(n_q) (Newton-Schulz keeps signs and stays in
+  // [-1, 1]), plus 1e-3 for the BF16x3 rounding; N = sum_c (1 - S_cc) / 2.
+  MuProbe probe;
+  if (opt.prec == SUBMAT_MIXED_BF16_REFINE)
+    probe = [&](double mu, double* n, double* bnd) -> submat_status {
+      probe_mode = true;
+      const submat_status ps = sign(K, mu, D, st);
+      probe_mode = false;
+      if (ps != SUBMAT_OK && ps != SUBMAT_ERR_NOT_CONVERGED) return ps;
+      SM_TRY(trace(D, n, st));
+      double b = 0.0;
+      for (int q = col_lo; q < col_hi; ++q)
+        b += 0.5 * qext[q] * (res_resid[q] * std::sqrt(double(qn[q])) + 1e-3);
+      *bnd = (last_flags & FLAG_DIVERGED) ? HUGE_VAL : b;
+      return SUBMAT_OK;
+    };
   MuSearchOut r;
-  submat_status s = mu_bisect(eval, bound, n_el, mu0, tol, max_steps, &r);
-  // every evaluation resets the statistics: the step count is set last
+  submat_status s = mu_bisect(eval, bound, n_el, mu0, tol, max_steps, &r, probe);
+  // every evaluation resets the statistics: the step counts are set last
   stats.mu_steps = r.steps;
+  stats.mu_probes = r.probes;
   if (s == SUBMAT_OK || s == SUBMAT_ERR_MU_NO_ROOT || s == SUBMAT_ERR_NOT_CONVERGED) *mu_out = r.mu;
   if ((s == SUBMAT_OK || s == SUBMAT_ERR_MU_NO_ROOT) && last == SUBMAT_ERR_NOT_CONVERGED) {
     set_error("mu search ended at mu = %.17g, where %d submatrices did not converge (D written)", r.mu,

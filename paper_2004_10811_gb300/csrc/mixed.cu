@@ -1072,7 +1072,10 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     // W from the squaring, Z = 3/8 W^2 + 5/6 I from a second symmetric product.
     const bool third = opt.iteration == 1;
     int cur = 0;
-    for (int k = 0; k < opt.max_iter; ++k) {
+    // a probe (mu search) caps the iteration: its unconverged submatrices
+    // only widen the trace bound
+    const int ns_cap = probe_mode ? std::min(opt.max_iter, kProbeMaxIter) : opt.max_iter;
+    for (int k = 0; k < ns_cap; ++k) {
       TcGemmParams g1 = tc(SYM, NSYM, cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0,
                            cur ? MS_XH1 : MS_XH0, cur ? MS_XL1 : MS_XL0, 1, third ? 1.0f : -0.5f, 0.0f);
       g1.diag = third ? -5.0f / 3.0f : 1.5f;
@@ -1088,7 +1091,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         const CertLinear lin{1, {b.X[0][0], nullptr, nullptr}, {b.X[0][1], nullptr, nullptr}};
         SM_CUDA(launch_certify(wv.dev, ns, sq, lin, cert_limits(third), max_ld(wv), d_flags + 2, st));
       }
-      SM_CUDA(launch_ns_update(wv.dev, ns, tol_eff, floor_thr, opt.max_iter, d_flags, st));
+      SM_CUDA(launch_ns_update(wv.dev, ns, tol_eff, floor_thr, ns_cap, d_flags, st));
       int z_hi = MS_YH, z_lo = MS_YL;
       if (third) {  // Z = 3/8 W^2 + 5/6 I into H's buffers
         TcGemmParams gw = tc(SYM, NSYM, MS_YH, MS_YL, MS_YH, MS_YL, 1, 0.375f, 0.0f);
@@ -1118,6 +1121,19 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       if (reinterpret_cast<int*>(h_pinned)[0] == 0) break;
     }
     SM_CUDA(cudaEventRecord(ev[2], st));
+
+    if (probe_mode) {
+      // the BF16x3 iterate as it stands (no correction, no FP64 fallback):
+      // S = hi + lo, extracted as it is; the trace bound comes from the
+      // submatrices' final residuals (Plan::mu_search)
+      SM_CUDA(cudaMemsetAsync(ms->submax, 0, sizeof(unsigned long long) * max_wave, st));
+      k_widen<<<eg, 256, 0, st>>>(wv.dev, ns.par, b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.S, ms->submax);
+      SM_KCHECK();
+      SM_CUDA(cudaEventRecord(ev[3], st));
+      SM_CUDA(launch_scatter_f64(g, wv.dev, ns, b.S, b.S, D, d_trpart, geom(wv), st));
+      SM_TRY(collect_wave(wv, st));
+      continue;
+    }
 
     // ---- correction rounds ----
     tc_class = KC_TC_REF;

@@ -18,6 +18,7 @@ const char* last_error();
 size_t mixed_bytes_per_elem();
 size_t adjoint_tc_bytes_per_elem();
 constexpr int kPowerIters = 10;  // power steps of the spectral estimate
+constexpr int kProbeMaxIter = 40;  // Newton-Schulz cap of a mu-search probe
 void free_mixed(void* state);
 void free_adjoint_tc(void* state);
 
@@ -39,11 +40,18 @@ int slice_max_slices();
 // evaluation was made.
 struct MuSearchOut {
   double mu = 0, n_best = 0, lo = 0, hi = 0;
-  int steps = 0;
+  int steps = 0;        // full evaluations
+  int probes = 0;       // probe evaluations
+  int probe_steps = 0;  // bisection steps that a probe decided
 };
+// probe (may be empty): a cheaper evaluation returning N_p and a bound B with
+// |N(mu) - N_p| <= B; a bisection step takes the probe's side when
+// |N_p - n_el| > B, and after the first inconclusive probe only full
+// evaluations follow.
+using MuProbe = std::function<submat_status(double, double*, double*)>;
 submat_status mu_bisect(const std::function<submat_status(double, double*)>& eval,
                         const std::function<double()>& bound, double n_el, double mu0, double tol,
-                        int max_steps, MuSearchOut* out);
+                        int max_steps, MuSearchOut* out, const MuProbe& probe = MuProbe());
 
 
 // Finite temperature (fermi.cu): the Chebyshev series of tanh(c x) on
@@ -188,6 +196,7 @@ struct Plan {
   std::vector<int> res_iters, res_notconv;
   std::vector<double> res_resid, res_beta, res_bound;  // res_bound: min(max row abs-sum, ||a||_F)
   int last_flags = 0;              // status word of the last read_flags
+  bool probe_mode = false;         // mixed path: stop after the BF16x3 iteration (mu-search probe)
   submat_stats stats{};
   KernelTimer timer;
   long long launches_at_start = 0;

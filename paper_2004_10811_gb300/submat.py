@@ -65,7 +65,8 @@ class Stats(C.Structure):
         ("ms_scatter", C.c_double), ("workspace_bytes", C.c_size_t), ("launches", C.c_int64),
         ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_int32 * 8), ("kernel_work", C.c_double * 8),
         ("kernel_exec", C.c_double * 8), ("mu_steps", C.c_int32), ("scale_reduced", C.c_int32),
-        ("poly_degree", C.c_int32), ("poly_trunc", C.c_double), ("dn_dmu", C.c_double),
+        ("poly_degree", C.c_int32), ("poly_trunc", C.c_double), ("mu_probes", C.c_int32),
+        ("dn_dmu", C.c_double),
     ]
 
     def as_dict(self):
@@ -111,8 +112,8 @@ def load(path: str = LIB_PATH):
     lib.submat_debug_slice_plan.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int,
                                             C.POINTER(C.c_int32)]
     lib.submat_debug_mu_bisect.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
-                                           C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int32),
-                                           C.POINTER(C.c_double)]
+                                           C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_int32), C.POINTER(C.c_double)]
     lib.submat_debug_fermi_poly.argtypes = [C.c_double, C.c_double, C.c_int, vp, C.c_int,
                                             C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)]
     lib.submat_last_error.argtypes = []
@@ -354,19 +355,22 @@ def debug_slice_plan(nx, ny, sym_pairs, per_acc):
     return out[:n.value]
 
 
-def debug_mu_bisect(levels, n_el, mu0, tol=1e-9, max_steps=60, bound_scale=1.0):
+def debug_mu_bisect(levels, n_el, mu0, tol=1e-9, max_steps=60, bound_scale=1.0, probe_err=0.0,
+                    with_probes=False):
     """Host-only test hook (include/submat_debug.h): the mu search's bisection on
     the electron count of the given levels, with the spectral bound scaled by
-    ``bound_scale``.  Returns (mu, steps, N(mu), status)."""
+    ``bound_scale`` and, with ``probe_err`` > 0, probes off by that much.
+    Returns (mu, steps, N(mu), status), and the probe count with_probes."""
     lib = load()
     lv = np.ascontiguousarray(levels, dtype=np.float64)
     mu, n = C.c_double(), C.c_double()
-    steps = C.c_int32()
+    steps, probes = C.c_int32(), C.c_int32()
     st = lib.submat_debug_mu_bisect(lv.ctypes.data_as(C.c_void_p), len(lv), float(n_el), float(mu0),
-                                    float(tol), int(max_steps), float(bound_scale), C.byref(mu),
-                                    C.byref(steps), C.byref(n))
+                                    float(tol), int(max_steps), float(bound_scale), float(probe_err),
+                                    C.byref(mu), C.byref(steps), C.byref(probes), C.byref(n))
     _check(st, allow=(6, 7))
-    return mu.value, steps.value, n.value, STATUS[st]
+    out = (mu.value, steps.value, n.value, STATUS[st])
+    return out + (probes.value,) if with_probes else out
 
 
 NOALLOC_MAX_N = 512

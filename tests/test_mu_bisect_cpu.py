@@ -95,3 +95,23 @@ def test_unreachable_target_is_rejected(sm):
         with pytest.raises(sm.SubmatError) as ei:
             sm.debug_mu_bisect(lv, target, 0.0, tol=1e-9)
         assert ei.value.name == "INVALID_ARG"
+
+
+@pytest.mark.parametrize("target,mu0,tol", [(40.0, 1.2, 1e-9), (40.5, 1.2, 1e-12), (40.0, -0.95, 1e-9),
+                                            (70.0, -0.9, 1e-9)])
+def test_probes_keep_the_result_and_save_full_evaluations(sm, target, mu0, tol):
+    """Probes off by up to 3 electrons (with that bound) decide the steps far
+    from the target; the search ends at the same mu and status as without
+    them, with fewer full evaluations, and the returned mu's N is full."""
+    lv = gapped_levels(6)
+    ref = sm.debug_mu_bisect(lv, target, mu0, tol=tol, max_steps=200)
+    mu, steps, n, status, probes = sm.debug_mu_bisect(lv, target, mu0, tol=tol, max_steps=200, probe_err=3.0,
+                                                      with_probes=True)
+    assert status == ref[3]
+    assert n == count(lv, mu)
+    if status == "OK":
+        assert abs(n - target) <= tol * target
+    else:
+        assert abs(mu - ref[0]) <= 1e-9 * np.max(np.abs(lv - mu0)) * 4
+    assert probes > 0
+    assert steps < ref[1]
