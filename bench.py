@@ -220,6 +220,74 @@ def sweep(args):
                           "fp64_fallback_submatrices": int(st["refine_fallback"])}), flush=True)
 
 
+def shard_run(args, m, desc, pkg, dist, rank, world, local, dev):
+    """Strong scaling (shard.py): every rank holds the blocks of its own block
+    rows, a device halo exchange brings what its chunk's submatrices need, the
+    chunk is evaluated by a column-range plan and Tr D is allreduced.  A step
+    is that whole sequence; the time is the maximum over ranks."""
+    import numpy as np
+    import torch
+    from paper_2004_10811_gb300.shard import ShardedPattern, gpu_solver, sharded_density
+
+    class _Single:  # the world-size-1 stand-ins for the collectives
+        P2POp = None
+
+        @staticmethod
+        def all_reduce(t):
+            return t
+
+        @staticmethod
+        def all_gather_object(out, obj):
+            out[0] = obj
+
+        @staticmethod
+        def barrier():
+            pass
+
+    comm = dist if dist is not None else _Single
+    sp = ShardedPattern(m.block_sizes, m.row_ptr, m.col_idx, rank, world)
+    owned = np.zeros_like(m.vals)
+    for p in np.nonzero(sp.owner == rank)[0]:
+        owned[sp.vp[p]:sp.vp[p + 1]] = m.vals[sp.vp[p]:sp.vp[p + 1]]
+    K0 = torch.from_numpy(owned).to(dev)
+    solve = gpu_solver(sp, device=dev, prec=args.prec)
+    K = K0.clone()
+    for _ in range(max(1, args.warmup)):
+        K.copy_(K0)
+        sharded_density(sp, K, m.mu, solve, comm, exchange=world > 1)
+    comm.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            K.copy_(K0)
+            _d, tr = sharded_density(sp, K, m.mu, solve, comm, exchange=world > 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    comm.barrier()
+    t = e0.elapsed_time(e1) / 1e3
+    tt = torch.tensor([t], device=dev)
+    comm.all_reduce(tt, op=dist.ReduceOp.MAX) if dist is not None else None
+    t = float(tt.item())
+    clocks = clk.summary()
+    if rank == 0:
+        value = t / args.steps
+        line = {"metric": METRIC, "value": value, "unit": "s/build", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * value, "higher_is_better": False,
+                "scaling": "strong", "vs_baseline": None,
+                "dtype": "bf16x3+f64" if args.prec == "mixed" else args.prec, "data": "synthetic",
+                "config": {"workload": args.workload, "description": desc, "prec": args.prec,
+                           "parallelism": f"{world} ranks, Sigma n^3-balanced column chunks, device halo "
+                                          "exchange and trace allreduce", "chunk_rank0": list(sp.chunk)},
+                "trace": tr, "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                                        "reasons": clocks["reasons"]}}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -233,6 +301,10 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=0,
                     help="block columns timed on the FP64 path (0: the whole build)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the whole-build FP32 path timing")
+    ap.add_argument("--shard", action="store_true",
+                    help="strong scaling: all ranks share one system, each evaluates a Sigma n^3-balanced "
+                         "chunk of block columns after a device halo exchange (shard.py); default is weak "
+                         "scaling, one seeded instance per rank")
     ap.add_argument("--group-size", type=int, default=2,
                     help="block columns per submatrix for the grouped key (periodic k-means on the molecule "
                          "centres, Section IV-C); 0 skips it")
@@ -265,8 +337,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     from synth import make_config
-    # weak scaling: each rank builds its own seeded instance of the workload
-    m = make_config(cfg_index, seed=None if rank == 0 else 1000 + cfg_index + 7919 * rank)
+    # weak scaling: each rank builds its own seeded instance of the workload;
+    # --shard: one instance shared by all ranks
+    m = make_config(cfg_index, seed=None if (rank == 0 or args.shard) else 1000 + cfg_index + 7919 * rank)
 
     if args.impl == "reference":
         reference_arm(args, m, desc)
@@ -290,6 +363,9 @@ def main():
 
     peaks, peak_src = load_peaks()
     dev = torch.device("cuda", local)
+    if args.shard:
+        shard_run(args, m, desc, pkg, dist, rank, world, local, dev)
+        return
     K = torch.from_numpy(m.vals).to(dev)
     D = torch.empty_like(K)
     columns = tuple(int(x) for x in args.columns.split(":")) if args.columns else None

@@ -6,17 +6,21 @@ into contiguous chunks, balanced on the O(n_j^3) cost of their submatrices
 total / nranks, every rank gets at least one column).  Contiguous chunks keep
 neighbouring columns -- which share most blocks -- on one rank (Section IV-B2).
 
-Data movement, once per pattern and per K (Section IV-B1: every block goes
-once to each rank that needs it):
+Data movement (Section IV-B1: every block goes once to each rank that needs it):
   * a rank owns the K blocks of the block rows of its chunk;
   * it needs the blocks of every submatrix it evaluates: the halo;
-  * one all-to-all moves the halo blocks; assembly is then local.
-D's block columns are disjoint across ranks (no reduction).  The trace and
-the electron count of the mu search are a sum-allreduce of one double; the
-adjoint's Kbar contributions overlap and are sum-reduced.
+  * one exchange of point-to-point messages moves the halo blocks, once per
+    K; assembly is then local.
+Everything lives in device memory on the rank's GPU: the value index lists
+are built once per pattern, halo values are packed and unpacked on the
+device, and the messages are device tensors (NCCL; gloo ranks use the same
+code with CPU tensors).  D's block columns are disjoint across ranks (no
+reduction); Tr D and the mu search's electron count (and dN/dmu at finite
+temperature) are sum-allreduces of scalars; the adjoint's Kbar contributions
+overlap and are sum-reduced in place.
 
-The local evaluation is a ``Plan`` with ``columns=(lo, hi)``; tests may pass
-any callable with the same contract.
+The local evaluation is a ``Plan`` with ``columns=(lo, hi)``
+(``gpu_solver``); tests may pass any callable with the same contract.
 """
 from __future__ import annotations
 
@@ -82,6 +86,13 @@ def block_value_ranges(block_sizes, row_ptr, col_idx):
     return vp
 
 
+def value_index(vp, blocks):
+    """Flat value positions of the given CSR blocks, in block order."""
+    if len(blocks) == 0:
+        return np.zeros(0, dtype=np.int64)
+    return np.concatenate([np.arange(vp[p], vp[p + 1], dtype=np.int64) for p in blocks])
+
+
 class ShardedPattern:
     """Per-rank view of one pattern: chunk, owned blocks, halo, exchange lists."""
 
@@ -94,6 +105,7 @@ class ShardedPattern:
         self.chunks = partition_columns(dims, nranks)
         self.chunk = self.chunks[rank]
         self.vp = block_value_ranges(self.block_sizes, self.row_ptr, self.col_idx)
+        self.nvals = int(self.vp[-1])
         # owner of every block = the rank whose chunk holds its block row
         rows = np.repeat(np.arange(len(self.block_sizes)), np.diff(self.row_ptr))
         bounds = np.array([c[0] for c in self.chunks] + [len(self.block_sizes)])
@@ -102,6 +114,9 @@ class ShardedPattern:
         # what this rank receives from each peer, and sends to each peer
         self.recv = [self.halo[self.owner[self.halo] == r] for r in range(nranks)]
         self.send = None  # filled by exchange_lists()
+        # this rank's block columns of D (flat value positions)
+        self.mine = np.nonzero((self.col_idx >= self.chunk[0]) & (self.col_idx < self.chunk[1]))[0]
+        self._dev = {}
 
     def exchange_lists(self, dist):
         """Tell every owner which of its blocks this rank needs (one object
@@ -113,6 +128,23 @@ class ShardedPattern:
         self.send = [np.asarray(every[q][self.rank], dtype=np.int64) for q in range(self.nranks)]
         return self.send
 
+    def device_index(self, device, dist=None):
+        """Flat value positions, as int64 tensors on `device`, of what goes to
+        and comes from every peer (built once per pattern and device)."""
+        import torch
+        key = str(device)
+        if key not in self._dev:
+            if self.send is None:
+                self.exchange_lists(dist)
+            t = lambda a: torch.from_numpy(a).to(device)
+            self._dev[key] = {
+                "send": [t(value_index(self.vp, self.send[q])) for q in range(self.nranks)],
+                "recv": [t(value_index(self.vp, self.recv[q])) for q in range(self.nranks)],
+                "mine": t(value_index(self.vp, self.mine)),
+            }
+        return self._dev[key]
+
+    # host helpers (tests, and callers that hold NumPy arrays)
     def gather_values(self, vals, blocks):
         if len(blocks) == 0:
             return np.zeros(0)
@@ -126,94 +158,166 @@ class ShardedPattern:
             o += b - a
 
 
-def exchange_halo(sp, owned_vals, dist):
-    """All-to-all of halo blocks.  ``owned_vals`` is a full-length value array
-    holding this rank's owned blocks (other entries ignored).  Returns a
-    full-length array holding every block this rank needs."""
+def exchange_halo(sp, K_local, dist):
+    """Moves the halo blocks between ranks, in place: ``K_local`` (a
+    full-length float64 tensor on this rank's device: its owned blocks filled,
+    the rest anything) receives every block this rank's submatrices need.
+    Packing and unpacking run on the device; the messages are batched
+    point-to-point sends and receives (NCCL with CUDA tensors, gloo with CPU
+    tensors).  Returns K_local."""
     import torch
-    if sp.send is None:
-        sp.exchange_lists(dist)
-    send = [torch.from_numpy(sp.gather_values(owned_vals, sp.send[q])) for q in range(sp.nranks)]
-    sizes = [int(sum(sp.vp[p + 1] - sp.vp[p] for p in sp.recv[q])) for q in range(sp.nranks)]
-    recv = [torch.empty(sizes[q], dtype=torch.float64) for q in range(sp.nranks)]
-    # point-to-point pairs (works on gloo and NCCL alike)
-    reqs = []
+    idx = sp.device_index(K_local.device, dist)
+    sends = [K_local.index_select(0, idx["send"][q]) for q in range(sp.nranks)]
+    recvs = [torch.empty(idx["recv"][q].numel(), dtype=K_local.dtype, device=K_local.device)
+             for q in range(sp.nranks)]
+    ops = []
     for q in range(sp.nranks):
         if q == sp.rank:
-            recv[q].copy_(send[q])
+            recvs[q].copy_(sends[q])
             continue
-        reqs.append(dist.isend(send[q].contiguous(), q))
-        reqs.append(dist.irecv(recv[q], q))
-    for rq in reqs:
-        rq.wait()
-    local = np.zeros_like(owned_vals)
+        if sends[q].numel():
+            ops.append(dist.P2POp(dist.isend, sends[q], q))
+        if recvs[q].numel():
+            ops.append(dist.P2POp(dist.irecv, recvs[q], q))
+    if ops:
+        for rq in dist.batch_isend_irecv(ops):
+            rq.wait()
     for q in range(sp.nranks):
-        sp.scatter_values(local, sp.recv[q], recv[q].numpy())
-    return local
+        if recvs[q].numel():
+            K_local.index_copy_(0, idx["recv"][q], recvs[q])
+    return K_local
 
 
-def sharded_density(sp, owned_vals, mu, solve, dist):
+def allreduce_sum(values, device, dist):
+    """Sum of a few doubles over ranks, as one device allreduce."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    return t.tolist()
+
+
+def sharded_density(sp, K_local, mu, solve, dist, exchange=True):
     """This rank's block columns of D and the global trace.
 
-    ``solve(local_vals, mu, chunk) -> D values`` evaluates the chunk's block
-    columns (a column-range Plan on the GPU).  Returns (D values holding this
-    rank's block columns, Tr D summed over ranks)."""
-    import torch
-    local = exchange_halo(sp, owned_vals, dist)
-    d = solve(local, mu, sp.chunk)
-    tr = 0.0
-    for j in range(*sp.chunk):
-        p = int(np.searchsorted(sp.col_idx[sp.row_ptr[j]:sp.row_ptr[j + 1]], j)) + int(sp.row_ptr[j])
-        b = int(sp.block_sizes[j])
-        tr += float(np.trace(d[sp.vp[p]:sp.vp[p + 1]].reshape(b, b)))
-    t = torch.tensor([tr], dtype=torch.float64)
-    dist.all_reduce(t)
-    return d, float(t.item())
+    ``solve(K_local, mu, chunk) -> (D, tr)`` evaluates the chunk's block
+    columns on this rank's device (D a full-length tensor, zero outside the
+    chunk; tr the trace over the chunk).  Returns (D, Tr D summed over
+    ranks)."""
+    if exchange:
+        exchange_halo(sp, K_local, dist)
+    d, tr = solve(K_local, mu, sp.chunk)
+    (total,) = allreduce_sum([tr], K_local.device, dist)
+    return d, total
+
+
+def sharded_mu_search(sp, K_local, n_el, mu0, solve, dist, tol=1e-9, max_steps=60, bound=None, kT=0.0,
+                      dn_dmu=None):
+    """mu with Tr D(mu) = n_el over all ranks (Section IV-G): every trial mu is
+    evaluated on every rank's chunk and the electron count (and dN/dmu at
+    finite temperature) is sum-allreduced, so all ranks take the same steps.
+    Zero temperature: bisection on [mu0 - s, mu0 + s] on the side of n_el
+    (s = 1.01 bound + 1e-12); finite temperature: Newton steps kept inside
+    that bracket, bisection otherwise.  ``bound``: a spectral bound of the
+    submatrices at mu0 (max over ranks is taken); ``dn_dmu()``: this rank's
+    dN/dmu of the last evaluation.  Returns (mu, D, N, steps)."""
+    exchange_halo(sp, K_local, dist)
+    dev = K_local.device
+    steps = 0
+
+    def evaluate(mu):
+        nonlocal steps
+        d, tr = solve(K_local, mu, sp.chunk)
+        vals = [tr, dn_dmu() if (kT > 0 and dn_dmu) else 0.0]
+        n, dn = allreduce_sum(vals, dev, dist)
+        steps += 1
+        return d, n, dn
+
+    d, n, dn = evaluate(mu0)
+    mu = mu0
+    if abs(n - n_el) <= tol * abs(n_el):
+        return mu, d, n, steps
+    (b,) = allreduce_sum([bound or 0.0], dev, dist)
+    span = 1.01 * b + 1e-12 + (40.0 * kT if kT > 0 else 0.0)
+    lo, hi = (mu0, mu0 + span) if n < n_el else (mu0 - span, mu0)
+    while steps < max_steps and hi - lo > 1e-10 * max(b, 1e-300):
+        nxt = 0.5 * (lo + hi)
+        if kT > 0 and dn > 0:
+            newton = mu - (n - n_el) / dn
+            if lo < newton < hi:
+                nxt = newton
+        mu = nxt
+        d, n, dn = evaluate(mu)
+        if abs(n - n_el) <= tol * abs(n_el):
+            break
+        if n < n_el:
+            lo = mu
+        else:
+            hi = mu
+    return mu, d, n, steps
+
+
+def sharded_backward(sp, K_local, mu, Dbar_local, backward, dist):
+    """Kbar over all ranks: each rank adds the contributions of its chunk's
+    submatrices (``backward(K_local, mu, Dbar, chunk) -> Kbar`` on the
+    device), then one in-place sum-allreduce of the full-length Kbar (the
+    contributions overlap on shared blocks).  ``Dbar_local`` must hold this
+    rank's block columns of Dbar."""
+    kbar = backward(K_local, mu, Dbar_local, sp.chunk)
+    dist.all_reduce(kbar)
+    return kbar
 
 
 def gather_columns(sp, d_local, dist):
-    """Allgather of the block columns of D (optional: D replicated).  The
-    blocks of block column j are the CSR positions whose column index is j."""
+    """Allgather of the block columns of D on the device (optional: D
+    replicated).  The blocks of block column j are the CSR positions whose
+    column index is j."""
     import torch
-    mine = np.nonzero((sp.col_idx >= sp.chunk[0]) & (sp.col_idx < sp.chunk[1]))[0]
-    flat = torch.from_numpy(sp.gather_values(d_local, mine))
-    sizes = [None] * sp.nranks
-    dist.all_gather_object(sizes, int(flat.numel()))
-    bufs = [torch.empty(s, dtype=torch.float64) for s in sizes]
-    _all_gather_uneven(bufs, flat, dist)
-    out = np.zeros_like(d_local)
+    idx = sp.device_index(d_local.device, dist)
+    flat = d_local.index_select(0, idx["mine"])
+    sizes = [int(x) for x in allreduce_sizes(sp, flat.numel(), d_local.device, dist)]
+    n = max(sizes)
+    pad = torch.zeros(n, dtype=flat.dtype, device=flat.device)
+    pad[:flat.numel()] = flat
+    tmp = [torch.empty(n, dtype=flat.dtype, device=flat.device) for _ in range(sp.nranks)]
+    dist.all_gather(tmp, pad)
+    out = d_local.clone()
     for q in range(sp.nranks):
         lo, hi = sp.chunks[q]
         blocks = np.nonzero((sp.col_idx >= lo) & (sp.col_idx < hi))[0]
-        sp.scatter_values(out, blocks, bufs[q].numpy())
+        pos = torch.from_numpy(value_index(sp.vp, blocks)).to(d_local.device)
+        out.index_copy_(0, pos, tmp[q][:sizes[q]])
     return out
 
 
-def _all_gather_uneven(bufs, flat, dist):
+def allreduce_sizes(sp, mine, device, dist):
+    """Every rank's element count, as one device allreduce of a one-hot vector."""
     import torch
-    n = max(b.numel() for b in bufs)
-    pad = torch.zeros(n, dtype=flat.dtype)
-    pad[:flat.numel()] = flat
-    tmp = [torch.empty(n, dtype=flat.dtype) for _ in bufs]
-    dist.all_gather(tmp, pad)
-    for b, t in zip(bufs, tmp):
-        b.copy_(t[:b.numel()])
+    t = torch.zeros(sp.nranks, dtype=torch.float64, device=device)
+    t[sp.rank] = float(mine)
+    dist.all_reduce(t)
+    return t.tolist()
 
 
 def gpu_solver(pattern, device=None, **plan_kwargs):
     """A ``solve`` for ``sharded_density``: a column-range Plan on this rank's
-    GPU (created on first use, reused for later calls with the same chunk)."""
+    GPU (created on first use, reused for later calls with the same chunk).
+    Takes and returns device tensors; D is a full-length tensor zero outside
+    the chunk, and the trace is the chunk's."""
     import torch
     from .submat import Plan
     cache = {}
 
-    def solve(local_vals, mu, chunk):
+    def plan_for(chunk):
         if chunk not in cache:
-            cache[chunk] = Plan(pattern.block_sizes, pattern.row_ptr, pattern.col_idx,
-                                columns=chunk, **plan_kwargs)
-        K = torch.from_numpy(np.ascontiguousarray(local_vals)).to(device or "cuda")
-        D = torch.zeros_like(K)
-        cache[chunk].sign(K, mu, out=D)
-        return D.cpu().numpy()
+            cache[chunk] = Plan(pattern.block_sizes, pattern.row_ptr, pattern.col_idx, columns=chunk,
+                                **plan_kwargs)
+        return cache[chunk]
 
+    def solve(K_local, mu, chunk):
+        plan = plan_for(chunk)
+        D = torch.zeros_like(K_local)
+        plan.sign(K_local, mu, out=D)
+        return D, plan.trace(D)
+
+    solve.plan_for = plan_for
     return solve

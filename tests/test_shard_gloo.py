@@ -1,15 +1,18 @@
-"""Multi-rank path on CPU: world-size-2 gloo ranks run the partition, the halo
-exchange, the per-rank evaluation and the trace allreduce.  The per-rank
-solver here is the CPU oracle (test infrastructure standing in for the GPU
-plan), so the gathered D must equal the single-process oracle D exactly."""
+"""Multi-rank path on CPU: gloo ranks (world size 2 and 3) run the partition,
+the halo exchange, the per-rank evaluation, the trace and electron-count
+allreduces, the finite-temperature mu search and the Kbar reduction, through
+the same functions the GPU ranks use (CPU tensors here).  The per-rank solver
+is the CPU oracle (test infrastructure standing in for the GPU plan), so the
+results must equal the single-process oracle's."""
 import os
 import socket
 
 import numpy as np
 import pytest
 
-from paper_2004_10811_gb300.shard import (ShardedPattern, gather_columns, halo_blocks,
-                                          partition_columns, sharded_density, submatrix_dims)
+from paper_2004_10811_gb300.shard import (ShardedPattern, exchange_halo, gather_columns, halo_blocks,
+                                          partition_columns, sharded_backward, sharded_density,
+                                          sharded_mu_search, submatrix_dims)
 from synth import make_config, random_symmetric_bsr, small_case
 
 
@@ -55,7 +58,8 @@ def test_halo_is_exactly_what_the_submatrices_read():
         assert set(halo_blocks(m.row_ptr, m.col_idx, chunk).tolist()) == need
 
 
-def _worker(rank, world, port, case, out):
+def _worker(rank, world, port, case, out, mode="density"):
+    import torch
     import torch.distributed as dist
     import oracle
     os.environ["MASTER_ADDR"] = "127.0.0.1"
@@ -65,44 +69,114 @@ def _worker(rank, world, port, case, out):
     sp = ShardedPattern(m.block_sizes, m.row_ptr, m.col_idx, rank, world)
     # each rank starts with only the blocks of its own block rows
     owned = np.zeros_like(m.vals)
-    rows = np.repeat(np.arange(m.nblk), np.diff(m.row_ptr))
     vp = sp.vp
     for p in np.nonzero(sp.owner == rank)[0]:
         owned[vp[p]:vp[p + 1]] = m.vals[vp[p]:vp[p + 1]]
+    K_local = torch.from_numpy(owned)
+    kT = 0.05
+    chunk_cols = list(range(*sp.chunk))
 
-    def solve(local_vals, mu, chunk):
-        mm = m.with_vals(local_vals)
-        d = oracle.density_matrix(mm, mu, columns=list(range(*chunk)))
-        return np.nan_to_num(d, nan=0.0)
+    def chunk_trace(d):
+        tr = 0.0
+        for j in chunk_cols:
+            p = int(np.searchsorted(m.col_idx[m.row_ptr[j]:m.row_ptr[j + 1]], j)) + int(m.row_ptr[j])
+            b = int(m.block_sizes[j])
+            tr += float(np.trace(d[vp[p]:vp[p + 1]].reshape(b, b)))
+        return tr
 
-    d_local, tr = sharded_density(sp, owned, m.mu, solve, dist)
-    d_all = gather_columns(sp, d_local, dist)
+    last = {}
+
+    def solve(K, mu, chunk):
+        # the oracle on the values this rank holds (owned + exchanged halo)
+        mm = m.with_vals(K.numpy())
+        if mode == "mu_T":
+            d = oracle.density_matrix_T(mm, mu, kT, columns=chunk_cols)
+        else:
+            d = oracle.density_matrix(mm, mu, columns=chunk_cols)
+        d = np.nan_to_num(d, nan=0.0)
+        last["d"] = d
+        return torch.from_numpy(d), chunk_trace(d)
+
+    def dn_dmu():
+        # sum over the chunk's columns c of (F_cc - sum_k F_kc^2) / kT
+        d = last["d"]
+        sq = sum(float(np.sum(d[vp[p]:vp[p + 1]] ** 2)) for p in sp.mine)
+        return (chunk_trace(d) - sq) / kT
+
+    if mode == "density":
+        d_local, tr = sharded_density(sp, K_local, m.mu, solve, dist)
+        d_all = gather_columns(sp, d_local, dist)
+        result = (d_all.numpy(), tr)
+    elif mode == "mu_T":
+        mu, d_local, n, steps = sharded_mu_search(sp, K_local, m.n_el, 0.4, solve, dist, tol=1e-12,
+                                                  max_steps=60, bound=4.0, kT=kT, dn_dmu=dn_dmu)
+        result = (gather_columns(sp, d_local, dist).numpy(), (mu, n, steps))
+    else:  # backward
+        exchange_halo(sp, K_local, dist)
+        dbar = np.random.default_rng(3).standard_normal(m.vals.shape)
+
+        def backward(K, mu, Dbar, chunk):
+            kb, _ = oracle.sign_backward(m.with_vals(K.numpy()), Dbar.numpy(), mu, columns=chunk_cols)
+            return torch.from_numpy(kb)
+
+        kbar = sharded_backward(sp, K_local, m.mu, torch.from_numpy(dbar), backward, dist)
+        result = (kbar.numpy(), None)
     if rank == 0:
-        np.save(out, d_all)
+        np.save(out, result[0])
         with open(out + ".tr", "w") as f:
-            f.write(repr(tr))
+            f.write(repr(result[1]))
     dist.barrier()
     dist.destroy_process_group()
-    del rows
+
+
+def _run(world, case, out, mode):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    port = free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, case, out, mode)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=180)
+        assert p.exitcode == 0
 
 
 @pytest.mark.parametrize("world", [2, 3])
 def test_two_and_three_gloo_ranks_reproduce_the_single_process_result(tmp_path, world):
-    import multiprocessing as mp
     import oracle
     case = small_case
     out = str(tmp_path / "d.npy")
-    ctx = mp.get_context("spawn")
-    port = free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, case, out)) for r in range(world)]
-    for p in procs:
-        p.start()
-    for p in procs:
-        p.join(timeout=120)
-        assert p.exitcode == 0
+    _run(world, case, out, "density")
     m = case()
     want = oracle.density_matrix(m, m.mu)
     got = np.load(out)
     assert np.array_equal(got, want)
     tr = float(open(out + ".tr").read())
     assert abs(tr - oracle.trace_bsr(m, want)) < 1e-12
+
+
+def test_finite_temperature_mu_search_over_two_gloo_ranks(tmp_path):
+    """The electron count and dN/dmu allreduced over ranks: every rank takes
+    the same Newton steps, and the search lands on the single-process
+    oracle's root."""
+    import oracle
+    out = str(tmp_path / "d.npy")
+    _run(2, small_case, out, "mu_T")
+    m = small_case()
+    mu, n, steps = eval(open(out + ".tr").read())
+    dec = oracle.decompose_all(m, 0.0)
+    mu_o, _n, _s = oracle.mu_search_newton_T(dec, m.n_el, 0.05, -4.0, 4.0, tol=1e-14)
+    assert abs(n - m.n_el) <= 1e-12 * m.n_el
+    assert abs(mu - mu_o) < 1e-9
+    assert steps < 30
+    assert np.max(np.abs(np.load(out) - oracle.density_matrix_T(m, mu, 0.05))) < 1e-12
+
+
+def test_kbar_sum_reduced_over_three_gloo_ranks(tmp_path):
+    import oracle
+    out = str(tmp_path / "kbar.npy")
+    _run(3, small_case, out, "backward")
+    m = small_case()
+    dbar = np.random.default_rng(3).standard_normal(m.vals.shape)
+    want, _ = oracle.sign_backward(m, dbar, m.mu)
+    assert np.max(np.abs(np.load(out) - want)) < 1e-12
