@@ -118,3 +118,76 @@ def test_vjp_matches_daleckii_krein_at_128_molecules(pkg, prec, mode, tol):
     got = kbar.cpu().numpy()
     assert np.max(np.abs(want)) > 0
     assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+def test_central_differences_on_the_2048x23_workload(pkg):
+    """The 2048x23 workload itself (submatrices of 1472-1932): central
+    differences (h = 1e-6) of E = Tr(D K) by the FP64 path against
+    Kbar_pq + Kbar_qp plus the explicit term, on 8 entries.  Only the block
+    columns whose submatrices contain both block rows of an entry (and the
+    two columns of the explicit term) change E, so E and the adjoint are
+    evaluated on those columns alone, with column-range plans (reading c11)."""
+    import torch
+    from synth import make_config
+    m = make_config(3)
+    rp, ci, vp = m.row_ptr, m.col_idx, m.val_ptr
+    rows = np.repeat(np.arange(m.nblk), np.diff(rp))
+    nbh = [set(ci[rp[j]:rp[j + 1]].tolist()) for j in range(m.nblk)]
+    perm_np = transpose_index(m)
+    rng = np.random.default_rng(11)
+    entries, colsets = [], []
+    while len(entries) < 8:  # entries whose affected column set is small
+        p = int(rng.integers(m.nnzb))
+        P, Q = int(rows[p]), int(ci[p])
+        C = sorted({j for j in nbh[P] & nbh[Q] if P in nbh[j] and Q in nbh[j]} | {P, Q})
+        if len(C) <= 26:
+            entries.append(int(vp[p] + rng.integers(vp[p + 1] - vp[p])))
+            colsets.append(C)
+
+    def runs(cols):
+        cols = sorted(set(cols))
+        out, a = [], cols[0]
+        for x, y in zip(cols, cols[1:] + [None]):
+            if y != x + 1:
+                out.append((a, x + 1))
+                a = y
+        return out
+
+    plans = {}
+
+    def plan(run):
+        if run not in plans:
+            plans[run] = pkg.Plan.from_bsr(m, prec="fp64", columns=run)
+        return plans[run]
+
+    K0 = torch.from_numpy(m.vals.copy()).cuda()
+    Kt = K0[torch.from_numpy(perm_np).cuda()].contiguous()
+    allc = sorted(set(j for C in colsets for j in C))
+    D0 = torch.zeros_like(K0)
+    kbar = torch.zeros_like(K0)
+    for run in runs(allc):
+        plan(run).sign(K0, 0.0, out=D0)
+        kbar += plan(run).sign_backward(K0, 0.0, Kt)
+    grad = D0.cpu().numpy()[perm_np] + kbar.cpu().numpy()
+    h = 1e-6
+    for i1, C in zip(entries, colsets):
+        i2 = int(perm_np[i1])
+        blocks = np.flatnonzero(np.isin(ci, C))
+        pos = np.concatenate([np.arange(vp[b], vp[b + 1]) for b in blocks])
+        es = []
+        for sgn in (1.0, -1.0):
+            v = m.vals.copy()
+            v[i1] += sgn * h
+            if i2 != i1:
+                v[i2] += sgn * h
+            Kd = torch.from_numpy(v).cuda()
+            D = torch.zeros_like(Kd)
+            for run in runs(C):
+                plan(run).sign(Kd, 0.0, out=D)
+            d = D.cpu().numpy()
+            es.append(float(np.dot(d[pos], v[perm_np[pos]])))
+        fd = (es[0] - es[1]) / (2 * h)
+        an = grad[i1] + (grad[i2] if i2 != i1 else 0.0)
+        assert abs(fd - an) <= 2e-6 * max(1.0, abs(an)), (i1, fd, an)
+    for p in plans.values():
+        p.close()
