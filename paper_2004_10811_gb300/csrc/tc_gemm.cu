@@ -426,6 +426,50 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       // only one chunk is live in registers, and the diagonal handled only
       // on diagonal sub-tiles.  TMEM is released after its last read.
       if constexpr (LEAN) {
+        if (p.out_i64) {
+          // exact integer sums of slice products (full tiles): per 32-column
+          // chunk the one or two accumulators (adjacent levels, combined as
+          // acc0 * 2^d + acc1 in 32-bit integers), scaled by 2^shift and
+          // handed to the L2 bulk add in 16-column row segments
+          const uint32_t tb = tbase;
+#pragma unroll 1
+          for (int c = 0; c < 4 * HALVES; ++c) {
+            float a0[32], a1[32];
+            tmem_ld32(tb + uint32_t(c * 32), a0);
+            if (p.nacc == 2) tmem_ld32(tb + uint32_t(BN + c * 32), a1);
+            tmem_wait_ld();
+            if (c == 4 * HALVES - 1) {
+              tc_fence_before();
+              if (!p.test_skip_arrive) mbar_arrive(&tempty[ab]);
+            }
+            const int cg0 = item.z * BN + c * 32;
+            if (rg >= ld || cg0 >= ld) continue;
+            const long long mul = 1LL << p.i64_shift;
+            uint8_t* srow = reinterpret_cast<uint8_t*>(stg) + r * I64_PITCH;
+#pragma unroll
+            for (int seg = 0; seg < 32 / I64_SEG; ++seg) {
+              asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+#pragma unroll
+              for (int q = 0; q < I64_SEG; ++q) {
+                const int k = seg * I64_SEG + q;
+                const int v = p.nacc == 2 ? __float2int_rn(a0[k]) * (1 << p.i64_dshift) + __float2int_rn(a1[k])
+                                          : __float2int_rn(a0[k]);
+                *reinterpret_cast<long long*>(srow + 8 * q) = (long long)v * mul;
+              }
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+              long long* d = p.out_i64 + base + int64_t(rg) * ld + cg0 + seg * I64_SEG;
+              if (p.i64_accumulate)
+                asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], %2;" ::"l"(d),
+                             "r"(smem_u32(srow)), "n"(I64_SEG * 8)
+                             : "memory");
+              else
+                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(d),
+                             "r"(smem_u32(srow)), "n"(I64_SEG * 8)
+                             : "memory");
+              asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+          }
+        } else
         for (int h = 0; h < HALVES; ++h) {
           const int sub_tj = item.z * HALVES + h;
           const bool last_h = h == HALVES - 1;
@@ -671,8 +715,9 @@ cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st) {
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   // the lean epilogue: one accumulator, double-buffered in TMEM, BF16-pair or
   // FP32 output without a mirror
-  const bool lean = p.tmem_cols >= 2 * bn && p.nacc == 1 && !p.out_i64 && !(p.sym && !p.upper_only) &&
-                    (p.out_f32 || p.out_hi);
+  const bool lean = (p.out_i64 ? p.tmem_cols >= 2 * p.nacc * bn && p.nacc <= 2 && !p.sym
+                                : p.tmem_cols >= 2 * bn && p.nacc == 1 && !(p.sym && !p.upper_only) &&
+                                      (p.out_f32 || p.out_hi));
   auto run = [&](auto kern) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
