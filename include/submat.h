@@ -61,7 +61,9 @@ typedef enum {
 typedef enum {
   SUBMAT_FP64 = 0,               /* Newton-Schulz in FP64 throughout */
   SUBMAT_FP32 = 1,               /* Newton-Schulz in FP32 (no refinement) */
-  SUBMAT_MIXED_BF16_REFINE = 2   /* BF16 tensor-core Newton-Schulz, then FP64 refinement */
+  SUBMAT_MIXED_BF16_REFINE = 2   /* tensor-core Newton-Schulz on FP16 (hi, lo) pairs, then an
+                                    FP64-anchored correction from BF16 and exact sliced
+                                    tensor-core products (the name predates the FP16 stage) */
 } submat_precision;
 
 typedef struct {
@@ -69,7 +71,7 @@ typedef struct {
   double tol;                  /* stop when ||X^2 - I||_F <= sqrt(n_j) * tol, then one more
                                   iteration (Section VI-A: involution as stopping test);
                                   0 selects 1e-14 for FP64, 1e-6 for FP32, 2e-5 for the
-                                  BF16x3 stage of the mixed path */
+                                  FP16x3 stage of the mixed path */
   int max_iter;                /* Newton-Schulz iteration cap; 0 selects 100 */
   int beta_mode;               /* X_0 = a / beta.  0 (default): beta = 1.05 x a 10-step
                                   power-iteration estimate of the spectral radius when that
@@ -272,7 +274,7 @@ submat_status submat_trace(submat_plan* plan, const double* D_vals, double* tr,
  * At zero temperature Tr D(mu) is a staircase: if the bracket shrinks below
  * 1e-10 x the spectral bound without meeting tol, the call returns
  * MU_NO_ROOT with mu_out and D at the bracket end nearest n_el.
- * Mixed plans probe each step first: the BF16x3 Newton-Schulz iterate alone
+ * Mixed plans probe each step first: the FP16x3 Newton-Schulz iterate alone
  * (no correction, no FP64 fallback, at most 40 iterations), whose trace is
  * within 1/2 sum_q b_q (r_q sqrt(n_q) + 1e-3) of the full result (r_q the
  * final involution residual, b_q the extracted width); the probe decides the

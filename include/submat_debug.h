@@ -23,7 +23,8 @@ extern "C" {
  *   n      logical dimension (n <= ld); only used for the residual
  *   A_hi, A_lo, B_hi, B_lo   device BF16 arrays [count][ld][ld]; the *_lo may be
  *          NULL when split == 0
- *   split  0: C = A_hi B_hi^T;  1: C = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
+ *   split  bit 0 clear: C = A_hi B_hi^T;  set: C = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T.
+ *          Bit 1 set: the operands are FP16 instead of BF16 (all four alike)
  *   sym    1: only tiles with ti <= tj are computed and each is mirrored
  *          (B must then be symmetric and A B^T symmetric)
  *   C      device FP32 [count][ld][ld] (output)

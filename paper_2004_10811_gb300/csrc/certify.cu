@@ -20,6 +20,7 @@
 // either factor alone being safe, and the square, E_0 (the adjoint's seed) and
 // beta follow: (cX)^2 = c^2 X^2, so no product is recomputed.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -51,11 +52,12 @@ __global__ void __launch_bounds__(256) k_cert_rowsum(WaveDev w, CertSquare sq, c
   for (int r = blockIdx.x * 8 + warp; r < n; r += gridDim.x * 8) {
     const int64_t row = base + int64_t(r) * ld;
     float acc = 0.0f;
-    if (sq.mode == 2) {
-      const __nv_bfloat16* hi = static_cast<const __nv_bfloat16*>(sq.hi);
-      const __nv_bfloat16* lo = static_cast<const __nv_bfloat16*>(sq.lo);
+    if (sq.mode >= 2) {
       for (int c = lane * 4; c < ld; c += 128) {
-        const float4 q = load_split4(hi, lo, row + c);
+        const float4 q = sq.mode == 3 ? load_split4(static_cast<const __half*>(sq.hi),
+                                                    static_cast<const __half*>(sq.lo), row + c)
+                                      : load_split4(static_cast<const __nv_bfloat16*>(sq.hi),
+                                                    static_cast<const __nv_bfloat16*>(sq.lo), row + c);
         const float v[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -126,17 +128,17 @@ __global__ void __launch_bounds__(256) k_cert_apply(WaveDev w, NsStateDev ns, Ce
     const int r = int(e / ld), col0 = int(e - int64_t(r) * ld);
     const int64_t i = base + e;
     float q[4];
-    if constexpr (sizeof(T) == 2) {
-      __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(sq.hi);
-      __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(sq.lo);
+    if constexpr (sizeof(T) == 2) {  // BF16 or FP16 pairs
+      T* hi = static_cast<T*>(sq.hi);
+      T* lo = static_cast<T*>(sq.lo);
       const float4 v = load_split4(hi, lo, i);
       q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
 #pragma unroll
       for (int k = 0; k < 4; ++k) q[k] = c2f * q[k] + ((col0 + k == r && r < n) ? dshift : 0.0f);
       store_split4(make_float4(q[0], q[1], q[2], q[3]), hi, lo, i);
       for (int b = 0; b < lin.count; ++b) {
-        __nv_bfloat16* lh = static_cast<__nv_bfloat16*>(lin.hi[b]);
-        __nv_bfloat16* ll = static_cast<__nv_bfloat16*>(lin.lo[b]);
+        T* lh = static_cast<T*>(lin.hi[b]);
+        T* ll = static_cast<T*>(lin.lo[b]);
         const float4 x = load_split4(lh, ll, i);
         store_split4(make_float4(cf * x.x, cf * x.y, cf * x.z, cf * x.w), lh, ll, i);
       }
@@ -205,10 +207,14 @@ cudaError_t launch_certify(const WaveDev& w, NsStateDev ns, CertSquare sq, CertL
   // rounding of the computed square, relative to sum_k |X_rk||X_kc|:
   // FP64 products; FP32 products (ld terms); BF16x3 split products (the
   // dropped lo*lo term and the pair's own rounding, ~2^-16, FP32 sums of ld
-  // terms), doubled for q -> X^2
+  // terms), doubled for q -> X^2.  FP16x3 split products (mode 3) round to
+  // ~2^-21 relative plus 2^-25 absolute per entry (FP16's subnormal step);
+  // with gx >= rho(X_0) >= 1/1.05 whenever the certificate matters (the power
+  // estimate never exceeds rho), the BF16 terms cover them with room to spare
+  // and are kept.
   double eps0 = 0x1p-50, eps_ld = 0x1p-52;
   if (sq.mode == 1) { eps0 = 0x1p-22; eps_ld = 0x1p-23; }
-  if (sq.mode == 2) { eps0 = 0x1p-12; eps_ld = 0x1p-22; }
+  if (sq.mode >= 2) { eps0 = 0x1p-12; eps_ld = 0x1p-22; }
   k_cert_decide<<<(w.nsub + 255) / 256, 256, 0, st>>>(w, ns, lim.gmax, lim.fcap, eps0, eps_ld, count);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -216,7 +222,8 @@ cudaError_t launch_certify(const WaveDev& w, NsStateDev ns, CertSquare sq, CertL
   if (ax > 32) ax = 32;
   if (ax < 1) ax = 1;
   const dim3 grid(unsigned(ax), unsigned(w.nsub));
-  if (sq.mode == 2) k_cert_apply<__nv_bfloat16><<<grid, 256, 0, st>>>(w, ns, sq, lin);
+  if (sq.mode == 3) k_cert_apply<__half><<<grid, 256, 0, st>>>(w, ns, sq, lin);
+  else if (sq.mode == 2) k_cert_apply<__nv_bfloat16><<<grid, 256, 0, st>>>(w, ns, sq, lin);
   else if (sq.mode == 1) k_cert_apply<float><<<grid, 256, 0, st>>>(w, ns, sq, lin);
   else k_cert_apply<double><<<grid, 256, 0, st>>>(w, ns, sq, lin);
   count_launch();

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -158,6 +159,8 @@ cudaError_t launch_check_finite(const double* v, int64_t count, int* flags, cuda
 // power iteration: rho[s] ~ rho(X_s) (a lower bound converging to it)
 cudaError_t launch_power_bf16(const WaveDev& w, const __nv_bfloat16* X, int iters, const int* state,
                               double* rho, int max_ld, cudaStream_t st);
+cudaError_t launch_power_f16(const WaveDev& w, const __half* X, int iters, const int* state, double* rho,
+                             int max_ld, cudaStream_t st);
 cudaError_t launch_power_f64(const WaveDev& w, const double* X, int iters, const int* state, double* rho,
                              int max_ld, cudaStream_t st);
 cudaError_t launch_power_f32(const WaveDev& w, const float* X, int iters, const int* state, double* rho,
@@ -175,9 +178,9 @@ cudaError_t launch_rescale_f32(const WaveDev& w, float* X, const double* rho, do
 // Representation of the squared iterate: 0 FP64 X^2, 1 FP32 X^2, 2 a BF16
 // (hi, lo) pair holding q = diag I + alpha X^2.
 struct CertSquare {
-  int mode;
+  int mode;        // 0 FP64, 1 FP32, 2 BF16 (hi, lo) pair, 3 FP16 pair
   void* hi;        // the square (FP64 / FP32 array, or the pair's hi)
-  void* lo;        // the pair's lo (mode 2)
+  void* lo;        // the pair's lo (modes 2 and 3)
   float alpha, diag;
 };
 // Up to three buffers that scale linearly with X_0 (X_0 itself, E_0, E_0^T),

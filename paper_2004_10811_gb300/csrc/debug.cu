@@ -60,6 +60,8 @@ extern "C" submat_status submat_debug_tc_gemm(int count, int ld, int n, const vo
   using namespace submat;
   clear_error();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int f16 = (split >> 1) & 1;  // bit 1: FP16 operands
+  split &= 1;
   if (count < 1 || count > (1 << 22) || ld < 64 || ld % 64 || ld > 8192 || n < 0 || n > ld ||
       !A_hi || !B_hi || !C || (split && (!A_lo || !B_lo))) {
     set_error("bad argument to submat_debug_tc_gemm");
@@ -130,6 +132,7 @@ extern "C" submat_status submat_debug_tc_gemm(int count, int ld, int n, const vo
   p.skip_state = -1;
   p.alpha = 1.0f; p.beta = 0.0f;
   p.sym = sym;
+  p.f16 = f16;
   p.out_f32 = C;
   p.res2 = res2;
   p.flags = d_flags;

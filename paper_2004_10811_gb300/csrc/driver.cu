@@ -250,13 +250,13 @@ submat_status Plan::mu_search(const double* K, double n_el, double mu0, double t
     for (int j = col_lo; j < col_hi; ++j) bmax = std::max(bmax, res_bound[j]);
     return bmax;
   };
-  // Mixed plans probe first: the BF16x3 iterate without correction or FP64
+  // Mixed plans probe first: the FP16x3 iterate without correction or FP64
   // fallback (a fraction of a build, and none of the slow fallbacks that
   // evaluations inside a band need).  Its trace error is bounded per block
   // column c of submatrix q: with X the final iterate, S = sign(a) and
   // e_l = x_l^2 - 1 in the eigenbasis, |(X - S)_cc| <= sum_l Q_cl^2 |e_l|
   // <= ||X^2 - I||_F = r_q sqrt(n_q) (Newton-Schulz keeps signs and stays in
-  // [-1, 1]), plus 1e-3 for the BF16x3 rounding; N = sum_c (1 - S_cc) / 2.
+  // [-1, 1]), plus 1e-3 for the FP16x3 rounding; N = sum_c (1 - S_cc) / 2.
   MuProbe probe;
   if (opt.prec == SUBMAT_MIXED_BF16_REFINE)
     probe = [&](double mu, double* n, double* bnd) -> submat_status {

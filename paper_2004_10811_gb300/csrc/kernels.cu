@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -342,7 +343,22 @@ __global__ void __launch_bounds__(1024) k_power(WaveDev w, const T* __restrict__
     for (int r = warp; r < n; r += nw) {
       const T* row = Xs + int64_t(r) * ld;
       float acc = 0.0f;
-      if constexpr (sizeof(T) == 2) {
+      if constexpr (std::is_same<T, __half>::value) {
+        // eight FP16 per lane and load (padding columns are zero in X and v)
+        for (int c = lane * 8; c < ld; c += 256) {
+          const uint4 q = *reinterpret_cast<const uint4*>(row + c);
+          const float4 v0 = *reinterpret_cast<const float4*>(v + c);
+          const float4 v1 = *reinterpret_cast<const float4*>(v + c + 4);
+          const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
+          const float vv8[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&qw[k]));
+            acc = fmaf(f.x, vv8[2 * k], acc);
+            acc = fmaf(f.y, vv8[2 * k + 1], acc);
+          }
+        }
+      } else if constexpr (sizeof(T) == 2) {
         // eight BF16 per lane and load (padding columns are zero in X and v)
         for (int c = lane * 8; c < ld; c += 256) {
           const uint4 q = *reinterpret_cast<const uint4*>(row + c);
@@ -407,6 +423,10 @@ static cudaError_t power_impl(const WaveDev& w, const T* X, int iters, const int
 
 cudaError_t launch_power_bf16(const WaveDev& w, const __nv_bfloat16* X, int iters, const int* state,
                               double* rho, int max_ld, cudaStream_t st) {
+  return power_impl(w, X, iters, state, rho, max_ld, st);
+}
+cudaError_t launch_power_f16(const WaveDev& w, const __half* X, int iters, const int* state, double* rho,
+                             int max_ld, cudaStream_t st) {
   return power_impl(w, X, iters, state, rho, max_ld, st);
 }
 cudaError_t launch_power_f64(const WaveDev& w, const double* X, int iters, const int* state, double* rho,

@@ -1,4 +1,4 @@
-// Mixed-precision path: BF16 tensor-core Newton-Schulz, then an FP64-anchored
+// Mixed-precision path: FP16 tensor-core Newton-Schulz, then an FP64-anchored
 // correction of the iterate (the paper evaluates sign by FP64
 // eigendecomposition, Section IV-F, and reports low-precision GPU iterations,
 // Section VI-A; this path combines both).
@@ -6,7 +6,9 @@
 // Why a correction is needed.  Newton-Schulz never looks at a_j after X_0, and
 // every involution is a fixed point, so rounding errors that anticommute with
 // sign(a) survive all later iterations at full size.  BF16 products leave such
-// errors of order 1e-3 (1e-5 with the three-term split hi*hi + hi*lo + lo*hi).
+// errors of order 1e-3 (1e-5 with the three-term split hi*hi + hi*lo + lo*hi);
+// FP16 (hi, lo) pairs with the same split leave ~1e-6, which is what the
+// iteration here uses.
 // With S~ = S + F, F = F_c + F_a split into the parts that commute /
 // anticommute with S = sign(a):
 //   I - S~^2 = -2 S F_c + O(F^2)              =>  F_c = -1/2 S~ (I - S~^2)
@@ -15,8 +17,9 @@
 // C = ([S~, a] - [F_c, a]) S~ and |a| ~ H = (S~ a + a S~) / 2 (SPD).  Only
 // I - S~^2 and S~ a must be accurate to ~1e-10 (FP64 products); everything
 // else is a small correction computed with BF16x3 tensor-core products, the
-// Lyapunov equation by conjugate gradients.  One round takes the error from
-// delta to O(delta^2 |a|/gap); from the BF16x3 iterate this is ~1e-10.
+// Lyapunov equation by conjugate gradients to a relative residual tol.  One
+// round takes the error from delta to O(delta^2 |a|/gap) + delta tol; from
+// the FP16x3 iterate (delta ~1e-6) with tol = 1e-2 this is ~1e-8.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -129,18 +132,22 @@ __device__ __forceinline__ double i64_to_f64_scaled(long long I, int k, bool neg
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
-// The final Newton-Schulz iterate as its BF16 (hi, lo) pair, in buffer 0 or
+// The final Newton-Schulz iterate as its FP16 (hi, lo) pair, in buffer 0 or
 // 1 per submatrix (par).  The value hi + lo is exact in FP32.
 struct PairSrc {
-  const __nv_bfloat16* hi[2];
-  const __nv_bfloat16* lo[2];
+  const __half* hi[2];
+  const __half* lo[2];
   const int* par;
 };
 
 __device__ __forceinline__ float pair_value(const PairSrc& src, int s, int64_t i) {
   const int k = src.par[s] ? 1 : 0;
-  return __bfloat162float(src.hi[k][i]) + __bfloat162float(src.lo[k][i]);
+  return pair_get(src.hi[k], src.lo[k], i);
 }
+
+// the Newton-Schulz buffers hold FP16 pairs (the correction reuses them for
+// BF16 operands)
+__host__ __device__ __forceinline__ __half* as_h(__nv_bfloat16* p) { return reinterpret_cast<__half*>(p); }
 
 // submax[s] = bit pattern of max |hi + lo| over the iterate of submatrix s
 __global__ void k_submax_pair(WaveDev w, PairSrc src, unsigned long long* submax) {
@@ -293,17 +300,19 @@ __global__ void __launch_bounds__(256) k_hp_finalize_sym(WaveDev w, const long l
   }
 }
 
-// X_0 = a / beta as a BF16 (hi, lo) pair
+// X_0 = a / beta as a (hi, lo) pair (FP16 for the forward iteration, BF16 for
+// the tensor-core adjoint's)
+template <typename H>
 __global__ void k_scale_split(WaveDev w, const double* __restrict__ A, const double* __restrict__ beta,
-                              __nv_bfloat16* xh, __nv_bfloat16* xl) {
+                              H* xh, H* xl) {
   const float ib = float(1.0 / beta[blockIdx.y]);
   FOR_SUB_ELEMS(w) split2f(d2f_trunc(A[base + e]) * ib, xh, xl, base + e);
 }
 
 // X <- f X on the split pair (re-split), f = 1 / (1.05 rho) when it tightens
 // the scale; beta follows
-__global__ void k_rescale_split(WaveDev w, __nv_bfloat16* xh, __nv_bfloat16* xl, const double* rho,
-                                double* beta, const int* state) {
+template <typename H>
+__global__ void k_rescale_split(WaveDev w, H* xh, H* xl, const double* rho, double* beta, const int* state) {
   const int sb = blockIdx.y;
   if (state[sb] == ST_DONE) return;
   const double r = rho[sb];
@@ -313,7 +322,7 @@ __global__ void k_rescale_split(WaveDev w, __nv_bfloat16* xh, __nv_bfloat16* xl,
   const float ff = float(f);
   FOR_SUB_ELEMS(w) {
     const int64_t i = base + e;
-    split2f((__bfloat162float(xh[i]) + __bfloat162float(xl[i])) * ff, xh, xl, i);
+    split2f(pair_get(xh, xl, i) * ff, xh, xl, i);
   }
 }
 
@@ -332,17 +341,17 @@ __device__ __forceinline__ void block_max_bits(float mx, unsigned long long* out
 }
 
 // ... and submax[s] = max |S| of the submatrix (bit pattern of a bound >= it)
-__global__ void k_widen(WaveDev w, const int* __restrict__ par, __nv_bfloat16* x0h, __nv_bfloat16* x0l,
-                        const __nv_bfloat16* __restrict__ x1h, const __nv_bfloat16* __restrict__ x1l,
+__global__ void k_widen(WaveDev w, const int* __restrict__ par, __half* x0h, __half* x0l,
+                        const __half* __restrict__ x1h, const __half* __restrict__ x1l,
                         double* __restrict__ S, unsigned long long* submax) {
   const bool one = par[blockIdx.y] != 0;
   float mx = 0.0f;
   FOR_SUB_ELEMS(w) {
     const int64_t i = base + e;
-    __nv_bfloat16 h = one ? x1h[i] : x0h[i];
-    __nv_bfloat16 l = one ? x1l[i] : x0l[i];
+    const __half h = one ? x1h[i] : x0h[i];
+    const __half l = one ? x1l[i] : x0l[i];
     if (one) { x0h[i] = h; x0l[i] = l; }
-    const float v = __bfloat162float(h) + __bfloat162float(l);  // exact: exponents 8+ apart
+    const float v = __half2float(h) + __half2float(l);  // exact: at most 22 significant bits
     S[i] = f2d_exact(v);
     mx = fmaxf(mx, fabsf(v));
   }
@@ -704,18 +713,47 @@ __global__ void k_cg_init(WaveDev w, float* __restrict__ X, const float* __restr
 }
 
 // After the direction update: a submatrix whose relative CG residual
-// sqrt(rr / rr0) fell below tol stops (its later CG launches return at once).
-// Counts the submatrices still iterating.
-__global__ void k_cg_check(int nsub, const double* rr, const double* rr0, int* cg_done, double tol2,
-                           int* d_active) {
+// sqrt(rr / rr0) fell below its tolerance sqrt(tol2[s]) stops (its later CG
+// launches return at once).  Counts the submatrices still iterating.
+__global__ void k_cg_check(int nsub, const double* rr, const double* rr0, int* cg_done,
+                           const double* __restrict__ tol2, int* d_active) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   int active = 0;
   if (s < nsub && !cg_done[s]) {
-    if (!(rr[s] > tol2 * rr0[s])) cg_done[s] = 1;
+    if (!(rr[s] > tol2[s] * rr0[s])) cg_done[s] = 1;
     else active = 1;
   }
   active = __syncthreads_count(active);
   if (threadIdx.x == 0 && active) atomicAdd(d_active, active);
+}
+
+__global__ void k_fill_f64(int n, double* v, double value) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) v[s] = value;
+}
+
+// Once every submatrix has reached the loose tolerance: the remaining error
+// is ~delta * tol with delta = max |F_c + F_a|, so a submatrix with
+// delta * tol > target resumes CG at tol = max(target / delta, tol_tight).
+// Counts them.
+__global__ void k_cg_tighten(int nsub, const unsigned long long* corr, int* cg_done, double* tol2,
+                             double target, double tol_tight, int* d_count) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int more = 0;
+  if (s < nsub && cg_done[s]) {
+    const double c = __longlong_as_double((long long)corr[s]);
+    const double t = sqrt(tol2[s]);
+    if (!(c * t <= target)) {
+      const double tn = c > 0.0 ? fmax(target / c, tol_tight) : tol_tight;  // c is NaN: tight
+      if (tn < t) {
+        tol2[s] = tn * tn;
+        cg_done[s] = 0;
+        more = 1;
+      }
+    }
+  }
+  more = __syncthreads_count(more);
+  if (threadIdx.x == 0 && more) atomicAdd(d_count, more);
 }
 
 // S <- S - F_c - F_a, and corr_s = max |F_c + F_a| (bits of a non-negative double)
@@ -777,14 +815,26 @@ __global__ void k_corr_max(WaveDev w, const float* __restrict__ Fc, const float*
 // Submatrices whose last correction was still large, or whose Lyapunov solve
 // did not converge (a gap far smaller than the spectral radius), are
 // re-solved by FP64 Newton-Schulz: state ACTIVE for those, DONE for the rest.
+// With per-submatrix tolerances (tol2 given), a submatrix is accepted when
+// its CG met its own tolerance and either delta * tol <= 2 target (the
+// correction grows a little after the tolerance was set) or it ran at
+// tol_tight with delta <= corr_tol.
 __global__ void k_pick_fallback(WaveDev w, NsStateDev ns, const unsigned long long* corr,
                                 const double* rr, const double* rr0, double corr_tol,
-                                double cg_tol2, int* fallback_flag, int* d_count) {
+                                double cg_tol2, const double* __restrict__ tol2, double tol_tight,
+                                double target, int* fallback_flag, int* d_count) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   int pick = 0;
   if (s < w.nsub) {
     const double c = __longlong_as_double((long long)corr[s]);
-    const bool bad = !(c <= corr_tol) || (rr[s] > cg_tol2 * rr0[s]);
+    bool bad;
+    if (tol2) {
+      const double t = sqrt(tol2[s]);
+      const bool small = c * t <= 2.0 * target || (t <= tol_tight * 1.0001 && c <= corr_tol);
+      bad = !small || (rr[s] > tol2[s] * 1.0001 * rr0[s]);
+    } else {
+      bad = !(c <= corr_tol) || (rr[s] > cg_tol2 * rr0[s]);
+    }
     fallback_flag[s] = bad ? 1 : 0;
     ns.par[s] = 0;
     if (bad) {
@@ -842,6 +892,7 @@ struct MixedState {
   unsigned long long* submax = nullptr;  // per slot: bit pattern of max |S|
   int* pick = nullptr;               // per slot: FP64 fallback
   unsigned long long* corr = nullptr;  // per slot: max |correction| of the last round
+  double* tol2 = nullptr;            // per slot: squared relative CG tolerance
 };
 
 }  // namespace
@@ -974,6 +1025,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     SM_TRY(alloc(&ms->cg_count, size_t(max_wave), "CG counts"));
     SM_TRY(alloc(&ms->pick, size_t(max_wave), "fallback flags"));
     SM_TRY(alloc(&ms->corr, size_t(max_wave), "correction sizes"));
+    SM_TRY(alloc(&ms->tol2, size_t(max_wave), "CG tolerances"));
     SM_TRY(alloc(&ms->submax, size_t(max_wave), "iterate maxima"));
   }
   const long long tmo = timeout_cycles_for(2.0);
@@ -1052,18 +1104,22 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     SM_CUDA(cudaEventRecord(ev[0], st));
     SM_TRY(gather_wave(wv, K, mu, b.A, st));
     const dim3 eg = elem_grid(wv);
-    k_scale_split<<<eg, 256, 0, st>>>(wv.dev, b.A, ns.beta, b.X[0][0], b.X[0][1]);
+    k_scale_split<<<eg, 256, 0, st>>>(wv.dev, b.A, ns.beta, as_h(b.X[0][0]), as_h(b.X[0][1]));
     SM_KCHECK();
     if (opt.beta_mode == 0) {
       // tighter scale: beta = 1.05 x a power estimate of rho(a) (fewer iterations)
-      SM_CUDA(launch_power_bf16(wv.dev, b.X[0][0], kPowerIters, ns.state, ns.rprev, max_ld(wv), st));
-      k_rescale_split<<<eg, 256, 0, st>>>(wv.dev, b.X[0][0], b.X[0][1], ns.rprev, ns.beta, ns.state);
+      SM_CUDA(launch_power_f16(wv.dev, as_h(b.X[0][0]), kPowerIters, ns.state, ns.rprev, max_ld(wv), st));
+      k_rescale_split<<<eg, 256, 0, st>>>(wv.dev, as_h(b.X[0][0]), as_h(b.X[0][1]), ns.rprev, ns.beta,
+                                          ns.state);
       SM_KCHECK();
       SM_CUDA(launch_reset_rprev(wv.dev, ns, st));
     }
     SM_CUDA(cudaEventRecord(ev[1], st));
 
-    // ---- BF16x3 Newton-Schulz on the tensor cores ----
+    // ---- FP16x3 Newton-Schulz on the tensor cores ----
+    // The iterates are FP16 (hi, lo) pairs: their entries stay below 3 in
+    // magnitude, and the three-term split carries ~21 bits against BF16's ~16,
+    // so the rounding the correction must remove is ~10x smaller.
     // X_{k+1} = X_k Z_k with Z_k = 1.5 I - 0.5 X_k^2: the squaring writes Z
     // (and the residual ||X^2 - I||_F from its raw accumulator), so the
     // update is a plain product whose epilogue loads nothing
@@ -1083,11 +1139,12 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       g1.res2 = ns.res2;
       g1.state = ns.state; g1.skip_state = ST_DONE;
       g1.upper_only = 1;
+      g1.f16 = 1;
       SM_CUDA(launch(g1));
       k_mirror_split<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Y[0], b.Y[1], ns.state, ST_DONE);
       SM_KCHECK();
       if (k == 0 && opt.beta_mode == 0) {  // the power estimate's scale, proven from X_0^2 or reduced
-        const CertSquare sq{2, b.Y[0], b.Y[1], g1.alpha, g1.diag};
+        const CertSquare sq{3, b.Y[0], b.Y[1], g1.alpha, g1.diag};
         const CertLinear lin{1, {b.X[0][0], nullptr, nullptr}, {b.X[0][1], nullptr, nullptr}};
         SM_CUDA(launch_certify(wv.dev, ns, sq, lin, cert_limits(third), max_ld(wv), d_flags + 2, st));
       }
@@ -1099,6 +1156,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         gw.out_hi = b.Hh[0]; gw.out_lo = b.Hh[1];
         gw.state = ns.state; gw.skip_state = ST_DONE;
         gw.upper_only = 1;
+        gw.f16 = 1;
         SM_CUDA(launch(gw));
         k_mirror_split<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Hh[0], b.Hh[1], ns.state, ST_DONE);
         SM_KCHECK();
@@ -1109,6 +1167,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       g2.out_hi = b.X[cur ^ 1][0]; g2.out_lo = b.X[cur ^ 1][1];
       g2.state = ns.state; g2.skip_state = ST_DONE;
       g2.upper_only = 1;
+      g2.f16 = 1;
       SM_CUDA(launch(g2));
       k_mirror_split<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.X[cur ^ 1][0], b.X[cur ^ 1][1], ns.state,
                                                            ST_DONE);
@@ -1123,11 +1182,12 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     SM_CUDA(cudaEventRecord(ev[2], st));
 
     if (probe_mode) {
-      // the BF16x3 iterate as it stands (no correction, no FP64 fallback):
+      // the FP16x3 iterate as it stands (no correction, no FP64 fallback):
       // S = hi + lo, extracted as it is; the trace bound comes from the
       // submatrices' final residuals (Plan::mu_search)
       SM_CUDA(cudaMemsetAsync(ms->submax, 0, sizeof(unsigned long long) * max_wave, st));
-      k_widen<<<eg, 256, 0, st>>>(wv.dev, ns.par, b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.S, ms->submax);
+      k_widen<<<eg, 256, 0, st>>>(wv.dev, ns.par, as_h(b.X[0][0]), as_h(b.X[0][1]), as_h(b.X[1][0]),
+                                  as_h(b.X[1][1]), b.S, ms->submax);
       SM_KCHECK();
       SM_CUDA(cudaEventRecord(ev[3], st));
       SM_CUDA(launch_scatter_f64(g, wv.dev, ns, b.S, b.S, D, d_trpart, geom(wv), st));
@@ -1152,11 +1212,12 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     SM_CUDA(cudaMemsetAsync(ms->submax, 0, sizeof(unsigned long long) * max_wave, st));
     // the final iterate: the sliced path reads its BF16 pair directly (the
     // first slicing writes S); the FP64 residual path widens it to S here
-    const PairSrc iterate{{b.X[0][0], b.X[1][0]}, {b.X[0][1], b.X[1][1]}, ns.par};
+    const PairSrc iterate{{as_h(b.X[0][0]), as_h(b.X[1][0])}, {as_h(b.X[0][1]), as_h(b.X[1][1])}, ns.par};
     if (hp_sliced) {
       k_submax_pair<<<eg, 256, 0, st>>>(wv.dev, iterate, ms->submax);
     } else {
-      k_widen<<<eg, 256, 0, st>>>(wv.dev, ns.par, b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.S, ms->submax);
+      k_widen<<<eg, 256, 0, st>>>(wv.dev, ns.par, as_h(b.X[0][0]), as_h(b.X[0][1]), as_h(b.X[1][0]),
+                                  as_h(b.X[1][1]), b.S, ms->submax);
     }
     SM_KCHECK();
     k_split64<<<eg, 256, 0, st>>>(wv.dev, b.A, b.Ah[0], b.Ah[1]);
@@ -1246,7 +1307,14 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     };
     const int rounds = std::max(1, opt.refine_rounds);
     const int cg_max = 60;          // CG cap per round
-    const double cg_tol = 1e-3;     // relative residual that ends CG for a submatrix (first correction)
+    // relative residual that ends CG for a submatrix (first correction): the
+    // remaining error is ~delta * tol, delta ~1e-6 - 5e-6 from the FP16x3
+    // iterate.  All submatrices first run to cg_tol; one whose correction
+    // makes delta * cg_tol exceed cg_target resumes to cg_target / delta
+    // (at most cg_tol_tight).
+    const double cg_tol = 1e-2;
+    const double cg_tol_tight = 1e-3;
+    const double cg_target = 2e-8;
     const double cg_tol_later = 1e-2;  // later rounds correct an O(1e-9) error: 1e-2 suffices
     const double cg_bad = 1e-2;     // above this after cg_max the submatrix falls back
     const double corr_tol = 1e-8;   // largest acceptable last-round correction
@@ -1255,7 +1323,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       // ---- the two high-precision residual products ----
       // T = I - S^2
       // the first round puts S on a 24-bit grid (four slices, S^2 exact): the
-      // rounding (<= 2^-24 max|S|) is well below the BF16x3 error that the
+      // rounding (<= 2^-24 max|S|) is well below the FP16x3 error that the
       // round corrects; later rounds, correcting O(1e-9) errors, keep 36 bits
       const int s_keep = rd == 0 ? 4 : HP_SLICES;
       if (rd > 0) {  // a's split, overwritten by its slices in the previous round
@@ -1273,10 +1341,10 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
             wv.dev, reinterpret_cast<const long long*>(b.T), ms->rs_x, ms->d_voff[wi], b.Y[0], b.Y[1]);
         SM_KCHECK();
       } else {
-        if (rd > 0) {
-          k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
-          SM_KCHECK();
-        }
+        // S's BF16 split for the correction products (in the first round X0
+        // still holds the iterate's FP16 pair)
+        k_split64<<<eg, 256, 0, st>>>(wv.dev, b.S, b.X[0][0], b.X[0][1]);
+        SM_KCHECK();
         GemmF64Args f{};
         f.w = wv.dev; f.items = wv.sym64; f.nitems = wv.n_sym64;
         f.A = b.S; f.B = b.S; f.C0 = nullptr; f.C = b.T;
@@ -1357,6 +1425,15 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       k_cg_init<<<eg, 256, 0, st>>>(wv.dev, x_in_dir ? nullptr : b.cx, b.cr, rr, b.Y[0], b.Y[1]);
       SM_KCHECK();
       SM_CUDA(cudaMemcpyAsync(rr0, rr, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
+      // with more rounds to come the first one solves to 1e-4, so that its
+      // remaining error (~1e-10) is well inside the last round's 1e-8 test
+      const double tol_r = rd > 0 ? cg_tol_later : (rounds >= 2 ? 1e-4 : cg_tol);
+      k_fill_f64<<<(wv.count + 255) / 256, 256, 0, st>>>(wv.count, ms->tol2, tol_r * tol_r);
+      SM_KCHECK();
+      // one round: after the loose tolerance, the size of each correction
+      // decides whether delta * cg_tol is small enough (else CG resumes at
+      // cg_tol_tight)
+      bool tighten = rounds == 1;
       for (int it = 0; it < cg_max; ++it) {
         // W = H P; the epilogue also sums pTp = <P, W + W^T> = 2 <P, W>
         SM_CUDA(cudaMemsetAsync(ptp, 0, sizeof(double) * 2 * max_wave, st));  // ptp and rr_new
@@ -1386,11 +1463,20 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         cg_total += 1;
         {  // convergence test after every step (one 4-byte read)
           SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
-          // with more rounds to come the first one solves to 1e-4, so that its
-          // remaining error (~1e-9) is well inside the last round's 1e-8 test
-          const double tol_r = rd > 0 ? cg_tol_later : (rounds >= 2 ? 1e-4 : cg_tol);
-          k_cg_check<<<(wv.count + 255) / 256, 256, 0, st>>>(wv.count, rr, rr0, ms->cg_done,
-                                                             tol_r * tol_r, d_active);
+          k_cg_check<<<(wv.count + 255) / 256, 256, 0, st>>>(wv.count, rr, rr0, ms->cg_done, ms->tol2,
+                                                             d_active);
+          SM_KCHECK();
+          SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+          SM_CUDA(cudaStreamSynchronize(st));
+          if (reinterpret_cast<int*>(h_pinned)[0] != 0) continue;
+          if (!tighten) break;
+          tighten = false;
+          SM_CUDA(cudaMemsetAsync(ms->corr, 0, sizeof(unsigned long long) * max_wave, st));
+          k_corr_max<<<eg, 256, 0, st>>>(wv.dev, b.Fc, b.cx, ms->corr);
+          SM_KCHECK();
+          SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
+          k_cg_tighten<<<(wv.count + 255) / 256, 256, 0, st>>>(wv.count, ms->corr, ms->cg_done, ms->tol2,
+                                                               cg_target, cg_tol_tight, d_active);
           SM_KCHECK();
           SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
           SM_CUDA(cudaStreamSynchronize(st));
@@ -1411,12 +1497,13 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     // the size of the last correction bounds the remaining error only when an
     // earlier round has already been applied (a single round's correction is
     // the low-precision error itself), so with one round only the CG test applies
-    // With one round, CG reaching cg_tol = 1e-3 within cg_max = 60 iterations
-    // bounds |a|/gap (<~ 250), so the remaining error delta^2 |a|/gap + delta
-    // cg_tol is below ~4e-8 for delta <= 1e-5: accept then, with a delta cap of 1e-4.
+    // With one round the remaining error is ~delta^2 |a|/gap + delta tol, and
+    // CG reaching its tolerance within cg_max = 60 iterations bounds |a|/gap:
+    // accept where delta tol <= 2 cg_target, or where CG ran to cg_tol_tight
+    // and delta <= 1e-4.
     k_pick_fallback<<<(wv.count + 255) / 256, 256, 0, st>>>(
-        wv.dev, ns, ms->corr, rr, rr0, rounds >= 2 ? corr_tol : 1e-4,
-        rounds >= 2 ? cg_bad * cg_bad : cg_tol * cg_tol * 1.0001, ms->pick, d_active);
+        wv.dev, ns, ms->corr, rr, rr0, rounds >= 2 ? corr_tol : 1e-4, cg_bad * cg_bad,
+        rounds >= 2 ? nullptr : ms->tol2, cg_tol_tight, cg_target, ms->pick, d_active);
     SM_KCHECK();
     SM_CUDA(cudaMemcpyAsync(h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     SM_CUDA(cudaStreamSynchronize(st));

@@ -196,7 +196,7 @@ struct Plan {
   std::vector<int> res_iters, res_notconv;
   std::vector<double> res_resid, res_beta, res_bound;  // res_bound: min(max row abs-sum, ||a||_F)
   int last_flags = 0;              // status word of the last read_flags
-  bool probe_mode = false;         // mixed path: stop after the BF16x3 iteration (mu-search probe)
+  bool probe_mode = false;         // mixed path: stop after the FP16x3 iteration (mu-search probe)
   submat_stats stats{};
   KernelTimer timer;
   long long launches_at_start = 0;

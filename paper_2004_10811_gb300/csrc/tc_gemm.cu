@@ -19,6 +19,7 @@
 // frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -39,6 +40,7 @@ constexpr int I64_SEG = 16, I64_PITCH = 144;
 constexpr int STG_BYTES = (BM * I64_PITCH > BM * STG_PITCH * 4) ? BM * I64_PITCH : BM * STG_PITCH * 4;
 
 // instruction descriptor: D F32, A and B BF16, both K-major, M = 128, N = BN
+// (FP16 operands clear the two format fields, bits 7-9 and 10-12)
 template <int BN>
 __device__ __forceinline__ constexpr uint32_t idesc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
@@ -168,6 +170,21 @@ __device__ __forceinline__ void pack_split2(float a, float b, uint32_t* hw, uint
   *lw = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+// the FP16 forms of the two above (operands in FP16: TcGemmParams::f16)
+__device__ __forceinline__ uint32_t pack_split_h(float o) {
+  const __half h = __float2half_rn(o);
+  const __half l = __float2half_rn(o - __half2float(h));
+  return uint32_t(__half_as_ushort(h)) | (uint32_t(__half_as_ushort(l)) << 16);
+}
+
+__device__ __forceinline__ void pack_split2_h(float a, float b, uint32_t* hw, uint32_t* lw) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+  *hw = *reinterpret_cast<const uint32_t*>(&h);
+  *lw = *reinterpret_cast<const uint32_t*>(&l);
+}
+
 // one 32-byte store (a full L2 sector); the address is 32-byte aligned
 __device__ __forceinline__ void st_v8(void* d, const uint32_t* w) {
   asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(d), "r"(w[0]), "r"(w[1]),
@@ -177,14 +194,20 @@ __device__ __forceinline__ void st_v8(void* d, const uint32_t* w) {
 
 // write 32 values (one row segment, 64-byte aligned) in the output format,
 // in whole 32-byte sectors
+template <bool F16>
 __device__ __forceinline__ void store_row(const TcGemmParams& p, int64_t idx, const float* o) {
   if (p.out_f32) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) st_v8(p.out_f32 + idx + 8 * q, reinterpret_cast<const uint32_t*>(o + 8 * q));
   } else {
     uint32_t hw[16], lw[16];
+    if constexpr (F16) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) pack_split2(o[2 * q], o[2 * q + 1], &hw[q], &lw[q]);
+      for (int q = 0; q < 16; ++q) pack_split2_h(o[2 * q], o[2 * q + 1], &hw[q], &lw[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) pack_split2(o[2 * q], o[2 * q + 1], &hw[q], &lw[q]);
+    }
     st_v8(p.out_hi + idx, hw);
     st_v8(p.out_hi + idx + 16, hw + 8);
     if (p.out_lo) {
@@ -196,11 +219,12 @@ __device__ __forceinline__ void store_row(const TcGemmParams& p, int64_t idx, co
 
 // store o[q] for q in [q_lo, q_hi) only (diagonal tiles of symmetric outputs):
 // whole segments as vectors, element stores only where the diagonal crosses
+template <bool F16>
 __device__ __forceinline__ void store_range(const TcGemmParams& p, int64_t idx, const float* o,
                                             int q_lo, int q_hi) {
   if (q_lo >= 32 || q_hi <= 0 || q_lo >= q_hi) return;
   if (q_lo <= 0 && q_hi >= 32) {
-    store_row(p, idx, o);
+    store_row<F16>(p, idx, o);
     return;
   }
 #pragma unroll
@@ -209,13 +233,14 @@ __device__ __forceinline__ void store_range(const TcGemmParams& p, int64_t idx, 
     if (p.out_f32) {
       p.out_f32[idx + q] = o[q];
     } else {
-      const uint32_t w = pack_split(o[q]);
+      const uint32_t w = F16 ? pack_split_h(o[q]) : pack_split(o[q]);
       p.out_hi[idx + q] = __ushort_as_bfloat16(static_cast<unsigned short>(w & 0xFFFFu));
       if (p.out_lo) p.out_lo[idx + q] = __ushort_as_bfloat16(static_cast<unsigned short>(w >> 16));
     }
   }
 }
 
+template <bool F16>
 __device__ __forceinline__ void load_c0(const TcGemmParams& p, int64_t idx, float* c) {
   if (p.c0_f32) {
     // whole 32-byte sectors per load
@@ -237,11 +262,21 @@ __device__ __forceinline__ void load_c0(const TcGemmParams& p, int64_t idx, floa
       const uint4 h = sh[q];
       const uint4 l = sl ? sl[q] : make_uint4(0, 0, 0, 0);
       const uint32_t hh[4] = {h.x, h.y, h.z, h.w}, ll[4] = {l.x, l.y, l.z, l.w};
+      if constexpr (F16) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        c[8 * q + 2 * e] = __uint_as_float(hh[e] << 16) + __uint_as_float(ll[e] << 16);
-        c[8 * q + 2 * e + 1] =
-            __uint_as_float(hh[e] & 0xFFFF0000u) + __uint_as_float(ll[e] & 0xFFFF0000u);
+        for (int e = 0; e < 4; ++e) {
+          const float2 fh = __half22float2(*reinterpret_cast<const __half2*>(&hh[e]));
+          const float2 fl = __half22float2(*reinterpret_cast<const __half2*>(&ll[e]));
+          c[8 * q + 2 * e] = fh.x + fl.x;
+          c[8 * q + 2 * e + 1] = fh.y + fl.y;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          c[8 * q + 2 * e] = __uint_as_float(hh[e] << 16) + __uint_as_float(ll[e] << 16);
+          c[8 * q + 2 * e + 1] =
+              __uint_as_float(hh[e] & 0xFFFF0000u) + __uint_as_float(ll[e] & 0xFFFF0000u);
+        }
       }
     }
   }
@@ -250,7 +285,7 @@ __device__ __forceinline__ void load_c0(const TcGemmParams& p, int64_t idx, floa
 // LEAN: the launch has one accumulator, a BF16-pair or FP32 output, no
 // mirror and double-buffered TMEM (the host checks), and the epilogue drains
 // it 32 columns at a time; the general epilogue is not compiled in.
-template <int BN, bool LEAN>
+template <int BN, bool LEAN, bool F16>
 __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGemmParams p) {
   constexpr int TILE_B = BN * BK * 2;  // one BN x 64 BF16 operand tile (B side)
   constexpr int HALVES = BN / 128;
@@ -359,7 +394,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       // diagonal (odd row block): only the right half is wanted, so the MMAs
       // run at N = 128 on B rows 128..255 into accumulator columns 128..255
       const bool half = BN == 256 && p.sym && item.z * 2 < item.y;
-      const uint32_t id = half ? idesc<128>() : idesc<BN>();
+      // operand format: BF16 (A and B fields 1) or FP16 (both 0)
+      const uint32_t id = (half ? idesc<128>() : idesc<BN>()) & (F16 ? ~((7u << 7) | (7u << 10)) : ~0u);
       const uint32_t boff = half ? uint32_t(128 * BK * 2) : 0u;
       const uint32_t doff = half ? 128u : 0u;
       for (int kb = 0; kb < nk; ++kb) {
@@ -498,7 +534,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
             const int64_t idx = base + int64_t(rg) * ld + cg0;
             const bool has_c0 = (p.c0_f32 || p.c0_hi) && p.beta != 0.0f && !p.dot_c0;
             float c0[32];
-            if (has_c0 || p.dot_c0) load_c0(p, idx, c0);
+            if (has_c0 || p.dot_c0) load_c0<F16>(p, idx, c0);
             float o[32];
             float pr = 0.0f, pd = 0.0f;
             if (!dtile) {
@@ -525,8 +561,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
             }
             if (p.res2) part += res_weight * double(pr);
             if (p.dot_c0) part += 2.0 * double(pd);
-            if (diag_sym) store_range(p, idx, o, r - c * 32, 32);
-            else store_row(p, idx, o);
+            if (diag_sym) store_range<F16>(p, idx, o, r - c * 32, 32);
+            else store_row<F16>(p, idx, o);
           }
         }
       } else {
@@ -617,7 +653,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
           float c0[32];
           const int64_t idx = base + int64_t(rg) * ld + cg0;
           const bool has_c0 = (p.c0_f32 || p.c0_hi) && p.beta != 0.0f && !p.dot_c0;
-          if (has_c0 || p.dot_c0) load_c0(p, idx, c0);
+          if (has_c0 || p.dot_c0) load_c0<F16>(p, idx, c0);
           const int dq = (rg < n) ? rg - cg0 : -1;  // diagonal position in this segment
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
@@ -642,8 +678,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
             }
             part += res_weight * double(pc);
           }
-          if (diag_sym) store_range(p, idx, o, r - c * 32, 32);
-          else store_row(p, idx, o);
+          if (diag_sym) store_range<F16>(p, idx, o, r - c * 32, 32);
+          else store_row<F16>(p, idx, o);
         } else {
 #pragma unroll
           for (int q = 0; q < 32; ++q) o[q] = 0.0f;
@@ -663,8 +699,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
             float w[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) w[i] = __uint_as_float(stg[(part4 * 32 + i) * STG_PITCH + (q ^ (8 * part4))]);
-            if (diag_sym) store_range(p, base + int64_t(mrow) * ld + mcol0, w, 0, c * 32 + q - part4 * 32);
-            else store_row(p, base + int64_t(mrow) * ld + mcol0, w);
+            if (diag_sym) store_range<F16>(p, base + int64_t(mrow) * ld + mcol0, w, 0, c * 32 + q - part4 * 32);
+            else store_row<F16>(p, base + int64_t(mrow) * ld + mcol0, w);
           }
           epi_bar();
         }
@@ -724,9 +760,15 @@ cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st) {
     kern<<<grid, 192, smem, st>>>(p);
     return cudaSuccess;
   };
+  // FP16 operands: lean launches only (the Newton-Schulz products)
+  if (p.f16 && !lean) return cudaErrorInvalidValue;
   cudaError_t e;
-  if (bn == 256) e = lean ? run(k_tc_gemm<256, true>) : run(k_tc_gemm<256, false>);
-  else e = lean ? run(k_tc_gemm<128, true>) : run(k_tc_gemm<128, false>);
+  if (bn == 256)
+    e = p.f16 ? run(k_tc_gemm<256, true, true>)
+              : (lean ? run(k_tc_gemm<256, true, false>) : run(k_tc_gemm<256, false, false>));
+  else
+    e = p.f16 ? run(k_tc_gemm<128, true, true>)
+              : (lean ? run(k_tc_gemm<128, true, false>) : run(k_tc_gemm<128, false, false>));
   if (e != cudaSuccess) return e;
   count_launch();
   return cudaGetLastError();

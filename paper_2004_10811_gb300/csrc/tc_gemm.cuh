@@ -57,6 +57,9 @@ struct TcGemmParams {
   int i64_shift;
   int i64_dshift;
   int i64_accumulate;
+  // operand and pair format: 0 BF16, 1 FP16 (A and B always share one
+  // format; the (hi, lo) output pairs and C0 pairs take the same)
+  int f16;
   int* flags;
   long long timeout_cycles;
   int test_skip_arrive;           // test hook: epilogue withholds its TMEM release

@@ -324,15 +324,17 @@ def make_autograd_sign(plan: Plan):
 
 def debug_tc_gemm(A_hi, B_hi, A_lo=None, B_lo=None, n=None, sym=False, res2=None, skip_arrive=False,
                   timeout_s=2.0, stream=None, allow_timeout=False, tile_n=128):
-    """Test hook: the grouped BF16 tensor-core GEMM alone (include/submat_debug.h).
+    """Test hook: the grouped tensor-core GEMM alone (include/submat_debug.h).
 
-    A_*, B_*: CUDA bfloat16 tensors [count, ld, ld]; returns (C float32, status name).
+    A_*, B_*: CUDA bfloat16 or float16 tensors [count, ld, ld], all of one
+    dtype; returns (C float32, status name).
     """
     import torch
     lib = load()
     count, ld, ld2 = A_hi.shape
-    assert ld == ld2 and A_hi.dtype == torch.bfloat16 and A_hi.is_contiguous()
-    split = A_lo is not None
+    assert ld == ld2 and A_hi.dtype in (torch.bfloat16, torch.float16) and A_hi.is_contiguous()
+    assert all(t is None or t.dtype == A_hi.dtype for t in (B_hi, A_lo, B_lo))
+    split = (A_lo is not None) | (2 if A_hi.dtype == torch.float16 else 0)
     C_ = torch.empty((count, ld, ld), dtype=torch.float32, device=A_hi.device)
     ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
     st = lib.submat_debug_tc_gemm(count, ld, ld if n is None else int(n), ptr(A_hi), ptr(A_lo),

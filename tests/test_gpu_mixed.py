@@ -1,4 +1,4 @@
-"""Parity of the mixed path (BF16x3 tensor-core Newton-Schulz + FP64-anchored
+"""Parity of the mixed path (FP16x3 tensor-core Newton-Schulz + FP64-anchored
 correction) with the CPU oracle: max|dD| <= 1e-7 and the trace."""
 import numpy as np
 import pytest

@@ -1,4 +1,4 @@
-"""The grouped tcgen05 BF16 GEMM alone, against torch references of the same
+"""The grouped tcgen05 BF16/FP16 GEMM alone, against torch references of the same
 product (through the C ABI test hook in include/submat_debug.h)."""
 import numpy as np
 import pytest
@@ -57,6 +57,34 @@ def test_split_product_carries_16_bits(sm, tile_n):
     plain, _ = sm.debug_tc_gemm(ah, bh)
     rel_plain = (plain.double() - ref).abs().max().item() / ref.abs().max().item()
     assert rel < 2e-5 and rel < rel_plain / 20, (rel, rel_plain)
+
+
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_fp16_split_product_carries_19_bits(sm, tile_n):
+    """FP16 operands (the Newton-Schulz format): the three-term split keeps
+    ~19 bits.  Entries of size 0.05 put most lo parts below FP16's normal
+    range (2^-14), so the bound also shows that the tensor cores keep
+    subnormal inputs: flushing them would cost ~1e-4 relative."""
+    import torch
+    g = torch.Generator().manual_seed(11)
+    x = torch.zeros(2, 384, 384, dtype=torch.float64)
+    y = torch.zeros_like(x)
+    x[:, :350, :350] = torch.randn(2, 350, 350, generator=g, dtype=torch.float64) * 0.05
+    y[:, :350, :350] = torch.randn(2, 350, 350, generator=g, dtype=torch.float64) * 0.05
+    split = lambda t: (t.to(torch.float16), (t - t.to(torch.float16).double()).to(torch.float16))
+    (ah, al), (bh, bl) = split(x), split(y)
+    assert (al.abs() < 2.0 ** -14).float().mean().item() > 0.5  # mostly subnormal lo parts
+    c, st = sm.debug_tc_gemm(ah.cuda(), bh.cuda(), al.cuda(), bl.cuda(), tile_n=tile_n)
+    ref = (x @ y.transpose(1, 2)).cuda()
+    rel = (c.double() - ref).abs().max().item() / ref.abs().max().item()
+    # ~2^-19: the tensor cores' FP32 accumulation, not the operands, limits it
+    assert st == "OK" and rel < 4e-6, rel
+    # the same product from BF16 pairs is less accurate (measured 2.4x)
+    xbh, xbl = x.to(torch.bfloat16), (x - x.to(torch.bfloat16).double()).to(torch.bfloat16)
+    ybh, ybl = y.to(torch.bfloat16), (y - y.to(torch.bfloat16).double()).to(torch.bfloat16)
+    cb, _ = sm.debug_tc_gemm(xbh.cuda(), ybh.cuda(), xbl.cuda(), ybl.cuda(), tile_n=tile_n)
+    rel_b = (cb.double() - ref).abs().max().item() / ref.abs().max().item()
+    assert rel < rel_b / 2, (rel, rel_b)
 
 
 @pytest.mark.parametrize("tile_n", [128, 256])
