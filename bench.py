@@ -313,6 +313,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--adjoint-sample", type=int, default=32,
                     help="block columns timed for the adjoint (submat_sign_backward); 0 skips it")
+    ap.add_argument("--kT", type=float, default=0.05,
+                    help="finite-temperature key: one whole build with the Fermi function at this kT "
+                         "(Section IV-F) on the FP32 and FP64 paths; 0 skips it")
     ap.add_argument("--mu-search", action="store_true",
                     help="also time submat_mu_search for the workload's electron count")
     ap.add_argument("--columns", default=None,
@@ -654,6 +657,60 @@ def main():
             gline["max_abs_err_vs_grouped_oracle"] = float(np.max(np.abs(Dg.cpu().numpy()[mk] - wantg[mk])))
             gline["parity_sample"] = f"{len(sample)} of {int(groups.max()) + 1} groups"
         line["grouped"] = gline
+
+    # ---- finite temperature: D = f(K - mu I) with the Fermi function (Section IV-F) ----
+    if args.kT > 0 and args.prec == "mixed" and world == 1 and not columns:
+        ft = {"kT": args.kT}
+        for prec in ("fp32", "fp64"):
+            # FP64 over a contiguous chunk of 1/16 of the block columns (a
+            # whole build at FP64 rates takes minutes)
+            nc = max(1, m.nblk // 16) if prec == "fp64" and m.nblk >= 32 else 0
+            with pkg.Plan.from_bsr(m, prec=prec, kT=args.kT, columns=(0, nc) if nc else None) as pt:
+                Dt = torch.zeros_like(K)
+                pt.sign(K, m.mu, out=Dt)  # warm-up: workspace and polynomial
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pt.sign(K, m.mu, out=Dt)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tt = e0.elapsed_time(e1) / 1e3
+                st_t = pt.stats()
+                mu_t = None
+                if args.mu_search and prec == "fp32":
+                    # Newton on the smooth N(mu), started 0.5 above mu (FP32 traces: tol 1e-6)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    try:
+                        mu_f, _Dt, status_t = pt.mu_search(K, m.n_el, mu0=m.mu + 0.5, tol=1e-6, max_steps=40,
+                                                           out=Dt)
+                    except pkg.SubmatError as exc:  # reported, not fatal to the line
+                        mu_f, status_t = None, str(exc)
+                    torch.cuda.synchronize()
+                    tm_t = time.perf_counter() - t0
+                    mu_t = {"mu0": m.mu + 0.5, "mu": mu_f, "status": status_t, "s_total": tm_t,
+                            "evaluations": int(pt.stats()["mu_steps"]), "builds_equivalent": tm_t / tt}
+            leg = {"poly_degree": int(st_t["poly_degree"]), "poly_trunc": float(st_t["poly_trunc"]),
+                   "dn_dmu": float(st_t["dn_dmu"])}
+            if mu_t is not None:
+                leg["mu_search"] = mu_t
+            if nc:
+                sub_n3 = float(np.sum(sub["dims"].astype(np.float64) ** 3))
+                chunk_n3 = float(np.sum(sub["dims"][:nc].astype(np.float64) ** 3))
+                leg.update(chunk_s=tt, s_per_build_est=tt * sub_n3 / chunk_n3,
+                           measured=f"block columns [0, {nc}) timed, scaled by sum n^3")
+            else:
+                leg.update(s_per_build=tt, measured="one whole build (every block column), CUDA events")
+            if not args.no_cpu:
+                import oracle
+                tcols = sample_columns(nc if nc else m.nblk, 12)
+                wantt = oracle.density_matrix_T(m, m.mu, args.kT, columns=tcols, workers=host_cores()[0])
+                mk = ~np.isnan(wantt)
+                leg["max_abs_err_vs_oracle"] = float(np.max(np.abs(Dt.cpu().numpy()[mk] - wantt[mk])))
+                leg["parity_sample"] = f"{len(tcols)} block columns"
+            ft[prec] = leg
+        line["finite_t"] = ft
 
     # ---- the adjoint (vector-Jacobian product) on a contiguous chunk of block columns ----
     if args.adjoint_sample > 0 and world == 1 and not columns:
