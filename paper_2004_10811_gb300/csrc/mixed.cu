@@ -573,6 +573,9 @@ __global__ void __launch_bounds__(256) k_mirror_f32(WaveDev w, float* C) {
 // given, X += alpha P.  (On large submatrices X moves in the direction kernel
 // instead, which reads P anyway; on small ones the direction kernel's blocks
 // are short and the extra bytes cost more there.)
+// R, X and P are symmetric, so R and X are kept on the upper tiles only (a
+// diagonal tile whole); an upper off-diagonal tile counts twice in <R, R>.
+// X's lower triangle is filled once CG ends.
 // Block (8, 32): thread (x, y) owns columns 4x..4x+3 of row y of each tile
 // (float4 accesses).
 template <bool MOVE_X>
@@ -582,7 +585,7 @@ __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float*
                                                          const __nv_bfloat16* __restrict__ pl, const double* rr,
                                                          const double* ptp, double* rr_new,
                                                          const int* __restrict__ cg_done, int* cg_count) {
-  __shared__ float ta_[32][33], tb_[32][33];
+  __shared__ float tb_[2][32][33];  // W's lower tiles (b, a) of the two pairs in flight
   __shared__ double red[8];
   const int s = blockIdx.y;
   if (cg_done[s]) return;
@@ -596,58 +599,56 @@ __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float*
   const int npair = T * (T + 1) / 2;
   const int x4 = threadIdx.x * 4, y = threadIdx.y;
   float part = 0.0f;
-  for (int pi = blockIdx.x; pi < npair; pi += gridDim.x) {
-    int a = 0, rem = pi;
-    while (rem >= T - a) { rem -= T - a; ++a; }
-    const int b = a + rem;
-    const int64_t iab = base + int64_t(a * 32 + y) * ld + b * 32 + x4;
-    const int64_t iba = base + int64_t(b * 32 + y) * ld + a * 32 + x4;
-    const float4 wab = *reinterpret_cast<const float4*>(W + iab);
-    const float4 wba = *reinterpret_cast<const float4*>(W + iba);
-    __syncthreads();
-    ta_[y][x4] = wab.x; ta_[y][x4 + 1] = wab.y; ta_[y][x4 + 2] = wab.z; ta_[y][x4 + 3] = wab.w;
-    tb_[y][x4] = wba.x; tb_[y][x4 + 1] = wba.y; tb_[y][x4 + 2] = wba.z; tb_[y][x4 + 3] = wba.w;
-    __syncthreads();
-    // each tile: every load (R, and X with the P pair) issued before any store
-    {
-      float4 rv = *reinterpret_cast<const float4*>(R + iab);
-      float4 xv = make_float4(0.f, 0.f, 0.f, 0.f), pv = xv;
+  // two tile pairs per iteration, every load issued before any store
+  for (int p0 = blockIdx.x; p0 < npair; p0 += 2 * gridDim.x) {
+    const int np = p0 + int(gridDim.x) < npair ? 2 : 1;
+    int64_t iab[2];
+    float wgt[2];
+    float4 wab[2], wba[2], rv[2], xv[2], pv[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (q >= np) continue;
+      int a = 0, rem = p0 + q * int(gridDim.x);
+      while (rem >= T - a) { rem -= T - a; ++a; }
+      const int b = a + rem;
+      iab[q] = base + int64_t(a * 32 + y) * ld + b * 32 + x4;
+      wgt[q] = a == b ? 1.0f : 2.0f;
+      wab[q] = *reinterpret_cast<const float4*>(W + iab[q]);
+      wba[q] = *reinterpret_cast<const float4*>(W + base + int64_t(b * 32 + y) * ld + a * 32 + x4);
+      rv[q] = *reinterpret_cast<const float4*>(R + iab[q]);
       if constexpr (MOVE_X) {
-        xv = *reinterpret_cast<const float4*>(X + iab);
-        pv = load_split4(ph, pl, iab);
+        xv[q] = *reinterpret_cast<const float4*>(X + iab[q]);
+        pv[q] = load_split4(ph, pl, iab[q]);
       }
-      const float tp0 = wab.x + tb_[x4][y], tp1 = wab.y + tb_[x4 + 1][y];
-      const float tp2 = wab.z + tb_[x4 + 2][y], tp3 = wab.w + tb_[x4 + 3][y];
-      if constexpr (MOVE_X) {
-        xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
-        xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
-        *reinterpret_cast<float4*>(X + iab) = xv;
-      }
-      rv.x = fmaf(-alpha, tp0, rv.x); rv.y = fmaf(-alpha, tp1, rv.y);
-      rv.z = fmaf(-alpha, tp2, rv.z); rv.w = fmaf(-alpha, tp3, rv.w);
-      *reinterpret_cast<float4*>(R + iab) = rv;
-      part = fmaf(rv.x, rv.x, part); part = fmaf(rv.y, rv.y, part);
-      part = fmaf(rv.z, rv.z, part); part = fmaf(rv.w, rv.w, part);
     }
-    if (a != b) {
-      float4 rv = *reinterpret_cast<const float4*>(R + iba);
-      float4 xv = make_float4(0.f, 0.f, 0.f, 0.f), pv = xv;
+    __syncthreads();  // the previous iteration's transposes have been read
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (q >= np) continue;
+      tb_[q][y][x4] = wba[q].x; tb_[q][y][x4 + 1] = wba[q].y;
+      tb_[q][y][x4 + 2] = wba[q].z; tb_[q][y][x4 + 3] = wba[q].w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (q >= np) continue;
+      // TP = W + W^T on the upper tile (a, b)
+      const float tp0 = wab[q].x + tb_[q][x4][y], tp1 = wab[q].y + tb_[q][x4 + 1][y];
+      const float tp2 = wab[q].z + tb_[q][x4 + 2][y], tp3 = wab[q].w + tb_[q][x4 + 3][y];
       if constexpr (MOVE_X) {
-        xv = *reinterpret_cast<const float4*>(X + iba);
-        pv = load_split4(ph, pl, iba);
+        float4 x = xv[q];
+        x.x = fmaf(alpha, pv[q].x, x.x); x.y = fmaf(alpha, pv[q].y, x.y);
+        x.z = fmaf(alpha, pv[q].z, x.z); x.w = fmaf(alpha, pv[q].w, x.w);
+        *reinterpret_cast<float4*>(X + iab[q]) = x;
       }
-      const float tp0 = wba.x + ta_[x4][y], tp1 = wba.y + ta_[x4 + 1][y];
-      const float tp2 = wba.z + ta_[x4 + 2][y], tp3 = wba.w + ta_[x4 + 3][y];
-      if constexpr (MOVE_X) {
-        xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
-        xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
-        *reinterpret_cast<float4*>(X + iba) = xv;
-      }
-      rv.x = fmaf(-alpha, tp0, rv.x); rv.y = fmaf(-alpha, tp1, rv.y);
-      rv.z = fmaf(-alpha, tp2, rv.z); rv.w = fmaf(-alpha, tp3, rv.w);
-      *reinterpret_cast<float4*>(R + iba) = rv;
-      part = fmaf(rv.x, rv.x, part); part = fmaf(rv.y, rv.y, part);
-      part = fmaf(rv.z, rv.z, part); part = fmaf(rv.w, rv.w, part);
+      float4 r = rv[q];
+      r.x = fmaf(-alpha, tp0, r.x); r.y = fmaf(-alpha, tp1, r.y);
+      r.z = fmaf(-alpha, tp2, r.z); r.w = fmaf(-alpha, tp3, r.w);
+      *reinterpret_cast<float4*>(R + iab[q]) = r;
+      float sq = 0.0f;
+      sq = fmaf(r.x, r.x, sq); sq = fmaf(r.y, r.y, sq);
+      sq = fmaf(r.z, r.z, sq); sq = fmaf(r.w, r.w, sq);
+      part = fmaf(wgt[q], sq, part);
     }
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -663,12 +664,16 @@ __global__ void __launch_bounds__(256) k_cg_update_pairs(WaveDev w, const float*
 // CG step 3: when X is given, X += alpha P (X = alpha P on the first step);
 // then P = R + (rr_new / rr) P, split for the next product.  Runs exactly when
 // the step's update ran (cg_done changes only after this kernel).  P is kept
-// only as the BF16 (hi, lo) pair that the product reads.
+// only as the BF16 (hi, lo) pair that the product reads, in full (the product
+// reads its rows); R and X are read and written on the upper tiles only, and
+// P's lower tiles are written from the upper ones through shared memory.
+// 32x32 tile pairs, block (8, 32) as in the update.
 template <bool MOVE_X>
 __global__ void __launch_bounds__(256) k_cg_dir(WaveDev w, const float* __restrict__ R, float* __restrict__ X,
                                                 const double* rr, const double* ptp, const double* rr_new,
                                                 __nv_bfloat16* ph, __nv_bfloat16* pl,
                                                 const int* __restrict__ cg_done, int first) {
+  __shared__ float tp_[2][32][33];
   const int s = blockIdx.y;
   if (cg_done[s]) return;
   const double d = rr[s];
@@ -677,21 +682,56 @@ __global__ void __launch_bounds__(256) k_cg_dir(WaveDev w, const float* __restri
   const float beta = d > 0.0 ? float(rr_new[s] / d) : 0.0f;
   const int ld = w.ld[s];
   const int64_t base = w.off[s];
-  const int64_t total4 = int64_t(ld) * ld / 4;
-  for (int64_t e4 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e4 < total4;
-       e4 += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t i = base + 4 * e4;
-    const float4 r = *reinterpret_cast<const float4*>(R + i);
-    const float4 p = load_split4(ph, pl, i);
-    if constexpr (MOVE_X) {
-      float4 x = first ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(X + i);
-      x.x = fmaf(alpha, p.x, x.x); x.y = fmaf(alpha, p.y, x.y);
-      x.z = fmaf(alpha, p.z, x.z); x.w = fmaf(alpha, p.w, x.w);
-      *reinterpret_cast<float4*>(X + i) = x;
+  const int T = ld / 32;
+  const int npair = T * (T + 1) / 2;
+  const int x4 = threadIdx.x * 4, y = threadIdx.y;
+  // two tile pairs per iteration, every load issued before any store
+  for (int p0 = blockIdx.x; p0 < npair; p0 += 2 * gridDim.x) {
+    const int np = p0 + int(gridDim.x) < npair ? 2 : 1;
+    int ta[2], tb[2];
+    int64_t iab[2];
+    float4 r[2], p[2], x[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (q >= np) continue;
+      int a = 0, rem = p0 + q * int(gridDim.x);
+      while (rem >= T - a) { rem -= T - a; ++a; }
+      ta[q] = a; tb[q] = a + rem;
+      iab[q] = base + int64_t(a * 32 + y) * ld + tb[q] * 32 + x4;
+      r[q] = *reinterpret_cast<const float4*>(R + iab[q]);
+      p[q] = load_split4(ph, pl, iab[q]);
+      if constexpr (MOVE_X)
+        x[q] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(X + iab[q]);
     }
-    store_split4(make_float4(fmaf(beta, p.x, r.x), fmaf(beta, p.y, r.y), fmaf(beta, p.z, r.z),
-                             fmaf(beta, p.w, r.w)),
-                 ph, pl, i);
+    float4 pn[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (q >= np) continue;
+      if constexpr (MOVE_X) {
+        float4 xx = x[q];
+        xx.x = fmaf(alpha, p[q].x, xx.x); xx.y = fmaf(alpha, p[q].y, xx.y);
+        xx.z = fmaf(alpha, p[q].z, xx.z); xx.w = fmaf(alpha, p[q].w, xx.w);
+        *reinterpret_cast<float4*>(X + iab[q]) = xx;
+      }
+      pn[q] = make_float4(fmaf(beta, p[q].x, r[q].x), fmaf(beta, p[q].y, r[q].y), fmaf(beta, p[q].z, r[q].z),
+                          fmaf(beta, p[q].w, r[q].w));
+      store_split4(pn[q], ph, pl, iab[q]);
+    }
+    __syncthreads();  // the previous iteration's transposes have been read
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (q >= np || ta[q] == tb[q]) continue;  // a diagonal tile is whole already
+      tp_[q][y][x4] = pn[q].x; tp_[q][y][x4 + 1] = pn[q].y; tp_[q][y][x4 + 2] = pn[q].z; tp_[q][y][x4 + 3] = pn[q].w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (q >= np || ta[q] == tb[q]) continue;
+      // lower tile (b, a), row y, columns x4..x4+3 = upper (a, b) column y, rows x4..x4+3
+      const int64_t iba = base + int64_t(tb[q] * 32 + y) * ld + ta[q] * 32 + x4;
+      store_split4(make_float4(tp_[q][x4][y], tp_[q][x4 + 1][y], tp_[q][x4 + 2][y], tp_[q][x4 + 3][y]), ph, pl,
+                   iba);
+    }
   }
 }
 
@@ -878,6 +918,16 @@ dim3 pair_grid(const Wave& wv) {
   for (int64_t l : wv.bucket_ld) t = std::max<int64_t>(t, l / 32);
   int64_t np = t * (t + 1) / 2;
   return dim3(unsigned(std::min<int64_t>(np, 512)), unsigned(wv.count));
+}
+
+// The same for the streaming tile-pair kernels (CG steps, mirrors): about
+// eight pairs per block, so that blocks are few and long enough for their
+// launch cost to vanish against their traffic.
+dim3 pair_grid_stream(const Wave& wv) {
+  int64_t t = 1;
+  for (int64_t l : wv.bucket_ld) t = std::max<int64_t>(t, l / 32);
+  int64_t np = t * (t + 1) / 2;
+  return dim3(unsigned(std::max<int64_t>(1, std::min<int64_t>((np + 7) / 8, 512))), unsigned(wv.count));
 }
 
 struct MixedState {
@@ -1141,7 +1191,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       g1.upper_only = 1;
       g1.f16 = 1;
       SM_CUDA(launch(g1));
-      k_mirror_split<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Y[0], b.Y[1], ns.state, ST_DONE);
+      k_mirror_split<<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Y[0], b.Y[1], ns.state, ST_DONE);
       SM_KCHECK();
       if (k == 0 && opt.beta_mode == 0) {  // the power estimate's scale, proven from X_0^2 or reduced
         const CertSquare sq{3, b.Y[0], b.Y[1], g1.alpha, g1.diag};
@@ -1158,7 +1208,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         gw.upper_only = 1;
         gw.f16 = 1;
         SM_CUDA(launch(gw));
-        k_mirror_split<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Hh[0], b.Hh[1], ns.state, ST_DONE);
+        k_mirror_split<<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Hh[0], b.Hh[1], ns.state, ST_DONE);
         SM_KCHECK();
         z_hi = MS_HH;
         z_lo = MS_HL;
@@ -1169,7 +1219,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       g2.upper_only = 1;
       g2.f16 = 1;
       SM_CUDA(launch(g2));
-      k_mirror_split<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.X[cur ^ 1][0], b.X[cur ^ 1][1], ns.state,
+      k_mirror_split<<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(wv.dev, b.X[cur ^ 1][0], b.X[cur ^ 1][1], ns.state,
                                                            ST_DONE);
       SM_KCHECK();
       SM_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int), st));
@@ -1360,7 +1410,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       g.out_f32 = b.Fc;
       g.upper_only = 1;
       SM_CUDA(launch(g));
-      k_mirror_f32<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Fc);
+      k_mirror_f32<<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(wv.dev, b.Fc);
       SM_KCHECK();
       // W = F_c a, before S a so that a's split and Y are free for a's slices
       k_split32<<<eg, 256, 0, st>>>(wv.dev, b.Fc, b.Y[0], b.Y[1]);
@@ -1413,7 +1463,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       g4.out_f32 = b.cr;
       g4.upper_only = 1;
       SM_CUDA(launch(g4));
-      k_mirror_f32<<<pair_grid(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cr);
+      k_mirror_f32<<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cr);
       SM_KCHECK();
       // CG on L -> H L + L H, per submatrix until the relative residual is below cg_tol
       SM_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * 4 * max_wave, st));
@@ -1446,17 +1496,17 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         SM_CUDA(launch(gh));
         // the X-free variants compile as lean as the kernels without X
         if (x_in_dir) {
-          k_cg_update_pairs<false><<<pair_grid(wv), dim3(8, 32), 0, st>>>(
+          k_cg_update_pairs<false><<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(
               wv.dev, b.cw, nullptr, b.cr, b.Y[0], b.Y[1], rr, ptp, rrn, ms->cg_done, ms->cg_count);
           SM_KCHECK();
-          k_cg_dir<true><<<eg, 256, 0, st>>>(wv.dev, b.cr, b.cx, rr, ptp, rrn, b.Y[0], b.Y[1], ms->cg_done,
-                                             it == 0);
+          k_cg_dir<true><<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cr, b.cx, rr, ptp, rrn, b.Y[0], b.Y[1],
+                                                                ms->cg_done, it == 0);
         } else {
-          k_cg_update_pairs<true><<<pair_grid(wv), dim3(8, 32), 0, st>>>(
+          k_cg_update_pairs<true><<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(
               wv.dev, b.cw, b.cx, b.cr, b.Y[0], b.Y[1], rr, ptp, rrn, ms->cg_done, ms->cg_count);
           SM_KCHECK();
-          k_cg_dir<false><<<eg, 256, 0, st>>>(wv.dev, b.cr, nullptr, rr, ptp, rrn, b.Y[0], b.Y[1], ms->cg_done,
-                                              0);
+          k_cg_dir<false><<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cr, nullptr, rr, ptp, rrn, b.Y[0],
+                                                                 b.Y[1], ms->cg_done, 0);
         }
         SM_KCHECK();
         SM_CUDA(cudaMemcpyAsync(rr, rrn, sizeof(double) * max_wave, cudaMemcpyDeviceToDevice, st));
@@ -1471,6 +1521,9 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
           if (reinterpret_cast<int*>(h_pinned)[0] != 0) continue;
           if (!tighten) break;
           tighten = false;
+          // max |F_c + F_a|: X's lower triangle from its upper tiles first
+          k_mirror_f32<<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cx);
+          SM_KCHECK();
           SM_CUDA(cudaMemsetAsync(ms->corr, 0, sizeof(unsigned long long) * max_wave, st));
           k_corr_max<<<eg, 256, 0, st>>>(wv.dev, b.Fc, b.cx, ms->corr);
           SM_KCHECK();
@@ -1483,6 +1536,9 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
           if (reinterpret_cast<int*>(h_pinned)[0] == 0) break;
         }
       }
+      // CG kept X on its upper tiles: the lower triangle from them
+      k_mirror_f32<<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(wv.dev, b.cx);
+      SM_KCHECK();
       SM_CUDA(cudaMemsetAsync(ms->corr, 0, sizeof(unsigned long long) * max_wave, st));
       if (rd + 1 < rounds) {  // S itself is needed by the next round
         SM_CUDA(cudaMemsetAsync(ms->submax, 0, sizeof(unsigned long long) * max_wave, st));
