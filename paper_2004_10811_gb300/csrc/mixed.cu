@@ -89,6 +89,22 @@ MixedBufs carve(void* ws, int64_t E) {
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;            \
        e += int64_t(gridDim.x) * blockDim.x)
 
+// Four consecutive entries per thread and step (ld is a multiple of 64, so
+// every submatrix has a multiple of four entries and 16-byte aligned rows).
+#define FOR_SUB_ELEMS4(w)                                                                \
+  const int s = blockIdx.y;                                                              \
+  const int ld = (w).ld[s];                                                              \
+  const int64_t total4 = int64_t(ld) * ld / 4;                                           \
+  const int64_t base = (w).off[s];                                                       \
+  for (int64_t e4 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e4 < total4;         \
+       e4 += int64_t(gridDim.x) * blockDim.x)
+
+__device__ __forceinline__ float4 load4_f64_trunc(const double* p) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  return make_float4(d2f_trunc(a.x), d2f_trunc(a.y), d2f_trunc(b.x), d2f_trunc(b.y));
+}
+
 constexpr int HP_SLICES = 6;  // 6-bit slices per operand in the sliced products
 constexpr int HP_BITS = 6;
 // slice products kept: p + q <= 8 (26 of 36).  The first dropped level weighs
@@ -306,7 +322,11 @@ template <typename H>
 __global__ void k_scale_split(WaveDev w, const double* __restrict__ A, const double* __restrict__ beta,
                               H* xh, H* xl) {
   const float ib = float(1.0 / beta[blockIdx.y]);
-  FOR_SUB_ELEMS(w) split2f(d2f_trunc(A[base + e]) * ib, xh, xl, base + e);
+  FOR_SUB_ELEMS4(w) {
+    const int64_t i = base + 4 * e4;
+    const float4 a = load4_f64_trunc(A + i);
+    store_split4(make_float4(a.x * ib, a.y * ib, a.z * ib, a.w * ib), xh, xl, i);
+  }
 }
 
 // X <- f X on the split pair (re-split), f = 1 / (1.05 rho) when it tightens
@@ -320,9 +340,10 @@ __global__ void k_rescale_split(WaveDev w, H* xh, H* xl, const double* rho, doub
   const double f = 1.0 / (1.05 * r);
   if (threadIdx.x == 0 && blockIdx.x == 0) beta[sb] = beta[sb] / f;
   const float ff = float(f);
-  FOR_SUB_ELEMS(w) {
-    const int64_t i = base + e;
-    split2f(pair_get(xh, xl, i) * ff, xh, xl, i);
+  FOR_SUB_ELEMS4(w) {
+    const int64_t i = base + 4 * e4;
+    const float4 v = load_split4(xh, xl, i);
+    store_split4(make_float4(v.x * ff, v.y * ff, v.z * ff, v.w * ff), xh, xl, i);
   }
 }
 
@@ -359,11 +380,17 @@ __global__ void k_widen(WaveDev w, const int* __restrict__ par, __half* x0h, __h
 }
 
 __global__ void k_split64(WaveDev w, const double* __restrict__ src, __nv_bfloat16* hi, __nv_bfloat16* lo) {
-  FOR_SUB_ELEMS(w) split2(src[base + e], hi, lo, base + e);
+  FOR_SUB_ELEMS4(w) {
+    const int64_t i = base + 4 * e4;
+    store_split4(load4_f64_trunc(src + i), hi, lo, i);
+  }
 }
 
 __global__ void k_split32(WaveDev w, const float* __restrict__ src, __nv_bfloat16* hi, __nv_bfloat16* lo) {
-  FOR_SUB_ELEMS(w) split2f(src[base + e], hi, lo, base + e);
+  FOR_SUB_ELEMS4(w) {
+    const int64_t i = base + 4 * e4;
+    store_split4(*reinterpret_cast<const float4*>(src + i), hi, lo, i);
+  }
 }
 
 // For a 32x32 tile pair (a, b), a <= b, with P = S a (FP64) and W = F_c a (FP32):
@@ -741,12 +768,13 @@ __global__ void k_cg_init(WaveDev w, float* __restrict__ X, const float* __restr
                           __nv_bfloat16* ph, __nv_bfloat16* pl) {
   __shared__ double red[32];
   float part = 0.0f;
-  FOR_SUB_ELEMS(w) {
-    const int64_t i = base + e;
-    const float r = R[i];
-    if (X) X[i] = 0.0f;
-    split2f(r, ph, pl, i);
-    part = fmaf(r, r, part);
+  FOR_SUB_ELEMS4(w) {
+    const int64_t i = base + 4 * e4;
+    const float4 r = *reinterpret_cast<const float4*>(R + i);
+    if (X) *reinterpret_cast<float4*>(X + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    store_split4(r, ph, pl, i);
+    part = fmaf(r.x, r.x, part); part = fmaf(r.y, r.y, part);
+    part = fmaf(r.z, r.z, part); part = fmaf(r.w, r.w, part);
   }
   const double t = block_sum(part, red);
   if (threadIdx.x == 0) atomicAdd(&rr[blockIdx.y], t);
@@ -908,7 +936,8 @@ int sym256_count(int t128, int t256) {
 }
 
 dim3 elem_grid(const Wave& wv) {
-  int64_t bx = (wv.max_ld2 + 256 * 8 - 1) / (256 * 8);
+  // about 32 entries per thread: few, long blocks
+  int64_t bx = (wv.max_ld2 + 256 * 32 - 1) / (256 * 32);
   bx = std::max<int64_t>(1, std::min<int64_t>(bx, 256));
   return dim3(unsigned(bx), unsigned(wv.count));
 }
@@ -1387,7 +1416,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         SM_KCHECK();
         SM_TRY(hp_product(S_SETS, s_keep, S_SETS, s_keep, true, b.T));
         // (I - S^2) straight to its split in Y
-        k_hp_finalize_sym<<<pair_grid(wv), dim3(8, 32), 0, st>>>(
+        k_hp_finalize_sym<<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(
             wv.dev, reinterpret_cast<const long long*>(b.T), ms->rs_x, ms->d_voff[wi], b.Y[0], b.Y[1]);
         SM_KCHECK();
       } else {
@@ -1454,7 +1483,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
       }
       // M = [S, a] - [F_c, a] (split into Y), H = (S a + a S) / 2 (split)
       // (the sliced S a is read as its exact int64 sum, scaled on the fly)
-      k_comm<<<pair_grid(wv), dim3(8, 32), 0, st>>>(
+      k_comm<<<pair_grid_stream(wv), dim3(8, 32), 0, st>>>(
           wv.dev, hp_sliced ? nullptr : b.T, hp_sliced ? reinterpret_cast<const long long*>(b.T) : nullptr,
           ms->rs_x, ms->rs_y, ms->d_voff[wi], b.cw, b.Y[0], b.Y[1], b.Hh[0], b.Hh[1]);
       SM_KCHECK();
