@@ -187,7 +187,7 @@ CertLimits cert_limits(bool third_order) {
 
 cudaError_t launch_cert_rowsum(const WaveDev& w, NsStateDev ns, CertSquare sq, int max_ld, cudaStream_t st) {
   if (w.nsub <= 0) return cudaSuccess;
-  int bx = (max_ld + 7) / 8;
+  int bx = (max_ld + 63) / 64;  // about eight rows per warp
   if (bx > 32) bx = 32;
   k_cert_rowsum<<<dim3(unsigned(bx), unsigned(w.nsub)), 256, 0, st>>>(w, sq, ns.state, ns.cert);
   count_launch();
@@ -199,7 +199,7 @@ cudaError_t launch_certify(const WaveDev& w, NsStateDev ns, CertSquare sq, CertL
   if (w.nsub <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(ns.cert, 0, sizeof(unsigned long long) * size_t(w.nsub), st);
   if (e != cudaSuccess) return e;
-  int bx = (max_ld + 7) / 8;
+  int bx = (max_ld + 63) / 64;  // about eight rows per warp
   if (bx > 32) bx = 32;
   k_cert_rowsum<<<dim3(unsigned(bx), unsigned(w.nsub)), 256, 0, st>>>(w, sq, ns.state, ns.cert);
   count_launch();

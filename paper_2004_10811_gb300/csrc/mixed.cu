@@ -1305,7 +1305,8 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     static const int A_SETS[HP_SLICES] = {MS_AH, MS_AL, MS_HH, MS_HL, MS_Z0, MS_Z1};
     SlicePtrs sl_s{{b.X[0][0], b.X[0][1], b.X[1][0], b.X[1][1], b.Y[0], b.Y[1]}};
     SlicePtrs sl_a{{b.Ah[0], b.Ah[1], b.Hh[0], b.Hh[1], b.Z[0], b.Z[1]}};
-    const dim3 slice_grid(unsigned(std::max<int64_t>(1, std::min<int64_t>(max_ld / 8, 256))), unsigned(wv.count));
+    // about eight rows per warp (k_slice takes one row per warp at a time)
+    const dim3 slice_grid(unsigned(std::max<int64_t>(1, std::min<int64_t>(max_ld / 64, 256))), unsigned(wv.count));
     // C (+)= sign * X Y^T from the slices: level t = p + q weighs 2^(-6 t); each
     // launch sums at most per_acc products of one level in one exact accumulator
     int hp_launch_products = 0;  // slice products issued (all residual products, this wave)
