@@ -46,11 +46,14 @@ submat_status submat_debug_tc_gemm(int count, int ld, int n, const void* A_hi, c
  * product of the mixed path.  The product sum over slice pairs (p, q),
  * p + q <= 8, of 2^(6 (8 - p - q)) X_p Y_q^T is grouped into exact FP32
  * accumulators (one level and one weight each, at most per_acc products) and
- * launches of one or two accumulators.
+ * launches of up to max_acc accumulators.
  *   nx, ny     slices of the two operands (1..6)
  *   sym_pairs  1: X = Y with symmetric slices (nx == ny): only p <= q, the
  *              p < q products carry twice the weight (shift + 1)
  *   per_acc    products per accumulator: 2 (K extents up to 2048) or 1
+ *   max_acc    accumulators per launch: 2 (256-wide tiles: paired groups at
+ *              most 2^6 apart, combined in 32-bit integers) or 4 (128-wide
+ *              tiles: any weights, combined in 64-bit integers)
  *   out        host int32[cap][5] or NULL: one record per slice product,
  *              (launch, accumulator, p, q, shift); the product's weight is
  *              2^shift times 2^(-48) in the int64 sum
@@ -58,8 +61,8 @@ submat_status submat_debug_tc_gemm(int count, int ld, int n, const void* A_hi, c
  *   count      host int32: records of the plan (written even when cap is short)
  * Returns OK, or INVALID_ARG (bad sizes, NULL count, cap too small).
  */
-submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, int per_acc, int32_t* out, int cap,
-                                      int32_t* count);
+submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, int per_acc, int max_acc, int32_t* out,
+                                      int cap, int32_t* count);
 
 /*
  * Host-only (no GPU needed): the bisection of submat_mu_search (Section IV-G,

@@ -151,25 +151,23 @@ extern "C" submat_status submat_debug_tc_gemm(int count, int ld, int n, const vo
   return SUBMAT_OK;
 }
 
-extern "C" submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, int per_acc, int32_t* out,
-                                                 int cap, int32_t* count) {
+extern "C" submat_status submat_debug_slice_plan(int nx, int ny, int sym_pairs, int per_acc, int max_acc,
+                                                 int32_t* out, int cap, int32_t* count) {
   using namespace submat;
   clear_error();
   const int smax = slice_max_slices();
   if (!count || nx < 1 || ny < 1 || nx > smax || ny > smax || (per_acc != 1 && per_acc != 2) ||
-      (sym_pairs && nx != ny) || cap < 0) {
+      (max_acc != 2 && max_acc != kSliceMaxAcc) || (sym_pairs && nx != ny) || cap < 0) {
     set_error("bad argument to submat_debug_slice_plan");
     return SUBMAT_ERR_INVALID_ARG;
   }
   std::vector<SliceGroup> groups;
   std::vector<SliceLaunch> launches;
-  slice_plan(nx, ny, sym_pairs != 0, per_acc, &groups, &launches);
+  slice_plan(nx, ny, sym_pairs != 0, per_acc, max_acc, &groups, &launches);
   int n = 0;
   for (size_t l = 0; l < launches.size(); ++l) {
-    const int g[2] = {launches[l].g0, launches[l].g1};
-    for (int acc = 0; acc < 2; ++acc) {
-      if (g[acc] < 0) continue;
-      const SliceGroup& gr = groups[size_t(g[acc])];
+    for (int acc = 0; acc < launches[l].ng; ++acc) {
+      const SliceGroup& gr = groups[size_t(launches[l].g[acc])];
       for (int i = 0; i < gr.np; ++i, ++n) {
         if (out && n < cap) {
           int32_t* r = out + 5 * int64_t(n);

@@ -978,17 +978,20 @@ struct MixedState {
 
 // Launch plan of an exact sliced product: groups of slice products (one level
 // and one weight per exact FP32 accumulator, at most per_acc products),
-// sorted by decreasing weight, and launches of one group or of two groups
-// whose weights differ by at most 2^6 and whose slices fit in six operand
-// tiles per stage (see the comments at the product's use below).
-void slice_sets(const SliceGroup* g0, const SliceGroup* g1, int* as, int* na_out, int* bs, int* nb_out) {
+// sorted by decreasing weight, and launches of up to max_acc groups whose
+// slices fit in six operand tiles per stage.  With max_acc = 2 the second
+// group is at most 2^6 below the first (the pair is combined in 32-bit
+// integers); with more, the epilogue combines in 64-bit integers and any
+// weights mix.  Each launch starts from the heaviest group left, so the
+// int64 sums grow from the top.
+void slice_sets(const SliceGroup* const* gs, int ng, int* as, int* na_out, int* bs, int* nb_out) {
   int na = 0, nb = 0;
-  for (const SliceGroup* g : {g0, g1}) {
-    if (!g) continue;
+  for (int k = 0; k < ng; ++k) {
+    const SliceGroup* g = gs[k];
     for (int i = 0; i < g->np; ++i) {
       bool fa = false, fb = false;
-      for (int k = 0; k < na; ++k) fa |= as[k] == g->pr[i][0];
-      for (int k = 0; k < nb; ++k) fb |= bs[k] == g->pr[i][1];
+      for (int t = 0; t < na; ++t) fa |= as[t] == g->pr[i][0];
+      for (int t = 0; t < nb; ++t) fb |= bs[t] == g->pr[i][1];
       if (!fa) as[na++] = g->pr[i][0];
       if (!fb) bs[nb++] = g->pr[i][1];
     }
@@ -997,11 +1000,12 @@ void slice_sets(const SliceGroup* g0, const SliceGroup* g1, int* as, int* na_out
   *nb_out = nb;
 }
 
-void slice_plan(int nx, int ny, bool sym_pairs, int per_acc, std::vector<SliceGroup>* groups_out,
+void slice_plan(int nx, int ny, bool sym_pairs, int per_acc, int max_acc, std::vector<SliceGroup>* groups_out,
                 std::vector<SliceLaunch>* launches) {
   std::vector<SliceGroup>& groups = *groups_out;
   groups.clear();
   launches->clear();
+  max_acc = std::max(1, std::min(max_acc, kSliceMaxAcc));
   for (int t = 2; t <= HP_MAX_LEVEL; ++t) {
     int pairs[HP_SLICES][2];
     int np = 0;
@@ -1033,16 +1037,31 @@ void slice_plan(int nx, int ny, bool sym_pairs, int per_acc, std::vector<SliceGr
   for (size_t i = 0; i < groups.size(); ++i) {
     if (used[i]) continue;
     used[i] = 1;
-    int best = -1, best_tiles = 1 << 30;
-    for (size_t j = i + 1; j < groups.size(); ++j) {
-      if (used[j] || groups[i].shift - groups[j].shift > 6) continue;
-      if (groups[i].np + groups[j].np > 4) continue;
-      int as[8], bs[8], na = 0, nb = 0;
-      slice_sets(&groups[i], &groups[j], as, &na, bs, &nb);
-      if (na + nb <= 6 && na + nb < best_tiles) { best = int(j); best_tiles = na + nb; }
+    SliceLaunch L{};
+    L.ng = 1;
+    L.g[0] = int(i);
+    int nprod = groups[i].np;
+    while (L.ng < max_acc) {
+      int best = -1, best_tiles = 1 << 30;
+      for (size_t j = i + 1; j < groups.size(); ++j) {
+        if (used[j]) continue;
+        if (max_acc == 2 && groups[i].shift - groups[j].shift > 6) continue;
+        if (nprod + groups[j].np > 2 * max_acc) continue;
+        const SliceGroup* gs[kSliceMaxAcc + 1];
+        for (int k = 0; k < L.ng; ++k) gs[k] = &groups[size_t(L.g[k])];
+        gs[L.ng] = &groups[j];
+        int as[16], bs[16], na = 0, nb = 0;
+        slice_sets(gs, L.ng + 1, as, &na, bs, &nb);
+        if (na + nb <= 6 && na + nb < best_tiles) { best = int(j); best_tiles = na + nb; }
+      }
+      if (best < 0) break;
+      used[size_t(best)] = 1;
+      L.g[L.ng++] = best;
+      nprod += groups[size_t(best)].np;
     }
-    if (best >= 0) used[best] = 1;
-    launches->push_back(SliceLaunch{int(i), best});
+    // accumulators in decreasing weight (accumulator 0 the heaviest)
+    std::sort(L.g, L.g + L.ng, [&](int x, int y) { return groups[size_t(x)].shift > groups[size_t(y)].shift; });
+    launches->push_back(L);
   }
 }
 
@@ -1321,16 +1340,21 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     // tiles per stage: fewer launches, so fewer int64 passes.
     auto hp_product = [&](const int* xs, int nx, const int* ys, int ny, bool sym_pairs,
                           double* out) -> submat_status {
+      // 128-wide tiles carry up to four accumulators (all of TMEM, single-
+      // buffered, combined in 64-bit integers); 256-wide ones two
+      const int want_w = opt.tile_n_hp == 256 ? 256 : 128;
       std::vector<SliceGroup> groups;
       std::vector<SliceLaunch> launches;
-      slice_plan(nx, ny, sym_pairs, per_acc, &groups, &launches);
+      slice_plan(nx, ny, sym_pairs, per_acc, want_w == 128 ? kSliceMaxAcc : 2, &groups, &launches);
       bool first = true;
       const int saved_bn = bn;
-      auto issue = [&](const SliceGroup* g0, const SliceGroup* g1) -> submat_status {
-        int as[8], bs_[8], na = 0, nb = 0;
-        slice_sets(g0, g1, as, &na, bs_, &nb);
+      auto issue = [&](const SliceLaunch& L) -> submat_status {
+        const SliceGroup* gs[kSliceMaxAcc];
+        for (int k = 0; k < L.ng; ++k) gs[k] = &groups[size_t(L.g[k])];
+        int as[16], bs_[16], na = 0, nb = 0;
+        slice_sets(gs, L.ng, as, &na, bs_, &nb);
         // 256-wide tiles when two pipeline stages of the launch's slices fit
-        int w = opt.tile_n_hp ? opt.tile_n_hp : 128;
+        int w = want_w;
         if (w == 256 && tc_smem_bytes(na, nb, 2, 256) > 227 * 1024) w = 128;
         use_width(w);
         TcGemmParams p;
@@ -1346,30 +1370,29 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         for (int k = 0; k < na; ++k) p.a_set[k] = xs[as[k] - 1];
         for (int k = 0; k < nb; ++k) p.b_set[k] = ys[bs_[k] - 1];
         int np = 0;
-        const SliceGroup* gs[2] = {g0, g1};
-        for (int acc = 0; acc < 2; ++acc) {
+        for (int acc = 0; acc < L.ng; ++acc) {
           const SliceGroup* g = gs[acc];
-          if (!g) continue;
           for (int i = 0; i < g->np; ++i, ++np) {
             int ia = 0, ib = 0;
             while (as[ia] != g->pr[i][0]) ++ia;
             while (bs_[ib] != g->pr[i][1]) ++ib;
             p.prod_a[np] = ia; p.prod_b[np] = ib; p.prod_acc[np] = acc; p.prod_first[np] = i == 0;
           }
+          p.i64_shifts[acc] = g->shift;
         }
         p.nprod = np;
-        p.nacc = g1 ? 2 : 1;
+        p.nacc = L.ng;
         p.nstage = tc_pick_stages(na, nb, bn);
-        // TMEM holds 512 columns: two accumulators of 256 columns leave room
-        // for one set only (single-buffered)
+        // TMEM holds 512 columns: two sets of the accumulators when they fit
+        // (the next tile's MMAs overlap this one's drain), else one
         p.tmem_cols = std::min(512, 2 * p.nacc * bn);
         p.off = wv.dev.off; p.ld = wv.dev.ld; p.n = wv.dev.n;
         p.skip_state = -1;
         p.flags = d_flags;
         p.timeout_cycles = tmo;
         p.out_i64 = reinterpret_cast<long long*>(out);
-        p.i64_shift = g1 ? g1->shift : g0->shift;
-        p.i64_dshift = g1 ? g0->shift - g1->shift : 0;
+        p.i64_shift = L.ng == 2 ? gs[1]->shift : gs[0]->shift;
+        p.i64_dshift = L.ng == 2 ? gs[0]->shift - gs[1]->shift : 0;
         p.i64_accumulate = first ? 0 : 1;
         const int saved = tc_class;
         tc_class = KC_TC_HP;
@@ -1380,8 +1403,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
         first = false;
         return SUBMAT_OK;
       };
-      for (const SliceLaunch& L : launches)
-        SM_TRY(issue(&groups[L.g0], L.g1 >= 0 ? &groups[L.g1] : nullptr));
+      for (const SliceLaunch& L : launches) SM_TRY(issue(L));
       use_width(saved_bn);
       return SUBMAT_OK;
     };

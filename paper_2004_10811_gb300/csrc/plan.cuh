@@ -27,10 +27,13 @@ void free_adjoint_tc(void* state);
 // level and weight 2^shift.  A launch carries group g0 and, if g1 >= 0, group
 // g1 in a second accumulator (g0's weight the larger).
 struct SliceGroup { int np; int pr[2][2]; int shift; };
-struct SliceLaunch { int g0, g1; };
-void slice_plan(int nx, int ny, bool sym_pairs, int per_acc, std::vector<SliceGroup>* groups,
+constexpr int kSliceMaxAcc = 4;  // accumulators (groups) per launch at most
+struct SliceLaunch { int ng; int g[kSliceMaxAcc]; };
+// max_acc 2: pairs of groups at most 2^6 apart (combined in 32-bit integers);
+// max_acc 4: up to four groups of any weights (combined in 64-bit integers)
+void slice_plan(int nx, int ny, bool sym_pairs, int per_acc, int max_acc, std::vector<SliceGroup>* groups,
                 std::vector<SliceLaunch>* launches);
-void slice_sets(const SliceGroup* g0, const SliceGroup* g1, int* as, int* na, int* bs, int* nb);
+void slice_sets(const SliceGroup* const* gs, int ng, int* as, int* na, int* bs, int* nb);
 int slice_max_slices();
 
 // The mu search's bracketing bisection on any evaluator of N(mu) (driver.cu).

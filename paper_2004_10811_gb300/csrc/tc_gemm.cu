@@ -464,34 +464,37 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       if constexpr (LEAN) {
         if (p.out_i64) {
           // exact integer sums of slice products (full tiles): per 32-column
-          // chunk the one or two accumulators (adjacent levels, combined as
-          // acc0 * 2^d + acc1 in 32-bit integers), scaled by 2^shift and
+          // chunk the sum over the accumulators of acc_k * 2^shift_k in 64-bit
+          // integers (|acc_k| < 2^24, shift_k <= 36, at most four terms),
           // handed to the L2 bulk add in 16-column row segments
           const uint32_t tb = tbase;
 #pragma unroll 1
           for (int c = 0; c < 4 * HALVES; ++c) {
-            float a0[32], a1[32];
-            tmem_ld32(tb + uint32_t(c * 32), a0);
-            if (p.nacc == 2) tmem_ld32(tb + uint32_t(BN + c * 32), a1);
-            tmem_wait_ld();
+            long long v[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = 0;
+#pragma unroll 1
+            for (int k = 0; k < p.nacc; ++k) {
+              float a[32];
+              tmem_ld32(tb + uint32_t(k * BN + c * 32), a);
+              tmem_wait_ld();
+              const int sh = p.i64_shifts[k];
+#pragma unroll
+              for (int q = 0; q < 32; ++q) v[q] += (long long)__float2int_rn(a[q]) << sh;
+            }
             if (c == 4 * HALVES - 1) {
               tc_fence_before();
               if (!p.test_skip_arrive) mbar_arrive(&tempty[ab]);
             }
             const int cg0 = item.z * BN + c * 32;
             if (rg >= ld || cg0 >= ld) continue;
-            const long long mul = 1LL << p.i64_shift;
             uint8_t* srow = reinterpret_cast<uint8_t*>(stg) + r * I64_PITCH;
 #pragma unroll
             for (int seg = 0; seg < 32 / I64_SEG; ++seg) {
               asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 #pragma unroll
-              for (int q = 0; q < I64_SEG; ++q) {
-                const int k = seg * I64_SEG + q;
-                const int v = p.nacc == 2 ? __float2int_rn(a0[k]) * (1 << p.i64_dshift) + __float2int_rn(a1[k])
-                                          : __float2int_rn(a0[k]);
-                *reinterpret_cast<long long*>(srow + 8 * q) = (long long)v * mul;
-              }
+              for (int q = 0; q < I64_SEG; ++q)
+                *reinterpret_cast<long long*>(srow + 8 * q) = v[seg * I64_SEG + q];
               asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
               long long* d = p.out_i64 + base + int64_t(rg) * ld + cg0 + seg * I64_SEG;
               if (p.i64_accumulate)
@@ -745,13 +748,20 @@ cudaError_t launch_tc_gemm(const TcGemmParams& p, int grid, cudaStream_t st) {
     return cudaErrorInvalidValue;
   if (p.nacc * bn > p.tmem_cols) return cudaErrorInvalidValue;
   if (p.out_i64 && p.sym) return cudaErrorInvalidValue;  // integer outputs: full tiles only
-  if (p.out_i64 && (p.nacc > 2 || (p.nacc == 2 && (p.i64_dshift < 0 || p.i64_dshift > 6))))
+  // the lean epilogue combines up to four integer accumulators in 64 bits
+  // (weights 2^i64_shifts[k]); the general one two in 32 bits (d <= 6)
+  const bool lean_i64 = p.out_i64 && !p.sym && p.nacc <= 4 && p.nacc * bn <= p.tmem_cols &&
+                        (p.nacc > 2 ? bn == 128 : p.tmem_cols >= 2 * p.nacc * bn);
+  if (p.out_i64 && !lean_i64 && (p.nacc > 2 || (p.nacc == 2 && (p.i64_dshift < 0 || p.i64_dshift > 6))))
     return cudaErrorInvalidValue;
+  if (p.out_i64)
+    for (int k = 0; k < p.nacc; ++k)
+      if (lean_i64 && (p.i64_shifts[k] < 0 || p.i64_shifts[k] > 36)) return cudaErrorInvalidValue;
   const int smem = tc_smem_bytes(p.na, p.nb, p.nstage, bn);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   // the lean epilogue: one accumulator, double-buffered in TMEM, BF16-pair or
   // FP32 output without a mirror
-  const bool lean = (p.out_i64 ? p.tmem_cols >= 2 * p.nacc * bn && p.nacc <= 2 && !p.sym
+  const bool lean = (p.out_i64 ? lean_i64
                                 : p.tmem_cols >= 2 * bn && p.nacc == 1 && !(p.sym && !p.upper_only) &&
                                       (p.out_f32 || p.out_hi));
   auto run = [&](auto kern) -> cudaError_t {

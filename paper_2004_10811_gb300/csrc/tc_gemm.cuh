@@ -56,6 +56,9 @@ struct TcGemmParams {
   long long* out_i64;
   int i64_shift;
   int i64_dshift;
+  // lean epilogue: accumulator k carries the weight 2^i64_shifts[k] and up to
+  // four accumulators are combined in 64-bit integers (any weights)
+  int i64_shifts[4];
   int i64_accumulate;
   // operand and pair format: 0 BF16, 1 FP16 (A and B always share one
   // format; the (hi, lo) output pairs and C0 pairs take the same)

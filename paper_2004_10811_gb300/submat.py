@@ -109,7 +109,7 @@ def load(path: str = LIB_PATH):
     lib.submat_debug_tc_gemm.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, C.c_int,
                                          vp, vp, C.c_int, C.c_double, C.c_int, vp]
     lib.submat_dense_sign_noalloc.argtypes = [C.c_int, vp, C.c_double, vp, C.POINTER(C.c_int), vp]
-    lib.submat_debug_slice_plan.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int,
+    lib.submat_debug_slice_plan.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int,
                                             C.POINTER(C.c_int32)]
     lib.submat_debug_mu_bisect.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
                                            C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int32),
@@ -344,15 +344,15 @@ def debug_tc_gemm(A_hi, B_hi, A_lo=None, B_lo=None, n=None, sym=False, res2=None
     return C_, STATUS[st]
 
 
-def debug_slice_plan(nx, ny, sym_pairs, per_acc):
+def debug_slice_plan(nx, ny, sym_pairs, per_acc, max_acc=4):
     """Host-only test hook (include/submat_debug.h): the launch plan of an exact
     sliced product as an int32 array of (launch, accumulator, p, q, shift) rows."""
     lib = load()
     n = C.c_int32()
-    _check(lib.submat_debug_slice_plan(int(nx), int(ny), int(bool(sym_pairs)), int(per_acc), None, 0,
+    _check(lib.submat_debug_slice_plan(int(nx), int(ny), int(bool(sym_pairs)), int(per_acc), int(max_acc), None, 0,
                                        C.byref(n)))
     out = np.zeros((max(1, n.value), 5), np.int32)
-    _check(lib.submat_debug_slice_plan(int(nx), int(ny), int(bool(sym_pairs)), int(per_acc),
+    _check(lib.submat_debug_slice_plan(int(nx), int(ny), int(bool(sym_pairs)), int(per_acc), int(max_acc),
                                        out.ctypes.data_as(C.c_void_p), n.value, C.byref(n)))
     return out[:n.value]
 
