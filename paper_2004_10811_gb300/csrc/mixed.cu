@@ -1308,7 +1308,7 @@ submat_status Plan::sign_mixed(const double* K, double mu, double* D, cudaStream
     const bool hp_sliced = opt.hp_mode == 0 && max_ld <= 4096;
     const int per_acc = max_ld <= 2048 ? 2 : 1;
     SM_CUDA(cudaMemsetAsync(ms->submax, 0, sizeof(unsigned long long) * max_wave, st));
-    // the final iterate: the sliced path reads its BF16 pair directly (the
+    // the final iterate: the sliced path reads its FP16 pair directly (the
     // first slicing writes S); the FP64 residual path widens it to S here
     const PairSrc iterate{{as_h(b.X[0][0]), as_h(b.X[1][0])}, {as_h(b.X[0][1]), as_h(b.X[1][1])}, ns.par};
     if (hp_sliced) {

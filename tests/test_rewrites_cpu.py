@@ -226,3 +226,90 @@ def test_one_round_with_an_inexact_lyapunov_solve_meets_the_acceptance_bound():
     fa_cg = fa + 1e-3 * np.linalg.norm(fa) / np.linalg.norm(noise) * noise  # relative residual ~1e-3
     err = np.max(np.abs(st - fc - fa_cg - s))
     assert err < 4e-8, err
+
+
+def lyapunov_cg(h, c, steps, upper_tiles=False, tile=32, weight=2.0):
+    """CG on L -> H L + L H = C (H SPD, C symmetric), as the mixed path runs
+    it.  With upper_tiles, R and X are updated on the tiles (a, b), a <= b,
+    only (a diagonal tile whole); P is completed from its upper tiles; the
+    inner product <R, R> counts an off-diagonal tile `weight` times."""
+    n = len(h)
+    nt = n // tile
+    up = np.zeros((n, n), dtype=bool)
+    for a in range(nt):
+        for b in range(a, nt):
+            up[a * tile:(a + 1) * tile, b * tile:(b + 1) * tile] = True
+    # off-diagonal upper tiles: weight, diagonal tiles: 1, lower tiles: not stored
+    wgt = np.where(up & ~up.T, weight, np.where(up, 1.0, 0.0))
+
+    def inner(m):
+        return float(np.sum(wgt * m * m)) if upper_tiles else float(np.sum(m * m))
+
+    def full(m):  # the lower tiles from the upper ones
+        return np.where(up, m, m.T) if upper_tiles else m
+
+    x = np.zeros_like(c)
+    r = c.copy()
+    p = c.copy()
+    rr = inner(r)
+    for _ in range(steps):
+        w = h @ full(p)
+        tp = w + w.T
+        alpha = rr / float(np.sum(full(p) * tp))  # <P, W + W^T>, from the full product
+        x = x + alpha * full(p)
+        r_new = r - alpha * tp
+        if upper_tiles:
+            r_new = np.where(up, r_new, 0.0)  # the lower tiles are never written
+        rr_new = inner(r_new)
+        p = r_new + (rr_new / rr) * full(p)
+        r, rr = r_new, rr_new
+    return full(x) if upper_tiles else x
+
+
+def test_cg_on_upper_tiles_equals_the_full_cg():
+    """R, X and P are symmetric, so updating the upper tiles only, completing
+    P from them and counting off-diagonal tiles twice in <R, R> reproduces the
+    full CG; counting them once does not."""
+    n = 96
+    rng = np.random.default_rng(11)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    h = (q * rng.uniform(0.2, 1.5, n)) @ q.T
+    h = 0.5 * (h + h.T)
+    c = sym(n, 12)
+    full = lyapunov_cg(h, c, 12)
+    upper = lyapunov_cg(h, c, 12, upper_tiles=True)
+    assert np.max(np.abs(upper - full)) <= 1e-12 * np.max(np.abs(full))
+    # the solution itself: H L + L H = C to the CG's accuracy after 40 steps
+    lx = lyapunov_cg(h, c, 40, upper_tiles=True)
+    assert np.max(np.abs(h @ lx + lx @ h - c)) <= 1e-8 * np.max(np.abs(c))
+    wrong = lyapunov_cg(h, c, 12, upper_tiles=True, weight=1.0)
+    assert np.max(np.abs(wrong - full)) > 1e-3 * np.max(np.abs(full))
+
+
+def test_cg_tolerance_from_the_correction_size():
+    """The one-round rule: a correction of size delta solved to a relative
+    residual tol leaves ~delta * tol; CG stops at tol = 1e-2 where
+    delta * 1e-2 <= 2e-8, and resumes at max(2e-8 / delta, 1e-3) otherwise.
+    The remaining error then stays below 4e-8 for delta up to 2e-5."""
+    n = 60
+    rng = np.random.default_rng(13)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([rng.uniform(-1.0, -0.3, 20), rng.uniform(0.3, 1.4, n - 20)])
+    a = (q * lam) @ q.T
+    a = 0.5 * (a + a.T)
+    s = (q * np.sign(lam)) @ q.T
+    i = np.eye(n)
+    pert = sym(n, 14)
+    for delta in (1e-6, 2e-6, 5e-6, 2e-5):
+        st = s + delta * pert / np.max(np.abs(pert))
+        fc = -0.5 * st @ (i - st @ st)
+        h = 0.5 * (st @ a + a @ st)
+        c = ((st @ a - a @ st) - (fc @ a - a @ fc)) @ st
+        w, qh = np.linalg.eigh(h)
+        fa = qh @ ((qh.T @ c @ qh) / (w[:, None] + w[None, :])) @ qh.T
+        d = np.max(np.abs(fc + fa))
+        tol = 1e-2 if d * 1e-2 <= 2e-8 else max(2e-8 / d, 1e-3)
+        noise = sym(n, 15)
+        fa_cg = fa + tol * np.linalg.norm(fa) / np.linalg.norm(noise) * noise
+        err = np.max(np.abs(st - fc - fa_cg - s))
+        assert err < 4e-8, (delta, tol, err)
